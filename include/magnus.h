@@ -1,0 +1,230 @@
+/*
+ * magnus.h - C ABI of the GB300 (sm_103a) MAGNUS SpGEMM library.
+ *
+ * Computes C = A * B for sparse matrices in CSR form with FP64 values,
+ * int32 column indices and int64 row pointers, following MAGNUS
+ * (Wolfson-Pou, Laukemann, Petrini, ICS'25, arXiv 2501.07056):
+ *
+ *   setup     (Section 3.1)   per-row intermediate-product count P_i and row
+ *                             categorisation into sort / dense / fine / coarse;
+ *   symbolic  (Section 2.1)   exact nnz of every row of C ("precise
+ *                             prediction") and the prefix sum into C.rowPtr;
+ *   numeric   (Algorithms 1-4) coarse reorder (Algorithm 4), fine reorder
+ *                             (Algorithm 3), per-chunk hybrid accumulation
+ *                             (sort or dense, Section 3.4) and CSR output.
+ *
+ * Conventions shared by every entry point:
+ *   - Matrix and output pointers are DEVICE pointers (cudaMalloc'ed or any
+ *     memory the current device can address).  They are owned by the caller
+ *     and must stay valid until the call's work on `stream` has finished.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All device work is ordered on it.  The current device must be
+ *     the device that owns the pointers.
+ *   - Every function returns a magnus status (0 = MAGNUS_OK).  No C++
+ *     exception crosses this boundary.  After MAGNUS_CUDA_ERROR the CUDA
+ *     error string is available from magnus_last_cuda_error().
+ *   - Input CSR rows must hold strictly ascending column indices in
+ *     [0, n_cols) (the paper does not fix an order; this library requires
+ *     it, and checks it when magnus_params_t.validate is set).
+ *   - Output rows of C hold strictly ascending column indices.  An entry is
+ *     present whenever some product reaches it, even if its value sums to 0.
+ */
+#ifndef MAGNUS_H
+#define MAGNUS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+enum magnus_status {
+  MAGNUS_OK = 0,
+  MAGNUS_INVALID_ARG = 1,        /* NULL pointer, negative size, A.n_cols != B.n_rows */
+  MAGNUS_UNSORTED_OR_DUP = 2,    /* validate=1 found an unsorted/duplicate/out-of-range column */
+  MAGNUS_INDEX_OVERFLOW = 3,     /* a size does not fit the index types (cols >= 2^31, rows >= 2^31) */
+  MAGNUS_OUT_OF_MEMORY = 4,      /* device allocation failed or the request exceeds the memory cap */
+  MAGNUS_CUDA_ERROR = 5,         /* a CUDA runtime call failed; see magnus_last_cuda_error() */
+  MAGNUS_TIMEOUT = 6,            /* a bounded device-side wait expired (reserved) */
+  MAGNUS_NOT_SYMBOLIC = 7,       /* magnus_numeric called before magnus_symbolic on this plan */
+  MAGNUS_BAD_STATE = 8           /* the plan was built for other inputs or is unusable */
+};
+
+/* ---- row categories (Section 3.1) ------------------------------------- */
+enum magnus_category {
+  MAGNUS_CAT_AUTO = -1,   /* categorise each row by the rules of Section 3.1 */
+  MAGNUS_CAT_SORT = 0,    /* sort-based accumulator over the whole row (Algorithm 2) */
+  MAGNUS_CAT_DENSE = 1,   /* dense accumulator over the row's column range (Algorithm 1) */
+  MAGNUS_CAT_FINE = 2,    /* fine-level reorder then per-chunk accumulation (Algorithm 3) */
+  MAGNUS_CAT_COARSE = 3   /* coarse-level reorder (Algorithm 4), then the fine level */
+};
+
+/* ---- CSR operand -------------------------------------------------------
+ * row_ptr: n_rows+1 int64, row_ptr[0] = 0, nondecreasing, row_ptr[n_rows] = nnz.
+ * col:     nnz int32, per row strictly ascending, in [0, n_cols).
+ * val:     nnz float64; may be NULL where only the structure is needed
+ *          (magnus_plan, magnus_symbolic).  All three are device pointers.  */
+typedef struct {
+  int64_t n_rows;
+  int64_t n_cols;
+  int64_t nnz;
+  const int64_t* row_ptr;
+  const int32_t* col;
+  const double* val;
+} magnus_csr_t;
+
+/* ---- tuning parameters ---------------------------------------------------
+ * Every field has an "automatic" value (0, or -1 for force_category) that the
+ * planner replaces by a value derived from the device (Section 3.5 model
+ * re-derived for shared memory and L2; see magnus_chunk_model).
+ *
+ * sort_threshold      rows with P_i < sort_threshold use the sort accumulator
+ *                     (Section 3.1, category 1).  Range 1..257; 0 = 257.
+ * force_category      -1 = automatic; otherwise every non-empty row is put in
+ *                     that category (used to exercise each stage).
+ * chunk_len_fine_log2 log2 of the fine chunk length (columns) for the numeric
+ *                     phase; 0 = from the model.
+ * chunk_len_coarse_log2 log2 of the coarse chunk length (columns); 0 = from
+ *                     the model (m_CmaxSMEM).  A coarse chunk length below
+ *                     the fine one is raised to it.
+ * dense_chunk_threshold per-chunk hybrid threshold (Section 3.4): a fine chunk
+ *                     with at least this many products uses the dense
+ *                     accumulator, otherwise the sort accumulator; 0 = auto.
+ * validate            1 = check the input CSR structure on the device in
+ *                     magnus_plan (returns MAGNUS_UNSORTED_OR_DUP on failure).
+ * max_scratch_bytes   upper bound on the reorder staging buffer of one batch
+ *                     (Section 3.3 batching); 0 = automatic (a fraction of
+ *                     the free device memory at plan time).                 */
+typedef struct {
+  int32_t sort_threshold;
+  int32_t force_category;
+  int32_t chunk_len_fine_log2;
+  int32_t chunk_len_coarse_log2;
+  int32_t dense_chunk_threshold;
+  int32_t validate;
+  int64_t max_scratch_bytes;
+} magnus_params_t;
+
+/* Fill *p with the automatic values.  Returns MAGNUS_INVALID_ARG on NULL. */
+int magnus_params_default(magnus_params_t* p);
+
+typedef struct magnus_plan_s* magnus_plan_t;
+
+/* magnus_plan - setup phase (Section 3.1).
+ * Computes P_i = sum_{j in S(A_i)} nnz(B_j) (Section 5, n_interProd per row),
+ * each row's intermediate column range, and the category of every row; sorts
+ * rows into per-category lists.  Reads A and B structure (values unused);
+ * A->n_cols must equal B->n_rows.  The plan keeps copies of the two
+ * descriptors (not of the data): A and B must stay unchanged and alive until
+ * magnus_free.  `params` may be NULL (all automatic).  Synchronises `stream`
+ * once (category counts are read back).  On success *plan owns device memory
+ * released by magnus_free.  On failure *plan is set to NULL. */
+int magnus_plan(magnus_plan_t* plan, const magnus_csr_t* A, const magnus_csr_t* B,
+                const magnus_params_t* params, void* stream);
+
+/* magnus_symbolic - exact nnz of every row of C (Section 2.1, precise
+ * prediction) and C.rowPtr by prefix sum.
+ * c_row_ptr: device, A.n_rows+1 int64, written (c_row_ptr[0] = 0).
+ * nnz_c:     host, receives c_row_ptr[A.n_rows].  The call synchronises
+ *            `stream` to read it (the caller needs it to allocate C).
+ * Per-(row, coarse chunk) counts of coarse rows are kept in the plan for
+ * magnus_numeric. */
+int magnus_symbolic(magnus_plan_t plan, int64_t* c_row_ptr, int64_t* nnz_c, void* stream);
+
+/* magnus_numeric - Algorithms 1-4: fills C.col and C.val.
+ * a_val, b_val: device values of A and B (same structure as at plan time;
+ *               they may differ from the values seen earlier, so a plan can
+ *               be reused for new values).
+ * c_row_ptr:    the array written by magnus_symbolic on this plan.
+ * c_col, c_val: device, nnz_c entries each, written.
+ * Does not synchronise the stream.  Returns MAGNUS_NOT_SYMBOLIC if
+ * magnus_symbolic has not completed on this plan. */
+int magnus_numeric(magnus_plan_t plan, const double* a_val, const double* b_val,
+                   const int64_t* c_row_ptr, int32_t* c_col, double* c_val, void* stream);
+
+/* Release the plan and all device memory it owns.  Safe on NULL.  Work the
+ * plan enqueued must be complete or ordered before any reuse of that memory
+ * (frees are stream-ordered on the plan's last stream). */
+void magnus_free(magnus_plan_t plan);
+
+/* Static message for a status code. */
+const char* magnus_strerror(int status);
+
+/* Text of the last CUDA error seen by this library in the calling thread
+ * (empty string if none). */
+const char* magnus_last_cuda_error(void);
+
+/* ---- plan introspection ------------------------------------------------ */
+typedef struct {
+  int64_t n_rows;               /* rows of A (= rows of C) */
+  int64_t n_cols;               /* columns of B (= m_C) */
+  int64_t n_interprod;          /* sum of P_i (Section 5) */
+  int64_t max_row_products;     /* max P_i */
+  int64_t nnz_c;                /* after magnus_symbolic, else -1 */
+  int64_t rows_empty;           /* rows with P_i = 0 */
+  int64_t rows_per_category[4]; /* indexed by magnus_category */
+  int64_t products_per_category[4];
+  int64_t staged_products_numeric; /* products written to and re-read from
+                                      global staging by the last numeric call */
+  int64_t scratch_bytes;        /* largest staging buffer used */
+  int32_t sort_threshold;
+  int32_t chunk_len_fine_log2;
+  int32_t chunk_len_fine_sym_log2;
+  int32_t chunk_len_coarse_log2;
+  int32_t n_chunks_coarse;
+  int32_t dense_cols;           /* max column range of a dense row */
+  int32_t dense_chunk_threshold;
+  int32_t key_bits32;           /* 1 if sort keys fit in 32 bits */
+  int32_t n_batches_fine;
+  int32_t n_batches_coarse;
+} magnus_plan_info_t;
+
+int magnus_plan_info(magnus_plan_t plan, magnus_plan_info_t* info);
+
+/* ---- device timing of the stages --------------------------------------
+ * When enabled on a plan, every later magnus_symbolic / magnus_numeric call
+ * records CUDA events on its stream around each stage; magnus_stage_times
+ * returns the elapsed milliseconds of the last call (synchronising on the
+ * events).  Stage indices: see MAGNUS_STAGE_*.  Disabled by default. */
+enum magnus_stage {
+  MAGNUS_STAGE_SYM_SORT = 0, MAGNUS_STAGE_SYM_DENSE = 1, MAGNUS_STAGE_SYM_FINE = 2,
+  MAGNUS_STAGE_SYM_COARSE = 3, MAGNUS_STAGE_SYM_SCAN = 4,
+  MAGNUS_STAGE_NUM_SORT = 5, MAGNUS_STAGE_NUM_DENSE = 6, MAGNUS_STAGE_NUM_FINE = 7,
+  MAGNUS_STAGE_NUM_COARSE = 8, MAGNUS_STAGE_COUNT = 9
+};
+int magnus_enable_timing(magnus_plan_t plan, int enable);
+int magnus_stage_times(magnus_plan_t plan, double* ms, int n);
+
+/* Number of kernels this library has launched in this process. */
+uint64_t magnus_launch_count(void);
+
+/* ---- chunk model (host only; no GPU needed) -----------------------------
+ * The paper sizes chunks so that the accumulator and the reorder bookkeeping
+ * of one thread fit its private L2 (Section 3.5, Eq. 2-7).  On the GPU the
+ * private store is a thread block's shared memory and the active write lines
+ * of the reorder live in the shared L2, so Eq. 2 is evaluated with two
+ * budgets (shared memory per block, L2 share per resident block).
+ * Inputs: m_c (columns of C), smem_bytes (accumulator budget per block),
+ * l2_bytes (device L2), resident_blocks (blocks resident device-wide).
+ * Output fields are log2 chunk lengths in columns.  Returns MAGNUS_INVALID_ARG
+ * for non-positive inputs. */
+typedef struct {
+  int32_t m_c_log2;             /* ceil(log2(m_c)) */
+  int32_t chunk_len_fine_log2;  /* numeric: FP64 value + 1 bitmap bit per column */
+  int32_t chunk_len_fine_sym_log2; /* symbolic: 1 bitmap bit per column */
+  int32_t n_chunks_fine_max_log2;  /* max fine chunks one row may use (L2 bound) */
+  int32_t m_c_max_log2;         /* widest column range handled by the fine level alone */
+  int32_t n_chunks_coarse;      /* m_C / 2^m_c_max_log2 (1 = fine level suffices) */
+  int64_t fine_smem_bytes;      /* shared memory of the fine accumulator + bookkeeping */
+} magnus_chunk_model_t;
+
+int magnus_chunk_model(int64_t m_c, int64_t smem_bytes, int64_t l2_bytes,
+                       int32_t resident_blocks, magnus_chunk_model_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MAGNUS_H */

@@ -1,0 +1,161 @@
+// Internal declarations shared by the host orchestration (magnus_api.cu) and
+// the kernel translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/magnus.h"
+
+namespace magnus {
+
+// Row bins.  Sort rows are split by capacity (32 * E products, E = 1,2,4,8)
+// so each warp kernel sorts in registers with a fixed network size.
+enum Bin : int {
+  BIN_EMPTY = 0,
+  BIN_SORT32 = 1,
+  BIN_SORT64 = 2,
+  BIN_SORT128 = 3,
+  BIN_SORT256 = 4,
+  BIN_DENSE = 5,
+  BIN_FINE = 6,
+  BIN_COARSE = 7,
+  NUM_BINS = 8
+};
+
+constexpr int SORT_MAX = 256;        // largest sort-row capacity
+constexpr int DENSE_NT = 256;        // threads of the dense/fine block kernels
+constexpr int FINE_MAX_CHUNKS = 4096;  // fine chunks one block can bookkeep in smem
+constexpr int GROUP_SORT_CAP = 1024; // block sort capacity for merged fine chunks
+
+// Parameters a kernel needs to categorise a row (Section 3.1).
+struct CatParams {
+  int32_t sort_threshold;     // sort iff P < sort_threshold
+  int32_t force;              // -1 or a magnus_category
+  int32_t dense_cols;         // dense iff column range <= dense_cols
+  int32_t fine_shift;         // fine chunk = col >> fine_shift (numeric)
+  int32_t fine_max_chunks;    // fine iff the row spans <= this many fine chunks
+};
+
+struct Csr {
+  int64_t n_rows, n_cols, nnz;
+  const int64_t* rp;
+  const int32_t* col;
+  const double* val;
+};
+
+// Kernel launchers (defined in the kernel translation units).  All return
+// cudaGetLastError() of the launch.
+cudaError_t launch_validate(const Csr& M, int* d_flag, cudaStream_t s);
+cudaError_t launch_rowinfo(const Csr& A, const Csr& B, CatParams cp, int64_t* P, uint8_t* bin,
+                           int32_t* lo, int32_t* hi, cudaStream_t s);
+cudaError_t launch_bin_partition(const uint8_t* bin, int64_t n, int32_t* rows_out,
+                                 int64_t* bin_counts_dev, int64_t* blk_scratch, int64_t nblk_cap,
+                                 cudaStream_t s);
+int64_t bin_partition_blocks(int64_t n);
+cudaError_t launch_gather_i64(const int64_t* src, const int32_t* idx, int64_t n, int64_t* dst,
+                              cudaStream_t s);
+cudaError_t launch_reduce_stats(const int64_t* P, int64_t n, int64_t* out2 /*sum,max*/,
+                                cudaStream_t s);
+
+// Device-wide exclusive scan of int64 in place: a[0..n) -> exclusive prefix,
+// a[n] = total (a must hold n+1 elements).  `tmp` needs scan_tmp_elems(n).
+int64_t scan_tmp_elems(int64_t n);
+cudaError_t launch_exclusive_scan_i64(int64_t* a, int64_t n, int64_t* tmp, cudaStream_t s);
+cudaError_t launch_scan_i32_to_i64(const int32_t* in, int64_t n, int64_t* out, int64_t* tmp,
+                                   cudaStream_t s);
+
+// Sort rows (warp per row).  cnt_out: per-row count (symbolic) written at
+// c_row_ptr-like array position row (count stored in out_cnt[row]).
+struct SortArgs {
+  Csr A, B;
+  const int32_t* rows;  // row list of the bin
+  int64_t n_rows;
+  int key32;            // 1: (col << slot_bits | slot) fits 32 bits
+  // symbolic
+  int64_t* out_cnt;     // indexed by row
+  // numeric
+  const int64_t* c_rp;
+  int32_t* c_col;
+  double* c_val;
+};
+cudaError_t launch_sort_rows(int bin, bool numeric, const SortArgs& a, int num_sms, cudaStream_t s);
+
+// Dense rows (block per row).
+struct DenseArgs {
+  Csr A, B;
+  const int32_t* rows;
+  int64_t n_rows;
+  const int32_t* lo;   // per row (indexed by row id)
+  const int32_t* hi;
+  int32_t dense_cols;
+  int64_t* out_cnt;
+  const int64_t* c_rp;
+  int32_t* c_col;
+  double* c_val;
+};
+cudaError_t launch_dense_rows(bool numeric, const DenseArgs& a, int num_sms, cudaStream_t s);
+
+// Fine rows (block per row, products staged in global scratch).
+struct FineArgs {
+  Csr A, B;
+  const int32_t* rows;      // rows of this batch
+  int64_t n_rows;
+  const int64_t* stage_off; // per batch row: offset into the staging buffers
+  const int32_t* lo;
+  const int32_t* hi;
+  int32_t shift;            // fine chunk shift for this phase
+  int32_t dense_chunk_threshold;
+  int32_t* stage_col;
+  double* stage_val;
+  int64_t* out_cnt;
+  const int64_t* c_rp;
+  int32_t* c_col;
+  double* c_val;
+};
+cudaError_t launch_fine_rows(bool numeric, const FineArgs& a, cudaStream_t s);
+
+// Coarse level (Algorithm 4) for one batch of coarse rows.
+struct CoarseArgs {
+  Csr A, B;
+  const int32_t* rows;       // batch rows (global row ids)
+  int64_t n_rows;            // rows in batch
+  int64_t list_base;         // index of the batch's first row in the coarse list
+  int32_t shift_coarse;      // coarse chunk = col >> shift_coarse
+  int32_t n_chunks;          // coarse chunks (m_C >> shift_coarse, rounded up)
+  int32_t shift_fine;        // fine chunk shift inside a coarse chunk
+  int32_t dense_chunk_threshold;
+  // scratch (device)
+  int32_t* col_cnt;          // n_B + 1   (A^CSC column counts / pointers)
+  int64_t* col_ptr;          // n_B + 1
+  int32_t* csc_row;          // nnz of the batch rows
+  double* csc_val;
+  int32_t* rows_b;           // coarseRowsB list
+  int32_t* n_rows_b;         // device counter
+  int64_t* counts;           // n_rows * n_chunks + 1 (becomes offsetsCoarse)
+  int32_t* cursor;           // n_rows * n_chunks
+  int32_t* chunk_col;        // staged products
+  double* chunk_val;
+  int32_t* fine_col;         // second staging buffer for the fine level
+  double* fine_val;
+  int64_t* scan_tmp;
+  int32_t* big_list;         // buckets too large for a warp
+  int32_t* n_big;
+  // results
+  int32_t* bucket_cnt;       // symbolic: per (coarse list row, chunk) nnz; numeric: read
+  int64_t* bucket_out;       // numeric: output offset per (batch row, chunk)
+  int64_t* out_cnt;          // symbolic: per row nnz (indexed by row)
+  const int64_t* c_rp;
+  int32_t* c_col;
+  double* c_val;
+  int num_sms;
+  int64_t nnz_batch;         // nnz of A over the batch rows
+};
+cudaError_t run_coarse_batch(bool numeric, CoarseArgs& a, cudaStream_t s);
+
+// Process-wide kernel launch counter.
+void count_launch(int n = 1);
+
+}  // namespace magnus

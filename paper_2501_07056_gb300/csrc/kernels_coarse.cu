@@ -1,0 +1,359 @@
+// Coarse level (Algorithm 4) for one batch of coarse rows (Section 3.3):
+//   1. coarseRowsB and the CSC form of the batch's submatrix of A
+//      (histogram, prefix sum, scatter);
+//   2. outer-product histogram: for each needed B row and each batch row i
+//      that references it, countsCoarse[i][B.col >> shiftCoarse] += 1;
+//   3. row-chained prefix sum (one exclusive scan of the row-major
+//      countsCoarse matrix gives every row's chunk offsets after the previous
+//      row's);
+//   4. outer-product reorder: the products A.val * B.val with their
+//      chunk-local columns are written at offsetsCoarse + running count;
+//   5. the fine level on every (row, coarse chunk): a warp sort for small
+//      chunks, a thread block running Algorithm 3 for large ones.
+// Each B row is loaded once per batch and reused for every batch row that
+// references it (the reason Algorithm 4 uses the outer product).
+#include "fine_level.cuh"
+#include "sort_accum.cuh"
+
+namespace magnus {
+
+static inline unsigned grid_cap_c(int64_t blocks, int64_t cap) {
+  return (unsigned)(blocks < cap ? (blocks < 1 ? 1 : blocks) : cap);
+}
+
+__global__ void k_csc_count(Csr A, const int32_t* __restrict__ rows, int64_t nb,
+                            int32_t* __restrict__ col_cnt, int32_t* __restrict__ rows_b,
+                            int32_t* __restrict__ n_rows_b) {
+  const int lane = lane_id();
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nb; t += nw) {
+    const int32_t row = rows[t];
+    for (int64_t j = A.rp[row] + lane; j < A.rp[row + 1]; j += 32) {
+      const int32_t b = A.col[j];
+      if (atomicAdd(&col_cnt[b], 1) == 0) rows_b[atomicAdd(n_rows_b, 1)] = b;
+    }
+  }
+}
+
+template <bool NUMERIC>
+__global__ void k_csc_fill(Csr A, const int32_t* __restrict__ rows, int64_t nb,
+                           const int64_t* __restrict__ col_ptr, int32_t* __restrict__ cursor,
+                           int32_t* __restrict__ csc_row, double* __restrict__ csc_val) {
+  const int lane = lane_id();
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nb; t += nw) {
+    const int32_t row = rows[t];
+    for (int64_t j = A.rp[row] + lane; j < A.rp[row + 1]; j += 32) {
+      const int32_t b = A.col[j];
+      const int64_t pos = col_ptr[b] + atomicAdd(&cursor[b], 1);
+      csc_row[pos] = (int32_t)t;
+      if (NUMERIC) csc_val[pos] = A.val[j];
+    }
+  }
+}
+
+// Outer-product traversal.  Warp per B row of coarseRowsB; the lanes hold 32
+// consecutive entries of the B row and loop over the A^CSC column of that B
+// row.  Lanes hitting the same (row, chunk) are combined with match_any so
+// one atomic serves them all.
+template <bool REORDER, bool NUMERIC>
+__global__ void k_coarse_outer(Csr B, const int32_t* __restrict__ rows_b,
+                               const int32_t* __restrict__ n_rows_b,
+                               const int64_t* __restrict__ col_ptr,
+                               const int32_t* __restrict__ csc_row,
+                               const double* __restrict__ csc_val, int sc, int nc,
+                               int64_t* __restrict__ counts, int32_t* __restrict__ cursor,
+                               int32_t* __restrict__ chunk_col, double* __restrict__ chunk_val) {
+  const int lane = lane_id();
+  const int nrb = *n_rows_b;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nrb; w += nw) {
+    const int32_t b = rows_b[w];
+    const int64_t bs = B.rp[b];
+    const int64_t L = B.rp[b + 1] - bs;
+    const int64_t cs = col_ptr[b], ce = col_ptr[b + 1];
+    for (int64_t k0 = 0; k0 < L; k0 += 32) {
+      const int64_t k = k0 + lane;
+      const bool valid = k < L;
+      const int32_t col = valid ? B.col[bs + k] : 0;
+      const double bv = (NUMERIC && valid) ? B.val[bs + k] : 0.0;
+      const int chunk = col >> sc;
+      const unsigned active = __ballot_sync(FULL, valid);
+      for (int64_t e = cs; e < ce; ++e) {
+        const int32_t t = csc_row[e];
+        const double av = NUMERIC ? csc_val[e] : 0.0;
+        if (valid) {
+          const int64_t slot = (int64_t)t * nc + chunk;
+          const unsigned m = __match_any_sync(active, chunk);
+          const int leader = __ffs(m) - 1;
+          if (!REORDER) {
+            if (lane == leader)
+              atomicAdd(reinterpret_cast<unsigned long long*>(&counts[slot]),
+                        (unsigned long long)__popc(m));
+          } else {
+            int base = 0;
+            if (lane == leader) base = atomicAdd(&cursor[slot], __popc(m));
+            base = __shfl_sync(m, base, leader);
+            const int64_t pos = counts[slot] + base + __popc(m & ((1u << lane) - 1));
+            st_stream(&chunk_col[pos], col - (chunk << sc));
+            if (NUMERIC) st_stream(&chunk_val[pos], av * bv);
+          }
+        }
+      }
+    }
+  }
+}
+
+// Output offset of every (batch row, coarse chunk) inside its row of C:
+// exclusive prefix over the chunks of the row's symbolic chunk counts.
+__global__ void k_bucket_offsets(const int32_t* __restrict__ bucket_cnt, int64_t nb, int nc,
+                                 int64_t list_base, int64_t* __restrict__ bucket_out) {
+  const int lane = lane_id();
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nb; t += nw) {
+    int64_t run = 0;
+    for (int c0 = 0; c0 < nc; c0 += 32) {
+      const int c = c0 + lane;
+      const int64_t v = (c < nc) ? bucket_cnt[(list_base + t) * nc + c] : 0;
+      const int64_t inc = warp_inclusive_scan(v);
+      if (c < nc) bucket_out[t * nc + c] = run + inc - v;
+      run += __shfl_sync(FULL, inc, 31);
+    }
+  }
+}
+
+__global__ void k_row_totals(const int32_t* __restrict__ bucket_cnt, const int32_t* __restrict__ rows,
+                             int64_t nb, int nc, int64_t list_base, int64_t* __restrict__ out_cnt) {
+  const int lane = lane_id();
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nb; t += nw) {
+    int64_t s = 0;
+    for (int c = lane; c < nc; c += 32) s += bucket_cnt[(list_base + t) * nc + c];
+    s = warp_sum(s);
+    if (lane == 0) out_cnt[rows[t]] = s;
+  }
+}
+
+// Small coarse chunks (at most 256 products): one warp sorts and merges.
+template <int E, typename K, bool NUMERIC>
+__device__ __forceinline__ int bucket_warp(const int32_t* __restrict__ ccol,
+                                           const double* __restrict__ cval, int n, double* vals,
+                                           K* skeys, int32_t col_add, int32_t* out_col,
+                                           double* out_val) {
+  using KT = KeyTraits<K>;
+  constexpr int SB = Log2Cap<E>::v;
+  const int lane = lane_id();
+  K key[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int s = e * 32 + lane;
+    if (s < n) {
+      key[e] = KT::template make<SB>(ccol[s], s);
+      if (NUMERIC) vals[s] = cval[s];
+    } else {
+      key[e] = ~K(0);
+    }
+  }
+  warp_bitonic_sort<E>(key);
+  __syncwarp();
+  return warp_merge_emit<E, K, NUMERIC>(key, n, vals, skeys, col_add, out_col, out_val);
+}
+
+constexpr int BK_NW = 4;
+
+template <typename K, bool NUMERIC>
+__global__ void __launch_bounds__(BK_NW * 32)
+    k_bucket_small(const int64_t* __restrict__ offs, int64_t nbk, const int32_t* __restrict__ chunk_col,
+                   const double* __restrict__ chunk_val, int sc, int nc, int64_t list_base,
+                   const int32_t* __restrict__ rows, int32_t* __restrict__ bucket_cnt,
+                   const int64_t* __restrict__ bucket_out, const int64_t* __restrict__ c_rp,
+                   int32_t* __restrict__ c_col, double* __restrict__ c_val,
+                   int32_t* __restrict__ big_list, int32_t* __restrict__ n_big) {
+  __shared__ double s_vals[BK_NW][NUMERIC ? SORT_MAX : 1];
+  __shared__ K s_keys[BK_NW][NUMERIC ? SORT_MAX : 1];
+  const int lane = lane_id(), w = warp_id();
+  const int64_t nw = (int64_t)gridDim.x * BK_NW;
+  for (int64_t id = (int64_t)blockIdx.x * BK_NW + w; id < nbk; id += nw) {
+    const int64_t p0 = offs[id];
+    const int n = (int)(offs[id + 1] - p0);
+    const int64_t t = id / nc;
+    const int c = (int)(id - t * nc);
+    if (n > SORT_MAX) {
+      if (lane == 0) big_list[atomicAdd(n_big, 1)] = (int32_t)id;
+      continue;
+    }
+    int32_t* oc = nullptr;
+    double* ov = nullptr;
+    if (NUMERIC) {
+      if (n == 0) continue;
+      const int64_t o = c_rp[rows[t]] + bucket_out[id];
+      oc = c_col + o;
+      ov = c_val + o;
+    }
+    int cnt = 0;
+    if (n > 0) {
+      const int32_t col_add = c << sc;
+      const int32_t* cc = chunk_col + p0;
+      const double* cv = NUMERIC ? chunk_val + p0 : nullptr;
+      if (n <= 32) cnt = bucket_warp<1, K, NUMERIC>(cc, cv, n, s_vals[w], s_keys[w], col_add, oc, ov);
+      else if (n <= 64) cnt = bucket_warp<2, K, NUMERIC>(cc, cv, n, s_vals[w], s_keys[w], col_add, oc, ov);
+      else if (n <= 128) cnt = bucket_warp<4, K, NUMERIC>(cc, cv, n, s_vals[w], s_keys[w], col_add, oc, ov);
+      else cnt = bucket_warp<8, K, NUMERIC>(cc, cv, n, s_vals[w], s_keys[w], col_add, oc, ov);
+    }
+    if (!NUMERIC && lane == 0) bucket_cnt[(list_base + t) * nc + c] = cnt;
+    __syncwarp();
+  }
+}
+
+// Large coarse chunks: one block runs the fine level (Algorithm 3) on the
+// chunk's staged products, reordering into the second staging buffer.
+template <bool NUMERIC>
+__global__ void __launch_bounds__(FNT)
+    k_bucket_big(const int64_t* __restrict__ offs, const int32_t* __restrict__ big_list,
+                 const int32_t* __restrict__ n_big, const int32_t* __restrict__ chunk_col,
+                 const double* __restrict__ chunk_val, int32_t* __restrict__ fine_col,
+                 double* __restrict__ fine_val, int sc, int sf, int nc, int dthr,
+                 int64_t list_base, const int32_t* __restrict__ rows,
+                 int32_t* __restrict__ bucket_cnt, const int64_t* __restrict__ bucket_out,
+                 const int64_t* __restrict__ c_rp, int32_t* __restrict__ c_col,
+                 double* __restrict__ c_val) {
+  extern __shared__ __align__(16) unsigned char fsm[];
+  const int shift = sf < sc ? sf : sc;  // the launch sizes shared memory with this shift
+  const FineSmem f = fine_carve(fsm, NUMERIC, shift, FINE_MAX_CHUNKS);
+  __shared__ int64_t ws[FNT / 32 + 1];
+  const int nbig = *n_big;
+  const int nch = 1 << (sc - shift);
+  for (int q = blockIdx.x; q < nbig; q += gridDim.x) {
+    const int64_t id = big_list[q];
+    const int64_t p0 = offs[id];
+    const int n = (int)(offs[id + 1] - p0);
+    const int64_t t = id / nc;
+    const int c = (int)(id - t * nc);
+    const int64_t col_base = (int64_t)c << sc;
+    int32_t* oc = nullptr;
+    double* ov = nullptr;
+    if (NUMERIC) {
+      const int64_t o = c_rp[rows[t]] + bucket_out[id];
+      oc = c_col + o;
+      ov = c_val + o;
+    }
+    const int32_t* cc = chunk_col + p0;
+    const double* cv = NUMERIC ? chunk_val + p0 : nullptr;
+    // histogram over fine chunks of the coarse chunk
+    for (int i = threadIdx.x; i < nch; i += FNT) f.cnt[i] = 0;
+    __syncthreads();
+    for (int p = threadIdx.x; p < n; p += FNT) atomicAdd(&f.cnt[cc[p] >> shift], 1);
+    __syncthreads();
+    int32_t run = 0;
+    for (int i0 = 0; i0 < nch; i0 += FNT) {
+      const int i = i0 + threadIdx.x;
+      const int64_t v = (i < nch) ? f.cnt[i] : 0;
+      int64_t tot;
+      const int64_t ex = block_exclusive_scan<FNT>(v, ws, &tot);
+      if (i < nch) {
+        f.off[i] = run + (int32_t)ex;
+        f.cnt[i] = 0;
+      }
+      run += (int32_t)tot;
+    }
+    if (threadIdx.x == 0) f.off[nch] = run;
+    __syncthreads();
+    int32_t* fc = fine_col + p0;
+    double* fv = NUMERIC ? fine_val + p0 : nullptr;
+    for (int p = threadIdx.x; p < n; p += FNT) {
+      const int32_t col = cc[p];
+      const int ch = col >> shift;
+      const int pos = f.off[ch] + atomicAdd(&f.cnt[ch], 1);
+      st_stream(&fc[pos], col);
+      if (NUMERIC) st_stream(&fv[pos], cv[p]);
+    }
+    __syncthreads();
+    const int64_t cnt = fine_accumulate_chunks<NUMERIC>(f, nch, shift, dthr, fc, fv, col_base,
+                                                        oc, ov, ws);
+    if (!NUMERIC && threadIdx.x == 0) bucket_cnt[(list_base + t) * nc + c] = (int32_t)cnt;
+    __syncthreads();
+  }
+}
+
+template <bool NUMERIC>
+static cudaError_t coarse_impl(CoarseArgs& a, cudaStream_t s) {
+  cudaError_t e;
+  const int64_t nB = a.B.n_rows;
+  const int64_t nbk = a.n_rows * a.n_chunks;
+  const int nt = 256;
+  const unsigned gw = grid_cap_c((a.n_rows + 7) / 8, (int64_t)a.num_sms * 32);
+#define CK(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
+  // 1. A^CSC and coarseRowsB
+  CK(cudaMemsetAsync(a.col_cnt, 0, (size_t)(nB + 1) * sizeof(int32_t), s));
+  CK(cudaMemsetAsync(a.n_rows_b, 0, sizeof(int32_t), s));
+  k_csc_count<<<gw, nt, 0, s>>>(a.A, a.rows, a.n_rows, a.col_cnt, a.rows_b, a.n_rows_b);
+  count_launch();
+  CK(cudaGetLastError());
+  CK(launch_scan_i32_to_i64(a.col_cnt, nB, a.col_ptr, a.scan_tmp, s));
+  CK(cudaMemsetAsync(a.col_cnt, 0, (size_t)(nB + 1) * sizeof(int32_t), s));
+  k_csc_fill<NUMERIC><<<gw, nt, 0, s>>>(a.A, a.rows, a.n_rows, a.col_ptr, a.col_cnt, a.csc_row,
+                                        a.csc_val);
+  count_launch();
+  CK(cudaGetLastError());
+  // 2. histogram
+  CK(cudaMemsetAsync(a.counts, 0, (size_t)(nbk + 1) * sizeof(int64_t), s));
+  const unsigned go = (unsigned)a.num_sms * 16;
+  k_coarse_outer<false, false><<<go, nt, 0, s>>>(a.B, a.rows_b, a.n_rows_b, a.col_ptr, a.csc_row,
+                                                 a.csc_val, a.shift_coarse, a.n_chunks, a.counts,
+                                                 a.cursor, a.chunk_col, a.chunk_val);
+  count_launch();
+  CK(cudaGetLastError());
+  // 3. row-chained prefix sum
+  CK(launch_exclusive_scan_i64(a.counts, nbk, a.scan_tmp, s));
+  // 4. reorder
+  CK(cudaMemsetAsync(a.cursor, 0, (size_t)nbk * sizeof(int32_t), s));
+  k_coarse_outer<true, NUMERIC><<<go, nt, 0, s>>>(a.B, a.rows_b, a.n_rows_b, a.col_ptr, a.csc_row,
+                                                  a.csc_val, a.shift_coarse, a.n_chunks, a.counts,
+                                                  a.cursor, a.chunk_col, a.chunk_val);
+  count_launch();
+  CK(cudaGetLastError());
+  // 5. fine level per (row, coarse chunk)
+  if (NUMERIC) {
+    k_bucket_offsets<<<gw, nt, 0, s>>>(a.bucket_cnt, a.n_rows, a.n_chunks, a.list_base,
+                                       a.bucket_out);
+    count_launch();
+    CK(cudaGetLastError());
+  }
+  CK(cudaMemsetAsync(a.n_big, 0, sizeof(int32_t), s));
+  const bool k32 = a.shift_coarse + 8 <= 32;
+  const unsigned gb = grid_cap_c((nbk + BK_NW - 1) / BK_NW, (int64_t)a.num_sms * 64);
+  if (k32)
+    k_bucket_small<uint32_t, NUMERIC><<<gb, BK_NW * 32, 0, s>>>(
+        a.counts, nbk, a.chunk_col, a.chunk_val, a.shift_coarse, a.n_chunks, a.list_base, a.rows,
+        a.bucket_cnt, a.bucket_out, a.c_rp, a.c_col, a.c_val, a.big_list, a.n_big);
+  else
+    k_bucket_small<uint64_t, NUMERIC><<<gb, BK_NW * 32, 0, s>>>(
+        a.counts, nbk, a.chunk_col, a.chunk_val, a.shift_coarse, a.n_chunks, a.list_base, a.rows,
+        a.bucket_cnt, a.bucket_out, a.c_rp, a.c_col, a.c_val, a.big_list, a.n_big);
+  count_launch();
+  CK(cudaGetLastError());
+  const size_t smem = fine_smem_bytes(NUMERIC, a.shift_fine < a.shift_coarse ? a.shift_fine : a.shift_coarse,
+                                      FINE_MAX_CHUNKS);
+  CK(cudaFuncSetAttribute(k_bucket_big<NUMERIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_bucket_big<NUMERIC><<<(unsigned)a.num_sms * 2, FNT, smem, s>>>(
+      a.counts, a.big_list, a.n_big, a.chunk_col, a.chunk_val, a.fine_col, a.fine_val,
+      a.shift_coarse, a.shift_fine, a.n_chunks, a.dense_chunk_threshold, a.list_base, a.rows,
+      a.bucket_cnt, a.bucket_out, a.c_rp, a.c_col, a.c_val);
+  count_launch();
+  CK(cudaGetLastError());
+  if (!NUMERIC) {
+    k_row_totals<<<gw, nt, 0, s>>>(a.bucket_cnt, a.rows, a.n_rows, a.n_chunks, a.list_base,
+                                   a.out_cnt);
+    count_launch();
+    CK(cudaGetLastError());
+  }
+#undef CK
+  return cudaSuccess;
+}
+
+cudaError_t run_coarse_batch(bool numeric, CoarseArgs& a, cudaStream_t s) {
+  if (a.n_rows == 0) return cudaSuccess;
+  return numeric ? coarse_impl<true>(a, s) : coarse_impl<false>(a, s);
+}
+
+}  // namespace magnus

@@ -1,0 +1,765 @@
+// C ABI of the MAGNUS SpGEMM library: parameter model, setup (plan),
+// symbolic and numeric phases.  Host orchestration only; every step of the
+// computation runs in the kernels of the other translation units.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace magnus;
+
+namespace magnus {
+uint64_t launches_total();
+size_t fine_smem_for(bool numeric, int shift);
+}
+
+static thread_local std::string g_cuda_err;
+
+static int cuda_fail(cudaError_t e, const char* where) {
+  g_cuda_err = std::string(where) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return MAGNUS_OUT_OF_MEMORY;
+  return MAGNUS_CUDA_ERROR;
+}
+
+#define CUDA_TRY(x)                                   \
+  do {                                                \
+    cudaError_t _e = (x);                             \
+    if (_e != cudaSuccess) return cuda_fail(_e, #x);  \
+  } while (0)
+
+#define MAG_TRY(x)             \
+  do {                         \
+    int _s = (x);              \
+    if (_s != MAGNUS_OK) return _s; \
+  } while (0)
+
+static int ceil_log2_i64(int64_t x) {
+  int b = 0;
+  while (((int64_t)1 << b) < x) ++b;
+  return b;
+}
+
+// ---------------------------------------------------------------------------
+// Chunk model: Eq. 2 of Section 3.5 evaluated with GPU storage terms.
+//   s_denseAccum  numeric 8 + 1/8 bytes per column (FP64 value + bitmap bit),
+//                 symbolic 1/8 byte (bitmap bit only)
+//   s_chunkFine   8 bytes in shared memory (count + offset, int32 each);
+//                 the active write lines of the reorder (two 128-byte lines per
+//                 chunk, col and val streams) live in L2, shared by all
+//                 resident blocks, so they bound the chunk count separately.
+// Among chunk lengths that satisfy both budgets, the one minimising Eq. 2
+// is taken.  When none does, the coarse level is needed: the widest column
+// range with a feasible fine level is m_CmaxSMEM (the analogue of Eq. 5).
+int magnus_chunk_model(int64_t m_c, int64_t smem_bytes, int64_t l2_bytes, int32_t resident_blocks,
+                       magnus_chunk_model_t* out) {
+  if (!out || m_c <= 0 || smem_bytes <= 0 || l2_bytes <= 0 || resident_blocks <= 0)
+    return MAGNUS_INVALID_ARG;
+  const int M = ceil_log2_i64(m_c);
+  const double s_da_num = 8.0 + 1.0 / 8.0;
+  const double s_da_sym = 1.0 / 8.0;
+  const double s_cf = 8.0;
+  const double line_bytes = 256.0;
+  double nmax = (double)l2_bytes / 2.0 / ((double)resident_blocks * line_bytes);
+  int nmax_log2 = 0;
+  while (std::ldexp(1.0, nmax_log2 + 1) <= nmax) ++nmax_log2;
+  if (nmax_log2 > 12) nmax_log2 = 12;  // shared-memory bookkeeping limit
+  auto feasible = [&](int m, int c, double s_da) {
+    const double acc = std::ldexp(1.0, c) * s_da;
+    const double book = std::ldexp(1.0, m - c) * s_cf;
+    return (m - c) <= nmax_log2 && acc + book <= (double)smem_bytes;
+  };
+  auto best_c = [&](int m, double s_da) {
+    int best = -1;
+    double bests = 0.0;
+    for (int c = 5; c <= m; ++c) {
+      if (!feasible(m, c, s_da)) continue;
+      const double s = std::ldexp(1.0, c) * s_da + std::ldexp(1.0, m - c) * s_cf;
+      if (best < 0 || s < bests) {
+        best = c;
+        bests = s;
+      }
+    }
+    return best;
+  };
+  memset(out, 0, sizeof(*out));
+  out->m_c_log2 = M;
+  out->n_chunks_fine_max_log2 = nmax_log2;
+  int m = M < 5 ? 5 : M;
+  int c = best_c(m, s_da_num);
+  while (c < 0 && m > 5) {
+    --m;
+    c = best_c(m, s_da_num);
+  }
+  if (c < 0) c = 5;
+  out->m_c_max_log2 = m;
+  out->chunk_len_fine_log2 = c;
+  out->n_chunks_coarse = (M > m) ? (int32_t)(1 << (M - m)) : 1;
+  out->fine_smem_bytes = (int64_t)(std::ldexp(1.0, c) * s_da_num + std::ldexp(1.0, m - c) * s_cf);
+  // Symbolic: bitmap only.  A single chunk over the whole range when the
+  // bitmap fits (no reorder at all); otherwise the Eq. 2 minimiser.
+  const int msym = M < 5 ? 5 : M;
+  if (std::ldexp(1.0, msym) * s_da_sym <= (double)smem_bytes) {
+    out->chunk_len_fine_sym_log2 = msym;
+  } else {
+    int cs = best_c(msym, s_da_sym);
+    out->chunk_len_fine_sym_log2 = cs < 0 ? c : cs;
+  }
+  return MAGNUS_OK;
+}
+
+// ---------------------------------------------------------------------------
+struct magnus_plan_s {
+  int device = 0;
+  int num_sms = 0;
+  int smem_optin = 0;
+  int64_t l2_bytes = 0;
+  Csr A{}, B{};
+  magnus_params_t params{};
+  int sort_T = 256;
+  int dense_cols = 8192;
+  int shift_fine = 13;
+  int shift_fine_sym = 20;
+  int shift_coarse = 24;
+  int n_chunks_coarse = 1;
+  int dthr = 256;
+  int col_bits = 0;
+  int64_t scratch_cap = 0;  // bytes
+  // device arrays owned by the plan
+  std::vector<void*> owned;
+  int64_t* P = nullptr;
+  uint8_t* bin = nullptr;
+  int32_t* lo = nullptr;
+  int32_t* hi = nullptr;
+  int32_t* rows_sorted = nullptr;
+  int64_t bin_off[NUM_BINS + 1] = {0};
+  // fine rows (heaviest first), batches as list index ranges
+  std::vector<int32_t> fine_rows;
+  std::vector<int64_t> fine_P;
+  std::vector<int32_t> fine_lo, fine_hi;
+  std::vector<int64_t> fine_batches;  // boundaries, size nb+1
+  int32_t* fine_rows_d = nullptr;
+  int64_t* fine_stage_off_d = nullptr;
+  std::vector<int64_t> fine_stage_off;
+  // coarse rows
+  std::vector<int32_t> coarse_rows;
+  std::vector<int64_t> coarse_P;
+  std::vector<int64_t> coarse_nnz;
+  std::vector<int64_t> coarse_batches;
+  int32_t* coarse_rows_d = nullptr;
+  int32_t* bucket_cnt = nullptr;
+  // state and statistics
+  bool symbolic_done = false;
+  int64_t nnz_c = -1;
+  int64_t n_interprod = 0, max_P = 0;
+  int64_t rows_cat[4] = {0}, prods_cat[4] = {0};
+  int64_t staged_numeric = 0, scratch_used = 0;
+  int key32[NUM_BINS] = {0};
+  // timing
+  bool timing = false;
+  cudaEvent_t ev[2 * MAGNUS_STAGE_COUNT] = {};
+  bool ev_used[MAGNUS_STAGE_COUNT] = {};
+  cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+int dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMallocAsync(p, bytes, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return cuda_fail(e, "cudaMallocAsync");
+  }
+  return MAGNUS_OK;
+}
+
+template <typename T>
+int plan_alloc(magnus_plan_t pl, T** p, size_t count, cudaStream_t s) {
+  void* v;
+  MAG_TRY(dev_alloc(&v, count * sizeof(T), s));
+  pl->owned.push_back(v);
+  *p = reinterpret_cast<T*>(v);
+  return MAGNUS_OK;
+}
+
+// Stream-ordered scratch freed when the guard goes out of scope.
+struct Scratch {
+  cudaStream_t s;
+  std::vector<void*> ptrs;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  ~Scratch() {
+    for (void* p : ptrs) cudaFreeAsync(p, s);
+  }
+  template <typename T>
+  int get(T** p, size_t count) {
+    void* v;
+    MAG_TRY(dev_alloc(&v, count * sizeof(T), s));
+    ptrs.push_back(v);
+    *p = reinterpret_cast<T*>(v);
+    return MAGNUS_OK;
+  }
+};
+
+void ensure_pool_retains(int dev) {
+  static bool done[64] = {false};
+  if (dev < 0 || dev >= 64 || done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done[dev] = true;
+}
+
+struct StageTimer {
+  magnus_plan_t p;
+  int stage;
+  cudaStream_t s;
+  StageTimer(magnus_plan_t pl, int st, cudaStream_t str) : p(pl), stage(st), s(str) {
+    if (p->timing) {
+      cudaEventRecord(p->ev[2 * stage], s);
+      p->ev_used[stage] = true;
+    }
+  }
+  ~StageTimer() {
+    if (p->timing) cudaEventRecord(p->ev[2 * stage + 1], s);
+  }
+};
+
+int check_csr(const magnus_csr_t* M) {
+  if (!M) return MAGNUS_INVALID_ARG;
+  if (M->n_rows < 0 || M->n_cols < 0 || M->nnz < 0) return MAGNUS_INVALID_ARG;
+  if (M->n_rows >= ((int64_t)1 << 31) - 1 || M->n_cols > ((int64_t)1 << 31) - 1)
+    return MAGNUS_INDEX_OVERFLOW;
+  if (!M->row_ptr) return MAGNUS_INVALID_ARG;
+  if (M->nnz > 0 && !M->col) return MAGNUS_INVALID_ARG;
+  return MAGNUS_OK;
+}
+
+// Batches of consecutive list entries with sum(P) <= cap (a single entry
+// above the cap forms its own batch).  Returns boundaries.
+std::vector<int64_t> make_batches(const std::vector<int64_t>& P, int64_t cap_products,
+                                  int64_t max_rows) {
+  std::vector<int64_t> b{0};
+  int64_t acc = 0, rows = 0;
+  for (size_t i = 0; i < P.size(); ++i) {
+    if (rows > 0 && (acc + P[i] > cap_products || rows >= max_rows)) {
+      b.push_back((int64_t)i);
+      acc = 0;
+      rows = 0;
+    }
+    acc += P[i];
+    ++rows;
+  }
+  if (b.back() != (int64_t)P.size()) b.push_back((int64_t)P.size());
+  return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int magnus_params_default(magnus_params_t* p) {
+  if (!p) return MAGNUS_INVALID_ARG;
+  memset(p, 0, sizeof(*p));
+  p->force_category = MAGNUS_CAT_AUTO;
+  return MAGNUS_OK;
+}
+
+const char* magnus_strerror(int s) {
+  switch (s) {
+    case MAGNUS_OK: return "ok";
+    case MAGNUS_INVALID_ARG: return "invalid argument";
+    case MAGNUS_UNSORTED_OR_DUP: return "input CSR has unsorted, duplicate or out-of-range columns";
+    case MAGNUS_INDEX_OVERFLOW: return "size exceeds the index types";
+    case MAGNUS_OUT_OF_MEMORY: return "out of device memory";
+    case MAGNUS_CUDA_ERROR: return "CUDA error";
+    case MAGNUS_TIMEOUT: return "device wait timed out";
+    case MAGNUS_NOT_SYMBOLIC: return "numeric called before symbolic";
+    case MAGNUS_BAD_STATE: return "plan in a bad state";
+    default: return "unknown status";
+  }
+}
+
+const char* magnus_last_cuda_error(void) { return g_cuda_err.c_str(); }
+
+uint64_t magnus_launch_count(void) { return launches_total(); }
+
+void magnus_free(magnus_plan_t p) {
+  if (!p) return;
+  cudaStream_t s = p->last_stream;
+  for (void* v : p->owned) cudaFreeAsync(v, s);
+  for (int i = 0; i < 2 * MAGNUS_STAGE_COUNT; ++i)
+    if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+  delete p;
+}
+
+static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t* B,
+                     const magnus_params_t* params, cudaStream_t s) {
+  CUDA_TRY(cudaGetDevice(&pl->device));
+  ensure_pool_retains(pl->device);
+  CUDA_TRY(cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device));
+  CUDA_TRY(cudaDeviceGetAttribute(&pl->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                  pl->device));
+  int l2 = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, pl->device));
+  pl->l2_bytes = l2;
+  pl->A = Csr{A->n_rows, A->n_cols, A->nnz, A->row_ptr, A->col, A->val};
+  pl->B = Csr{B->n_rows, B->n_cols, B->nnz, B->row_ptr, B->col, B->val};
+  if (params) pl->params = *params; else magnus_params_default(&pl->params);
+  const magnus_params_t& P = pl->params;
+  if (P.force_category < -1 || P.force_category > 3) return MAGNUS_INVALID_ARG;
+  if (P.sort_threshold < 0 || P.sort_threshold > SORT_MAX + 1) return MAGNUS_INVALID_ARG;
+  pl->sort_T = P.sort_threshold > 0 ? P.sort_threshold : 256;
+  const int64_t m_c = B->n_cols > 0 ? B->n_cols : 1;
+  pl->col_bits = ceil_log2_i64(m_c);
+  // chunk model with a 64 KB accumulator budget per block (two fine blocks
+  // per SM) and a 128 KB bitmap budget for the symbolic phase
+  magnus_chunk_model_t cm, cms;
+  MAG_TRY(magnus_chunk_model(m_c, 64 * 1024, pl->l2_bytes, pl->num_sms * 2, &cm));
+  MAG_TRY(magnus_chunk_model(m_c, 128 * 1024, pl->l2_bytes, pl->num_sms, &cms));
+  pl->dense_cols = 8192;
+  pl->shift_fine = P.chunk_len_fine_log2 > 0 ? P.chunk_len_fine_log2 : cm.chunk_len_fine_log2;
+  if (pl->shift_fine > 13) pl->shift_fine = 13;  // 2^13 doubles = 64 KB accumulator
+  if (pl->shift_fine < 5) pl->shift_fine = 5;
+  pl->shift_fine_sym = cms.chunk_len_fine_sym_log2;
+  if (pl->shift_fine_sym > 20) pl->shift_fine_sym = 20;  // 128 KB bitmap
+  if (pl->shift_fine_sym < pl->shift_fine) pl->shift_fine_sym = pl->shift_fine;
+  int sc = P.chunk_len_coarse_log2 > 0 ? P.chunk_len_coarse_log2 : cm.m_c_max_log2;
+  if (sc > pl->col_bits) sc = pl->col_bits;
+  if (sc < pl->shift_fine) sc = pl->shift_fine;
+  if (sc - pl->shift_fine > 12) sc = pl->shift_fine + 12;  // fine chunks per coarse chunk
+  if (sc > 31) sc = 31;
+  pl->shift_coarse = sc;
+  pl->n_chunks_coarse = (int)((m_c + ((int64_t)1 << sc) - 1) >> sc);
+  pl->dthr = P.dense_chunk_threshold > 0 ? P.dense_chunk_threshold : 256;
+  if (pl->dthr > GROUP_SORT_CAP) pl->dthr = GROUP_SORT_CAP;
+  for (int b = BIN_SORT32; b <= BIN_SORT256; ++b) {
+    const int sb = 4 + b;  // log2(32 * E): 5, 6, 7, 8
+    pl->key32[b] = (pl->col_bits + sb <= 32) ? 1 : 0;
+  }
+  size_t free_b = 0, total_b = 0;
+  CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  if (P.max_scratch_bytes > 0) {
+    pl->scratch_cap = P.max_scratch_bytes;
+  } else {
+    pl->scratch_cap = std::min<int64_t>((int64_t)(free_b / 4), (int64_t)32 << 30);
+    if (pl->scratch_cap < ((int64_t)64 << 20)) pl->scratch_cap = (int64_t)64 << 20;
+  }
+
+  const int64_t n = A->n_rows;
+  if (P.validate) {
+    int* flag;
+    MAG_TRY(plan_alloc(pl, &flag, 1, s));
+    CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    CUDA_TRY(launch_validate(pl->A, flag, s));
+    CUDA_TRY(launch_validate(pl->B, flag, s));
+    int h = 0;
+    CUDA_TRY(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (h) return MAGNUS_UNSORTED_OR_DUP;
+  }
+  MAG_TRY(plan_alloc(pl, &pl->P, n + 1, s));
+  MAG_TRY(plan_alloc(pl, &pl->bin, n + 1, s));
+  MAG_TRY(plan_alloc(pl, &pl->lo, n + 1, s));
+  MAG_TRY(plan_alloc(pl, &pl->hi, n + 1, s));
+  MAG_TRY(plan_alloc(pl, &pl->rows_sorted, n + 1, s));
+  CatParams cp;
+  cp.sort_threshold = pl->sort_T;
+  cp.force = P.force_category;
+  cp.dense_cols = pl->dense_cols;
+  cp.fine_shift = pl->shift_fine;
+  cp.fine_max_chunks = FINE_MAX_CHUNKS;
+  CUDA_TRY(launch_rowinfo(pl->A, pl->B, cp, pl->P, pl->bin, pl->lo, pl->hi, s));
+  int64_t* stats;
+  MAG_TRY(plan_alloc(pl, &stats, 2 + NUM_BINS + 1, s));
+  CUDA_TRY(launch_reduce_stats(pl->P, n, stats, s));
+  const int64_t nblk = bin_partition_blocks(n);
+  const int64_t m = (int64_t)NUM_BINS * nblk;
+  Scratch tmp(s);
+  int64_t* blk;
+  MAG_TRY(tmp.get(&blk, (size_t)(m + 1 + scan_tmp_elems(m) + 1)));
+  CUDA_TRY(launch_bin_partition(pl->bin, n, pl->rows_sorted, stats + 2, blk, nblk, s));
+  int64_t hstats[2 + NUM_BINS + 1];
+  CUDA_TRY(cudaMemcpyAsync(hstats, stats, sizeof(hstats), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  pl->n_interprod = hstats[0];
+  pl->max_P = hstats[1];
+  for (int b = 0; b <= NUM_BINS; ++b) pl->bin_off[b] = hstats[2 + b];
+
+  auto copy_bin = [&](int b, std::vector<int32_t>& rows, std::vector<int64_t>& Pv,
+                      std::vector<int32_t>* lo, std::vector<int32_t>* hi) -> int {
+    const int64_t cnt = pl->bin_off[b + 1] - pl->bin_off[b];
+    rows.resize(cnt);
+    Pv.resize(cnt);
+    if (cnt == 0) return MAGNUS_OK;
+    CUDA_TRY(cudaMemcpyAsync(rows.data(), pl->rows_sorted + pl->bin_off[b], cnt * 4,
+                             cudaMemcpyDeviceToHost, s));
+    int64_t* pg;
+    MAG_TRY(tmp.get(&pg, (size_t)cnt));
+    CUDA_TRY(launch_gather_i64(pl->P, pl->rows_sorted + pl->bin_off[b], cnt, pg, s));
+    CUDA_TRY(cudaMemcpyAsync(Pv.data(), pg, cnt * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (lo && hi) {
+      lo->resize(cnt);
+      hi->resize(cnt);
+      std::vector<int32_t> lo_all(pl->A.n_rows), hi_all(pl->A.n_rows);
+      CUDA_TRY(cudaMemcpyAsync(lo_all.data(), pl->lo, pl->A.n_rows * 4, cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaMemcpyAsync(hi_all.data(), pl->hi, pl->A.n_rows * 4, cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+      for (int64_t i = 0; i < cnt; ++i) {
+        (*lo)[i] = lo_all[rows[i]];
+        (*hi)[i] = hi_all[rows[i]];
+      }
+    }
+    return MAGNUS_OK;
+  };
+
+  // per-category statistics and the dense row count
+  std::vector<int32_t> drows;
+  std::vector<int64_t> dP;
+  MAG_TRY(copy_bin(BIN_DENSE, drows, dP, nullptr, nullptr));
+  MAG_TRY(copy_bin(BIN_FINE, pl->fine_rows, pl->fine_P, &pl->fine_lo, &pl->fine_hi));
+  MAG_TRY(copy_bin(BIN_COARSE, pl->coarse_rows, pl->coarse_P, nullptr, nullptr));
+  for (int b = BIN_SORT32; b <= BIN_SORT256; ++b)
+    pl->rows_cat[MAGNUS_CAT_SORT] += pl->bin_off[b + 1] - pl->bin_off[b];
+  pl->rows_cat[MAGNUS_CAT_DENSE] = (int64_t)drows.size();
+  pl->rows_cat[MAGNUS_CAT_FINE] = (int64_t)pl->fine_rows.size();
+  pl->rows_cat[MAGNUS_CAT_COARSE] = (int64_t)pl->coarse_rows.size();
+  auto sum = [](const std::vector<int64_t>& v) { return std::accumulate(v.begin(), v.end(), (int64_t)0); };
+  pl->prods_cat[MAGNUS_CAT_DENSE] = sum(dP);
+  pl->prods_cat[MAGNUS_CAT_FINE] = sum(pl->fine_P);
+  pl->prods_cat[MAGNUS_CAT_COARSE] = sum(pl->coarse_P);
+  pl->prods_cat[MAGNUS_CAT_SORT] = pl->n_interprod - pl->prods_cat[1] - pl->prods_cat[2] - pl->prods_cat[3];
+
+  // fine rows: heaviest first, batched by staging capacity (12 B/product)
+  if (!pl->fine_rows.empty()) {
+    const size_t nf = pl->fine_rows.size();
+    std::vector<size_t> order(nf);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t a, size_t b) { return pl->fine_P[a] > pl->fine_P[b]; });
+    std::vector<int32_t> r2(nf), l2(nf), h2(nf);
+    std::vector<int64_t> p2(nf);
+    for (size_t i = 0; i < nf; ++i) {
+      r2[i] = pl->fine_rows[order[i]];
+      p2[i] = pl->fine_P[order[i]];
+      l2[i] = pl->fine_lo[order[i]];
+      h2[i] = pl->fine_hi[order[i]];
+    }
+    pl->fine_rows.swap(r2);
+    pl->fine_P.swap(p2);
+    pl->fine_lo.swap(l2);
+    pl->fine_hi.swap(h2);
+    const int64_t cap = std::max<int64_t>(pl->scratch_cap / 12, pl->max_P);
+    pl->fine_batches = make_batches(pl->fine_P, cap, (int64_t)1 << 30);
+    pl->fine_stage_off.resize(nf);
+    for (size_t bi = 0; bi + 1 < pl->fine_batches.size(); ++bi) {
+      int64_t o = 0;
+      for (int64_t i = pl->fine_batches[bi]; i < pl->fine_batches[bi + 1]; ++i) {
+        pl->fine_stage_off[i] = o;
+        o += pl->fine_P[i];
+      }
+    }
+    MAG_TRY(plan_alloc(pl, &pl->fine_rows_d, nf, s));
+    MAG_TRY(plan_alloc(pl, &pl->fine_stage_off_d, nf, s));
+    CUDA_TRY(cudaMemcpyAsync(pl->fine_rows_d, pl->fine_rows.data(), nf * 4, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(pl->fine_stage_off_d, pl->fine_stage_off.data(), nf * 8,
+                             cudaMemcpyHostToDevice, s));
+  }
+  // coarse rows: batched by staging capacity (two 12 B/product buffers) and
+  // by the size of the (row, chunk) bookkeeping
+  if (!pl->coarse_rows.empty()) {
+    const size_t nc = pl->coarse_rows.size();
+    const int64_t cap = std::max<int64_t>(pl->scratch_cap / 24, pl->max_P);
+    const int64_t max_rows = std::max<int64_t>(1, ((int64_t)1 << 28) / pl->n_chunks_coarse);
+    pl->coarse_batches = make_batches(pl->coarse_P, cap, max_rows);
+    MAG_TRY(plan_alloc(pl, &pl->coarse_rows_d, nc, s));
+    CUDA_TRY(cudaMemcpyAsync(pl->coarse_rows_d, pl->coarse_rows.data(), nc * 4,
+                             cudaMemcpyHostToDevice, s));
+    // nnz of A per coarse row, for sizing the CSC buffers
+    std::vector<int64_t> rp(pl->A.n_rows + 1);
+    CUDA_TRY(cudaMemcpyAsync(rp.data(), pl->A.rp, (pl->A.n_rows + 1) * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    pl->coarse_nnz.resize(nc);
+    for (size_t i = 0; i < nc; ++i) pl->coarse_nnz[i] = rp[pl->coarse_rows[i] + 1] - rp[pl->coarse_rows[i]];
+    MAG_TRY(plan_alloc(pl, &pl->bucket_cnt, nc * (size_t)pl->n_chunks_coarse, s));
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return MAGNUS_OK;
+}
+
+int magnus_plan(magnus_plan_t* plan, const magnus_csr_t* A, const magnus_csr_t* B,
+                const magnus_params_t* params, void* stream) {
+  if (!plan) return MAGNUS_INVALID_ARG;
+  *plan = nullptr;
+  MAG_TRY(check_csr(A));
+  MAG_TRY(check_csr(B));
+  if (A->n_cols != B->n_rows) return MAGNUS_INVALID_ARG;
+  if (A->nnz > 0 && B->n_rows == 0) return MAGNUS_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  magnus_plan_t pl = new (std::nothrow) magnus_plan_s();
+  if (!pl) return MAGNUS_OUT_OF_MEMORY;
+  pl->last_stream = s;
+  int st = plan_impl(pl, A, B, params, s);
+  if (st != MAGNUS_OK) {
+    magnus_free(pl);
+    return st;
+  }
+  *plan = pl;
+  return MAGNUS_OK;
+}
+
+// Runs one phase (symbolic or numeric) over every category.
+static int run_phase(magnus_plan_t pl, bool numeric, int64_t* out_cnt, const int64_t* c_rp,
+                     int32_t* c_col, double* c_val, cudaStream_t s) {
+  Scratch scr(s);
+  Csr A = pl->A, B = pl->B;
+  const int st_base = numeric ? MAGNUS_STAGE_NUM_SORT : MAGNUS_STAGE_SYM_SORT;
+  // sort rows
+  {
+    StageTimer tm(pl, st_base + 0, s);
+    for (int b = BIN_SORT32; b <= BIN_SORT256; ++b) {
+      SortArgs a{};
+      a.A = A;
+      a.B = B;
+      a.rows = pl->rows_sorted + pl->bin_off[b];
+      a.n_rows = pl->bin_off[b + 1] - pl->bin_off[b];
+      a.key32 = pl->key32[b];
+      a.out_cnt = out_cnt;
+      a.c_rp = c_rp;
+      a.c_col = c_col;
+      a.c_val = c_val;
+      CUDA_TRY(launch_sort_rows(b, numeric, a, pl->num_sms, s));
+    }
+  }
+  // dense rows
+  {
+    StageTimer tm(pl, st_base + 1, s);
+    DenseArgs a{};
+    a.A = A;
+    a.B = B;
+    a.rows = pl->rows_sorted + pl->bin_off[BIN_DENSE];
+    a.n_rows = pl->bin_off[BIN_DENSE + 1] - pl->bin_off[BIN_DENSE];
+    a.lo = pl->lo;
+    a.hi = pl->hi;
+    a.dense_cols = pl->dense_cols;
+    a.out_cnt = out_cnt;
+    a.c_rp = c_rp;
+    a.c_col = c_col;
+    a.c_val = c_val;
+    CUDA_TRY(launch_dense_rows(numeric, a, pl->num_sms, s));
+  }
+  int64_t staged = 0;
+  // fine rows, batch by batch
+  {
+    StageTimer tm(pl, st_base + 2, s);
+    const int shift = numeric ? pl->shift_fine : pl->shift_fine_sym;
+    const size_t nbat = pl->fine_batches.empty() ? 0 : pl->fine_batches.size() - 1;
+    int32_t* scol = nullptr;
+    double* sval = nullptr;
+    int64_t cap = 0;
+    for (size_t bi = 0; bi < nbat; ++bi) {
+      const int64_t r0 = pl->fine_batches[bi], r1 = pl->fine_batches[bi + 1];
+      int64_t need = 0;
+      for (int64_t i = r0; i < r1; ++i) {
+        const int nch = (pl->fine_hi[i] >> shift) - (pl->fine_lo[i] >> shift) + 1;
+        if (nch > 1) need = std::max(need, pl->fine_stage_off[i] + pl->fine_P[i]);
+      }
+      if (need > cap) {
+        // staging covers the batch's rows that reorder (offsets are per batch)
+        MAG_TRY(scr.get(&scol, (size_t)need));
+        if (numeric) MAG_TRY(scr.get(&sval, (size_t)need));
+        cap = need;
+        pl->scratch_used = std::max<int64_t>(pl->scratch_used, need * (numeric ? 12 : 4));
+      }
+      for (int64_t i = r0; i < r1; ++i) {
+        const int nch = (pl->fine_hi[i] >> shift) - (pl->fine_lo[i] >> shift) + 1;
+        if (nch > 1) staged += pl->fine_P[i];
+      }
+      FineArgs a{};
+      a.A = A;
+      a.B = B;
+      a.rows = pl->fine_rows_d + r0;
+      a.n_rows = r1 - r0;
+      a.stage_off = pl->fine_stage_off_d + r0;
+      a.lo = pl->lo;
+      a.hi = pl->hi;
+      a.shift = shift;
+      a.dense_chunk_threshold = pl->dthr;
+      a.stage_col = scol;
+      a.stage_val = sval;
+      a.out_cnt = out_cnt;
+      a.c_rp = c_rp;
+      a.c_col = c_col;
+      a.c_val = c_val;
+      CUDA_TRY(launch_fine_rows(numeric, a, s));
+    }
+  }
+  // coarse rows, batch by batch
+  {
+    StageTimer tm(pl, st_base + 3, s);
+    const size_t nbat = pl->coarse_batches.empty() ? 0 : pl->coarse_batches.size() - 1;
+    if (nbat > 0) {
+      int64_t maxP = 0, maxNnz = 0, maxRows = 0;
+      for (size_t bi = 0; bi < nbat; ++bi) {
+        int64_t p = 0, z = 0;
+        for (int64_t i = pl->coarse_batches[bi]; i < pl->coarse_batches[bi + 1]; ++i) {
+          p += pl->coarse_P[i];
+          z += pl->coarse_nnz[i];
+        }
+        maxP = std::max(maxP, p);
+        maxNnz = std::max(maxNnz, z);
+        maxRows = std::max(maxRows, pl->coarse_batches[bi + 1] - pl->coarse_batches[bi]);
+      }
+      const int64_t nB = B.n_rows;
+      const int64_t nbk = maxRows * pl->n_chunks_coarse;
+      CoarseArgs a{};
+      a.A = A;
+      a.B = B;
+      a.shift_coarse = pl->shift_coarse;
+      a.n_chunks = pl->n_chunks_coarse;
+      a.shift_fine = pl->shift_fine;
+      a.dense_chunk_threshold = pl->dthr;
+      a.num_sms = pl->num_sms;
+      MAG_TRY(scr.get(&a.col_cnt, (size_t)nB + 1));
+      MAG_TRY(scr.get(&a.col_ptr, (size_t)nB + 1));
+      MAG_TRY(scr.get(&a.csc_row, (size_t)maxNnz));
+      if (numeric) MAG_TRY(scr.get(&a.csc_val, (size_t)maxNnz));
+      MAG_TRY(scr.get(&a.rows_b, (size_t)nB + 1));
+      MAG_TRY(scr.get(&a.n_rows_b, 2));
+      MAG_TRY(scr.get(&a.counts, (size_t)nbk + 1));
+      MAG_TRY(scr.get(&a.cursor, (size_t)nbk));
+      MAG_TRY(scr.get(&a.chunk_col, (size_t)maxP));
+      MAG_TRY(scr.get(&a.fine_col, (size_t)maxP));
+      if (numeric) {
+        MAG_TRY(scr.get(&a.chunk_val, (size_t)maxP));
+        MAG_TRY(scr.get(&a.fine_val, (size_t)maxP));
+        MAG_TRY(scr.get(&a.bucket_out, (size_t)nbk));
+      }
+      MAG_TRY(scr.get(&a.scan_tmp, (size_t)scan_tmp_elems(std::max<int64_t>(nB, nbk)) + 2));
+      MAG_TRY(scr.get(&a.big_list, (size_t)nbk));
+      MAG_TRY(scr.get(&a.n_big, 2));
+      pl->scratch_used = std::max<int64_t>(pl->scratch_used, maxP * (numeric ? 24 : 8));
+      a.bucket_cnt = pl->bucket_cnt;
+      a.out_cnt = out_cnt;
+      a.c_rp = c_rp;
+      a.c_col = c_col;
+      a.c_val = c_val;
+      for (size_t bi = 0; bi < nbat; ++bi) {
+        const int64_t r0 = pl->coarse_batches[bi], r1 = pl->coarse_batches[bi + 1];
+        a.rows = pl->coarse_rows_d + r0;
+        a.n_rows = r1 - r0;
+        a.list_base = r0;
+        int64_t z = 0;
+        for (int64_t i = r0; i < r1; ++i) {
+          z += pl->coarse_nnz[i];
+          staged += pl->coarse_P[i];
+        }
+        a.nnz_batch = z;
+        CUDA_TRY(run_coarse_batch(numeric, a, s));
+      }
+    }
+  }
+  if (numeric) pl->staged_numeric = staged;
+  return MAGNUS_OK;
+}
+
+int magnus_symbolic(magnus_plan_t pl, int64_t* c_row_ptr, int64_t* nnz_c, void* stream) {
+  if (!pl || !c_row_ptr || !nnz_c) return MAGNUS_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  pl->last_stream = s;
+  pl->symbolic_done = false;
+  for (int i = 0; i < MAGNUS_STAGE_COUNT; ++i) pl->ev_used[i] = false;
+  const int64_t n = pl->A.n_rows;
+  CUDA_TRY(cudaMemsetAsync(c_row_ptr, 0, (size_t)(n + 1) * sizeof(int64_t), s));
+  MAG_TRY(run_phase(pl, false, c_row_ptr, nullptr, nullptr, nullptr, s));
+  {
+    StageTimer tm(pl, MAGNUS_STAGE_SYM_SCAN, s);
+    Scratch scr(s);
+    int64_t* tmp;
+    MAG_TRY(scr.get(&tmp, (size_t)scan_tmp_elems(n) + 2));
+    CUDA_TRY(launch_exclusive_scan_i64(c_row_ptr, n, tmp, s));
+  }
+  int64_t h = 0;
+  CUDA_TRY(cudaMemcpyAsync(&h, c_row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  *nnz_c = h;
+  pl->nnz_c = h;
+  pl->symbolic_done = true;
+  return MAGNUS_OK;
+}
+
+int magnus_numeric(magnus_plan_t pl, const double* a_val, const double* b_val,
+                   const int64_t* c_row_ptr, int32_t* c_col, double* c_val, void* stream) {
+  if (!pl || !c_row_ptr) return MAGNUS_INVALID_ARG;
+  if (!pl->symbolic_done) return MAGNUS_NOT_SYMBOLIC;
+  if ((pl->A.nnz > 0 && !a_val) || (pl->B.nnz > 0 && !b_val)) return MAGNUS_INVALID_ARG;
+  if (pl->nnz_c > 0 && (!c_col || !c_val)) return MAGNUS_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  pl->last_stream = s;
+  for (int i = MAGNUS_STAGE_NUM_SORT; i < MAGNUS_STAGE_COUNT; ++i) pl->ev_used[i] = false;
+  pl->A.val = a_val;
+  pl->B.val = b_val;
+  return run_phase(pl, true, nullptr, c_row_ptr, c_col, c_val, s);
+}
+
+int magnus_plan_info(magnus_plan_t pl, magnus_plan_info_t* info) {
+  if (!pl || !info) return MAGNUS_INVALID_ARG;
+  memset(info, 0, sizeof(*info));
+  info->n_rows = pl->A.n_rows;
+  info->n_cols = pl->B.n_cols;
+  info->n_interprod = pl->n_interprod;
+  info->max_row_products = pl->max_P;
+  info->nnz_c = pl->symbolic_done ? pl->nnz_c : -1;
+  info->rows_empty = pl->bin_off[BIN_EMPTY + 1] - pl->bin_off[BIN_EMPTY];
+  for (int c = 0; c < 4; ++c) {
+    info->rows_per_category[c] = pl->rows_cat[c];
+    info->products_per_category[c] = pl->prods_cat[c];
+  }
+  info->staged_products_numeric = pl->staged_numeric;
+  info->scratch_bytes = pl->scratch_used;
+  info->sort_threshold = pl->sort_T;
+  info->chunk_len_fine_log2 = pl->shift_fine;
+  info->chunk_len_fine_sym_log2 = pl->shift_fine_sym;
+  info->chunk_len_coarse_log2 = pl->shift_coarse;
+  info->n_chunks_coarse = pl->n_chunks_coarse;
+  info->dense_cols = pl->dense_cols;
+  info->dense_chunk_threshold = pl->dthr;
+  info->key_bits32 = pl->key32[BIN_SORT256];
+  info->n_batches_fine = pl->fine_batches.empty() ? 0 : (int)pl->fine_batches.size() - 1;
+  info->n_batches_coarse = pl->coarse_batches.empty() ? 0 : (int)pl->coarse_batches.size() - 1;
+  return MAGNUS_OK;
+}
+
+int magnus_enable_timing(magnus_plan_t pl, int enable) {
+  if (!pl) return MAGNUS_INVALID_ARG;
+  if (enable && !pl->ev[0]) {
+    for (int i = 0; i < 2 * MAGNUS_STAGE_COUNT; ++i) CUDA_TRY(cudaEventCreate(&pl->ev[i]));
+  }
+  pl->timing = enable != 0;
+  return MAGNUS_OK;
+}
+
+int magnus_stage_times(magnus_plan_t pl, double* ms, int n) {
+  if (!pl || !ms || n < 0) return MAGNUS_INVALID_ARG;
+  for (int i = 0; i < n && i < MAGNUS_STAGE_COUNT; ++i) {
+    ms[i] = 0.0;
+    if (pl->timing && pl->ev_used[i]) {
+      CUDA_TRY(cudaEventSynchronize(pl->ev[2 * i + 1]));
+      float f = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&f, pl->ev[2 * i], pl->ev[2 * i + 1]));
+      ms[i] = f;
+    }
+  }
+  return MAGNUS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,284 @@
+"""Thin ctypes binding of libmagnus.so (C ABI in include/magnus.h).
+
+Only argument marshalling lives here; every step of the SpGEMM runs in the
+library's CUDA kernels.  Device memory and streams come from PyTorch.  The
+library is loaded on first use; if it is missing the call raises (there is no
+CPU fallback).
+
+Functions with the C names (``magnus_plan``, ``magnus_symbolic``,
+``magnus_numeric``, ``magnus_free`` ...) mirror the ABI one to one.
+``spgemm`` is the convenience call a user makes: it plans, runs the symbolic
+phase, allocates C with PyTorch and runs the numeric phase.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmagnus.so")
+
+c_i32, c_i64, c_p, c_u64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_uint64
+
+CAT_AUTO, CAT_SORT, CAT_DENSE, CAT_FINE, CAT_COARSE = -1, 0, 1, 2, 3
+STAGES = ["sym_sort", "sym_dense", "sym_fine", "sym_coarse", "sym_scan",
+          "num_sort", "num_dense", "num_fine", "num_coarse"]
+
+
+class CsrDesc(ctypes.Structure):
+    _fields_ = [("n_rows", c_i64), ("n_cols", c_i64), ("nnz", c_i64),
+                ("row_ptr", c_p), ("col", c_p), ("val", c_p)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("sort_threshold", c_i32), ("force_category", c_i32),
+                ("chunk_len_fine_log2", c_i32), ("chunk_len_coarse_log2", c_i32),
+                ("dense_chunk_threshold", c_i32), ("validate", c_i32),
+                ("max_scratch_bytes", c_i64)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n_rows", c_i64), ("n_cols", c_i64), ("n_interprod", c_i64),
+                ("max_row_products", c_i64), ("nnz_c", c_i64), ("rows_empty", c_i64),
+                ("rows_per_category", c_i64 * 4), ("products_per_category", c_i64 * 4),
+                ("staged_products_numeric", c_i64), ("scratch_bytes", c_i64),
+                ("sort_threshold", c_i32), ("chunk_len_fine_log2", c_i32),
+                ("chunk_len_fine_sym_log2", c_i32), ("chunk_len_coarse_log2", c_i32),
+                ("n_chunks_coarse", c_i32), ("dense_cols", c_i32),
+                ("dense_chunk_threshold", c_i32), ("key_bits32", c_i32),
+                ("n_batches_fine", c_i32), ("n_batches_coarse", c_i32)]
+
+    def as_dict(self):
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = list(v) if hasattr(v, "__len__") else v
+        return d
+
+
+class ChunkModel(ctypes.Structure):
+    _fields_ = [("m_c_log2", c_i32), ("chunk_len_fine_log2", c_i32),
+                ("chunk_len_fine_sym_log2", c_i32), ("n_chunks_fine_max_log2", c_i32),
+                ("m_c_max_log2", c_i32), ("n_chunks_coarse", c_i32),
+                ("fine_smem_bytes", c_i64)]
+
+
+class MagnusError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        msg = "%s: %s" % (where, _lib().magnus_strerror(status).decode())
+        if status == 5:
+            msg += " (%s)" % _lib().magnus_last_cuda_error().decode()
+        super().__init__(msg)
+
+
+_LIB = None
+
+# Exported symbols and their signatures (restype, argtypes).
+SIGNATURES = {
+    "magnus_params_default": (c_i32, [ctypes.POINTER(Params)]),
+    "magnus_plan": (c_i32, [ctypes.POINTER(c_p), ctypes.POINTER(CsrDesc), ctypes.POINTER(CsrDesc),
+                            ctypes.POINTER(Params), c_p]),
+    "magnus_symbolic": (c_i32, [c_p, c_p, ctypes.POINTER(c_i64), c_p]),
+    "magnus_numeric": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_p, c_p]),
+    "magnus_free": (None, [c_p]),
+    "magnus_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "magnus_last_cuda_error": (ctypes.c_char_p, []),
+    "magnus_plan_info": (c_i32, [c_p, ctypes.POINTER(PlanInfo)]),
+    "magnus_enable_timing": (c_i32, [c_p, ctypes.c_int]),
+    "magnus_stage_times": (c_i32, [c_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    "magnus_launch_count": (c_u64, []),
+    "magnus_chunk_model": (c_i32, [c_i64, c_i64, c_i64, c_i32, ctypes.POINTER(ChunkModel)]),
+}
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libmagnus.so is not built (run __graft_entry__.build()); "
+                               "there is no CPU fallback")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def _check(st, where):
+    if st != 0:
+        raise MagnusError(st, where)
+
+
+# ---------------------------------------------------------------------------
+# One-to-one wrappers of the C entry points.
+
+def magnus_params_default() -> Params:
+    p = Params()
+    _check(_lib().magnus_params_default(ctypes.byref(p)), "magnus_params_default")
+    return p
+
+
+def magnus_plan(A: CsrDesc, B: CsrDesc, params: Params | None, stream: int) -> int:
+    h = c_p()
+    _check(_lib().magnus_plan(ctypes.byref(h), ctypes.byref(A), ctypes.byref(B),
+                              ctypes.byref(params) if params is not None else None,
+                              c_p(stream)), "magnus_plan")
+    return h.value
+
+
+def magnus_symbolic(plan: int, c_row_ptr: int, stream: int) -> int:
+    nnz = c_i64()
+    _check(_lib().magnus_symbolic(c_p(plan), c_p(c_row_ptr), ctypes.byref(nnz), c_p(stream)),
+           "magnus_symbolic")
+    return nnz.value
+
+
+def magnus_numeric(plan: int, a_val: int, b_val: int, c_row_ptr: int, c_col: int, c_val: int,
+                   stream: int) -> None:
+    _check(_lib().magnus_numeric(c_p(plan), c_p(a_val), c_p(b_val), c_p(c_row_ptr), c_p(c_col),
+                                 c_p(c_val), c_p(stream)), "magnus_numeric")
+
+
+def magnus_free(plan: int) -> None:
+    if plan:
+        _lib().magnus_free(c_p(plan))
+
+
+def magnus_plan_info(plan: int) -> dict:
+    info = PlanInfo()
+    _check(_lib().magnus_plan_info(c_p(plan), ctypes.byref(info)), "magnus_plan_info")
+    return info.as_dict()
+
+
+def magnus_enable_timing(plan: int, enable: bool = True) -> None:
+    _check(_lib().magnus_enable_timing(c_p(plan), int(enable)), "magnus_enable_timing")
+
+
+def magnus_stage_times(plan: int) -> dict:
+    arr = (ctypes.c_double * len(STAGES))()
+    _check(_lib().magnus_stage_times(c_p(plan), arr, len(STAGES)), "magnus_stage_times")
+    return dict(zip(STAGES, list(arr)))
+
+
+def magnus_launch_count() -> int:
+    return int(_lib().magnus_launch_count())
+
+
+def magnus_chunk_model(m_c: int, smem_bytes: int, l2_bytes: int, resident_blocks: int) -> dict:
+    out = ChunkModel()
+    _check(_lib().magnus_chunk_model(m_c, smem_bytes, l2_bytes, resident_blocks,
+                                     ctypes.byref(out)), "magnus_chunk_model")
+    return {name: getattr(out, name) for name, _ in out._fields_}
+
+
+# ---------------------------------------------------------------------------
+# PyTorch-facing convenience layer.
+
+@dataclasses.dataclass
+class DeviceCSR:
+    """CSR on the GPU: int64 row_ptr, int32 col, float64 val (torch tensors)."""
+    n_rows: int
+    n_cols: int
+    row_ptr: "torch.Tensor"
+    col: "torch.Tensor"
+    val: "torch.Tensor"
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.numel())
+
+    def desc(self, with_val: bool = True) -> CsrDesc:
+        return CsrDesc(self.n_rows, self.n_cols, self.nnz, self.row_ptr.data_ptr(),
+                       self.col.data_ptr() if self.nnz else 0,
+                       self.val.data_ptr() if (with_val and self.nnz) else 0)
+
+    @staticmethod
+    def from_host(M, device="cuda", non_blocking=False) -> "DeviceCSR":
+        import torch
+        return DeviceCSR(M.n_rows, M.n_cols,
+                         torch.as_tensor(M.row_ptr).to(device, non_blocking=non_blocking),
+                         torch.as_tensor(M.col).to(device, non_blocking=non_blocking),
+                         torch.as_tensor(M.val).to(device, non_blocking=non_blocking))
+
+
+def make_params(sort_threshold=0, force_category=CAT_AUTO, chunk_len_fine_log2=0,
+                chunk_len_coarse_log2=0, dense_chunk_threshold=0, validate=0,
+                max_scratch_bytes=0) -> Params:
+    p = magnus_params_default()
+    p.sort_threshold = sort_threshold
+    p.force_category = force_category
+    p.chunk_len_fine_log2 = chunk_len_fine_log2
+    p.chunk_len_coarse_log2 = chunk_len_coarse_log2
+    p.dense_chunk_threshold = dense_chunk_threshold
+    p.validate = validate
+    p.max_scratch_bytes = max_scratch_bytes
+    return p
+
+
+class Plan:
+    """Owns a magnus plan for fixed A and B structures (values may change)."""
+
+    def __init__(self, A: DeviceCSR, B: DeviceCSR, params: Params | None = None, stream=None):
+        import torch
+        self.A, self.B = A, B
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = magnus_plan(A.desc(False), B.desc(False), params, self.stream.cuda_stream)
+        self.c_row_ptr = None
+        self.nnz_c = None
+
+    def symbolic(self, c_row_ptr=None) -> int:
+        import torch
+        if c_row_ptr is None:
+            c_row_ptr = torch.empty(self.A.n_rows + 1, dtype=torch.int64, device=self.A.row_ptr.device)
+        self.c_row_ptr = c_row_ptr
+        self.nnz_c = magnus_symbolic(self.handle, c_row_ptr.data_ptr(), self.stream.cuda_stream)
+        return self.nnz_c
+
+    def numeric(self, c_col=None, c_val=None, a_val=None, b_val=None):
+        import torch
+        dev = self.A.row_ptr.device
+        if c_col is None:
+            c_col = torch.empty(max(self.nnz_c, 1), dtype=torch.int32, device=dev)
+        if c_val is None:
+            c_val = torch.empty(max(self.nnz_c, 1), dtype=torch.float64, device=dev)
+        av = self.A.val if a_val is None else a_val
+        bv = self.B.val if b_val is None else b_val
+        magnus_numeric(self.handle, av.data_ptr() if av.numel() else 0,
+                       bv.data_ptr() if bv.numel() else 0, self.c_row_ptr.data_ptr(),
+                       c_col.data_ptr(), c_val.data_ptr(), self.stream.cuda_stream)
+        return c_col[:self.nnz_c], c_val[:self.nnz_c]
+
+    def info(self) -> dict:
+        return magnus_plan_info(self.handle)
+
+    def enable_timing(self, on=True):
+        magnus_enable_timing(self.handle, on)
+
+    def stage_times(self) -> dict:
+        return magnus_stage_times(self.handle)
+
+    def free(self):
+        if self.handle:
+            magnus_free(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def spgemm(A: DeviceCSR, B: DeviceCSR, params: Params | None = None, stream=None) -> DeviceCSR:
+    """C = A * B on the GPU (plan, symbolic, allocate, numeric)."""
+    plan = Plan(A, B, params, stream)
+    try:
+        plan.symbolic()
+        col, val = plan.numeric()
+        return DeviceCSR(A.n_rows, B.n_cols, plan.c_row_ptr, col, val)
+    finally:
+        plan.free()

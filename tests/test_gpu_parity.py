@@ -1,0 +1,198 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Structure (row pointers, column indices) must match bit-exactly; values must
+satisfy |c - c_ref| <= 1e-12 * max(|c_ref|, sum of |terms|).  Every
+category (sort, dense, fine, coarse) is exercised both where the setup picks
+it and where it is forced, on inputs spanning several tiles and ragged tails.
+"""
+import numpy as np
+import pytest
+
+from paper_2501_07056_gb300 import inputs
+from tests._gpu import assert_parity, run_gpu
+from tests._util import random_pattern_csr
+
+pytestmark = pytest.mark.gpu
+
+SORT, DENSE, FINE, COARSE = 0, 1, 2, 3
+
+
+def P(**kw):
+    from paper_2501_07056_gb300 import magnus
+    return magnus.make_params(**kw)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def test_uniform4096_auto():
+    A, B = inputs.workload("uniform4096")
+    got = run_gpu(A, B, same=True)
+    assert_parity(got, A, B)
+    info = got["info"]
+    assert info["n_interprod"] == 4096 * 64
+    assert info["rows_per_category"][SORT] == 4096
+
+
+@pytest.mark.parametrize("force,extra", [
+    (SORT, {}), (DENSE, {}), (FINE, {}), (FINE, dict(chunk_len_fine_log2=6)),
+    (COARSE, {}), (COARSE, dict(chunk_len_coarse_log2=10)),
+    (COARSE, dict(chunk_len_coarse_log2=8, chunk_len_fine_log2=5)),
+])
+def test_uniform4096_forced(force, extra):
+    A, B = inputs.workload("uniform4096")
+    got = run_gpu(A, B, P(force_category=force, validate=1, **extra), same=True)
+    assert_parity(got, A, B)
+    cats = got["info"]["rows_per_category"]
+    if force == DENSE:
+        assert cats[DENSE] == 4096
+    elif force != SORT:
+        assert cats[force] == 4096
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+@pytest.mark.parametrize("T", [0, 16, 100])
+def test_ragged_mixed_categories(seed, T):
+    A = inputs.ragged(3000, 20000, 0, 60, seed=seed, matrix_id=1)
+    B = inputs.ragged(20000, 70000, 0, 120, seed=seed, matrix_id=2)
+    got = run_gpu(A, B, P(sort_threshold=T, validate=1))
+    assert_parity(got, A, B)
+
+
+@pytest.mark.parametrize("force", [-1, SORT, DENSE, FINE, COARSE])
+def test_rmat_small(force):
+    A = inputs.rmat(13, 16, seed=0)
+    got = run_gpu(A, A, P(force_category=force, chunk_len_coarse_log2=10 if force == COARSE else 0),
+                  same=True)
+    assert_parity(got, A, A)
+
+
+@pytest.mark.parametrize("dthr", [1, 8, 1024])
+@pytest.mark.parametrize("force", [FINE, COARSE])
+def test_hybrid_threshold_extremes(dthr, force):
+    A = inputs.rmat(12, 16, seed=1)
+    got = run_gpu(A, A, P(force_category=force, dense_chunk_threshold=dthr,
+                          chunk_len_fine_log2=7, chunk_len_coarse_log2=9), same=True)
+    assert_parity(got, A, A)
+
+
+@pytest.mark.parametrize("force", [FINE, COARSE])
+def test_multiple_batches(force):
+    A = inputs.ragged(2000, 5000, 20, 60, seed=3, matrix_id=1)
+    B = inputs.ragged(5000, 30000, 10, 50, seed=3, matrix_id=2)
+    got = run_gpu(A, B, P(force_category=force, max_scratch_bytes=1 << 20,
+                          chunk_len_coarse_log2=12))
+    assert_parity(got, A, B)
+    info = got["info"]
+    nb = info["n_batches_fine"] if force == FINE else info["n_batches_coarse"]
+    assert nb > 1
+
+
+def _csr(n_rows, n_cols, rows_cols, vals=None):
+    lengths = np.array([len(r) for r in rows_cols], np.int64)
+    rp = np.concatenate(([0], np.cumsum(lengths))).astype(np.int64)
+    col = np.array([c for r in rows_cols for c in r], np.int32)
+    val = np.array(vals if vals is not None else np.linspace(-1, 1, col.size) + 0.5, np.float64)
+    return inputs.CSR(n_rows, n_cols, rp, col, val)
+
+
+@pytest.mark.parametrize("force", [-1, SORT, DENSE, FINE, COARSE])
+def test_edge_cases(force):
+    p = P(force_category=force)
+    # all products of a row land in one column (maximal duplication)
+    A = inputs.ragged(300, 400, 1, 200, seed=5, matrix_id=1)
+    B1 = _csr(400, 7, [[3]] * 400, np.random.default_rng(0).uniform(-1, 1, 400))
+    assert_parity(run_gpu(A, B1, p), A, B1)
+    # single column of C
+    B2 = _csr(400, 1, [[0]] * 400, np.random.default_rng(1).uniform(-1, 1, 400))
+    assert_parity(run_gpu(A, B2, p), A, B2)
+    # empty rows in A and in B, nonsquare, ragged
+    rng = np.random.default_rng(2)
+    A3 = random_pattern_csr(rng, 97, 131, 0.05)
+    B3 = random_pattern_csr(rng, 131, 3001, 0.02)
+    assert_parity(run_gpu(A3, B3, p), A3, B3)
+    # 1x1
+    A4 = _csr(1, 1, [[0]], [2.5])
+    assert_parity(run_gpu(A4, A4, p), A4, A4)
+
+
+def test_empty_matrices():
+    Z = inputs.CSR(5, 6, np.zeros(6, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    B = inputs.uniform(6, 9, 2, seed=1)
+    got = run_gpu(Z, B)
+    assert got["nnz"] == 0 and got["row_ptr"].tolist() == [0] * 6
+    E = inputs.CSR(0, 6, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    got = run_gpu(E, B)
+    assert got["nnz"] == 0 and got["row_ptr"].tolist() == [0]
+    A = inputs.uniform(5, 6, 3, seed=2)
+    Bz = inputs.CSR(6, 9, np.zeros(7, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    got = run_gpu(A, Bz)
+    assert got["nnz"] == 0
+
+
+@pytest.mark.parametrize("force", [-1, DENSE, FINE, COARSE])
+def test_wide_columns_64bit_keys(force):
+    # columns near 2^31 force 64-bit sort keys and many coarse chunks
+    n_cols = (1 << 31) - 1
+    rng = np.random.default_rng(4)
+    A = inputs.ragged(500, 800, 1, 40, seed=4, matrix_id=1)
+    rows = []
+    for _ in range(800):
+        k = int(rng.integers(0, 30))
+        rows.append(sorted(set(rng.integers(n_cols - (1 << 20), n_cols, size=k).tolist()) |
+                           set(rng.integers(0, 1 << 20, size=3).tolist())))
+    B = _csr(800, n_cols, rows, rng.uniform(-1, 1, sum(len(r) for r in rows)))
+    got = run_gpu(A, B, P(force_category=force))
+    assert_parity(got, A, B)
+
+
+def test_plan_reuse_new_values():
+    import torch
+    A = inputs.rmat(12, 16, seed=3)
+    got = run_gpu(A, A, same=True, keep_plan=True)
+    assert_parity(got, A, A)
+    plan, (dA, _) = got["plan"], got["dev"]
+    A2 = inputs.CSR(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val * -3.0 + 0.25)
+    v2 = torch.as_tensor(A2.val).cuda()
+    col, val = plan.numeric(a_val=v2, b_val=v2)
+    torch.cuda.synchronize()
+    got2 = dict(row_ptr=got["row_ptr"], col=col.cpu().numpy(), val=val.cpu().numpy())
+    assert_parity(got2, A2, A2)
+    plan.free()
+
+
+def test_validate_rejects_unsorted():
+    from paper_2501_07056_gb300 import magnus
+    A = _csr(2, 4, [[2, 1], [0]], [1.0, 2.0, 3.0])
+    B = inputs.uniform(4, 4, 2, seed=0)
+    with pytest.raises(magnus.MagnusError) as ei:
+        run_gpu(A, B, P(validate=1))
+    assert ei.value.status == 2
+    Aout = _csr(2, 4, [[0, 7], [1]], [1.0, 2.0, 3.0])
+    with pytest.raises(magnus.MagnusError):
+        run_gpu(Aout, B, P(validate=1))
+
+
+def test_numeric_before_symbolic():
+    import torch
+    from paper_2501_07056_gb300 import magnus
+    A = inputs.uniform(64, 64, 4, seed=0)
+    dA = magnus.DeviceCSR.from_host(A)
+    plan = magnus.Plan(dA, dA)
+    c = torch.zeros(10, dtype=torch.int64, device="cuda")
+    with pytest.raises(magnus.MagnusError) as ei:
+        magnus.magnus_numeric(plan.handle, dA.val.data_ptr(), dA.val.data_ptr(), c.data_ptr(),
+                              c.data_ptr(), c.data_ptr(), 0)
+    assert ei.value.status == 7
+    plan.free()
+
+
+def test_launch_counter_advances():
+    from paper_2501_07056_gb300 import magnus
+    A, B = inputs.workload("uniform4096")
+    n0 = magnus.magnus_launch_count()
+    run_gpu(A, B, same=True)
+    assert magnus.magnus_launch_count() > n0
