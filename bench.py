@@ -1,0 +1,456 @@
+#!/usr/bin/env python
+"""Benchmark of the MAGNUS SpGEMM hot path on GB300.
+
+Workload (one step = the whole hot path on one product): C = A*A with A a
+uniform random square matrix, n = 2^24, exactly 8 distinct uniform columns per
+row, FP64 values U(-1, 1), seed 0 (1.07e9 intermediate products).  A step is
+plan (setup, Section 3.1) + symbolic (Section 2.1) + allocation of C +
+numeric (Algorithms 1-4), timed with CUDA events on the calling stream.  The
+inputs (1.6 GB) are larger than the 126 MB L2, so no flush is needed between
+steps.
+
+Output: one JSON line (rank 0).  ``value`` is whole-job GFLOP/s
+(2 x intermediate products / s, Section 5 definition of n_interProd), ``e2e``
+the same metric through the public API with host buffers (H2D of A and D2H of
+C inside the timed region), ``roofline`` the dominant kernel's algorithmic
+bytes per launch over its measured duration against the measured HBM copy
+bandwidth, ``cpu_baseline`` the CPU oracle on a bounded row sample.
+
+``--impl reference`` times the CPU oracle instead (the reference arm): each
+step is the oracle on a bounded sample of the same workload on all host cores.
+
+Multi-GPU: rows of C are independent, but every product here fits one GPU,
+so N GPUs run N replicas of the workload (weak scaling); ranks synchronise
+with a barrier and the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "uniform2^24": "C=A*A, A uniform random square n=2^24, 8 distinct uniform cols/row, "
+                   "FP64 U(-1,1), int32 cols, seed 0",
+    "uniform2^22": "C=A*A, A uniform random square n=2^22, 8 distinct uniform cols/row, "
+                   "FP64 U(-1,1), int32 cols, seed 0",
+    "uniform4096": "C=A*A, A uniform random square n=4096, 8 distinct uniform cols/row, "
+                   "FP64 U(-1,1), int32 cols, seed 0",
+    "rmat20": "C=A*A, A R-MAT scale 20, edge factor 16, (a,b,c)=(.57,.19,.19), "
+              "duplicates merged, FP64 U(0,1), seed 0",
+}
+CPU_SAMPLE_ROWS = 1 << 21
+REF_STEP_ROWS = 1 << 18
+PROFILE_DIR = os.path.join(ROOT, "profiles")
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="uniform2^24", choices=sorted(WORKLOADS))
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--force-category", type=int, default=-1)
+    p.add_argument("--sort-threshold", type=int, default=0)
+    p.add_argument("--l2-fetch", type=int, default=0,
+                   help="L2 fetch granularity hint in bytes (0 = leave the setting alone)")
+    return p.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+# multi-rank plumbing (torchrun: one process per GPU)
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if backend == "nccl":
+                torch.cuda.set_device(self.local_rank)
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg is not None:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        return self._reduce(x, "max")
+
+    def sum(self, x: float) -> float:
+        return self._reduce(x, "sum")
+
+    def _reduce(self, x, op):
+        if self.pg is None:
+            return float(x)
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX if op == "max" else self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg is not None:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[2]), smax=float(parts[3]),
+                                 power=float(parts[4]) if parts[4] not in ("[N/A]", "N/A") else None,
+                                 hw=parts[6], hwt=parts[7], swt=parts[8], swp=parts[9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        pw = [r["power"] for r in rows if r["power"] is not None]
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows),
+                "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(pw) if pw else None}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+
+def peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def csrc_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2501_07056_gb300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, fn), "rb") as f:
+                h.update(fn.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_tag: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(PROFILE_DIR, "%s_%s.md" % (kernel_tag, workload.replace("^", "")))
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("csrc_sha256") != csrc_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def numeric_sort_alg_bytes(n_rows, nnz_a, n_inter, nnz_c):
+    """Algorithmic bytes of the numeric sort-row kernel (Eq. 8-9 split by
+    phase): A.rowPtr and C.rowPtr (8 B per row each), A.col + A.val (12 B)
+    and the begin/end B.rowPtr of its B row (16 B) per nonzero of A, B.col +
+    B.val per intermediate product (12 B), C.col + C.val per nonzero of C
+    (12 B)."""
+    return 16 * (n_rows + 1) + 28 * nnz_a + 12 * n_inter + 12 * nnz_c
+
+
+def ideal_bytes(n_rows, nnz_a, n_inter, nnz_c):
+    """Eq. 8 + Eq. 9 with s_rowPtr = 8, s_colIdx = 4, s_val = 8."""
+    read = 2 * (n_rows + 1) * 8 + nnz_a * (4 * 8 + 2 * 4 + 8) + n_inter * (2 * 4 + 8)
+    write = (n_rows + 1) * 8 + nnz_c * (4 + 8)
+    return read + write
+
+
+def workload_config(args, A, dist):
+    lens = np.diff(A.row_ptr)
+    return {"workload": WORKLOADS[args.workload], "n": A.n_rows, "nnz_a": A.nnz,
+            "n_interprod": int(lens[A.col].sum()),
+            "parallelism": "replicas" if dist.world > 1 else "single",
+            "l2": "inputs larger than L2 (A and B exceed the 126 MB L2), no flush",
+            "step": "plan+symbolic+alloc C+numeric"}
+
+
+# ---------------------------------------------------------------------------
+
+def cpu_oracle_rate(A, rows, threads):
+    import oracle
+    rp = A.row_ptr
+    lens = np.diff(rp)
+    prods = int(lens[A.col[rp[rows[0]]:rp[rows[-1] + 1]]].sum())
+    t0 = time.perf_counter()
+    oracle.spgemm(A, A, rows=rows, threads=threads)
+    dt = time.perf_counter() - t0
+    return 2.0 * prods / dt / 1e9, prods, dt
+
+
+def run_reference(args, dist):
+    """Reference arm: the CPU oracle as it stands on all host cores, each step
+    a bounded row sample of the workload."""
+    from paper_2501_07056_gb300 import inputs
+    if dist.rank != 0:
+        return None
+    A, _ = inputs.workload(args.workload)
+    threads = os.cpu_count() or 1
+    n = min(A.n_rows, REF_STEP_ROWS)
+    rows = np.arange(n, dtype=np.int64)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(A, rows, threads)
+    rates, total_prods, total_t = [], 0, 0.0
+    for _ in range(args.steps):
+        r, prods, dt = cpu_oracle_rate(A, rows, threads)
+        rates.append(r)
+        total_prods += prods
+        total_t += dt
+    value = 2.0 * total_prods / total_t / 1e9
+    sample = "rows 0..%d of the workload (%d products per step), C rows via Eq. 1" % (n - 1, total_prods // args.steps)
+    return {
+        "impl": "reference", "metric": "SpGEMM GFLOP/s", "value": value, "unit": "GFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args, A, dist),
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def run_ours(args, dist):
+    import torch
+
+    from paper_2501_07056_gb300 import inputs, magnus
+
+    dev = torch.device("cuda", dist.local_rank if dist.world > 1 else 0)
+    torch.cuda.set_device(dev)
+    magnus._lib()  # fail loudly if the library is missing
+    A, _ = inputs.workload(args.workload)
+    dA = magnus.DeviceCSR.from_host(A, dev)
+    torch.cuda.synchronize()
+    params = magnus.make_params(force_category=args.force_category,
+                                sort_threshold=args.sort_threshold,
+                                l2_fetch_bytes=args.l2_fetch)
+    stream = torch.cuda.current_stream()
+
+    def step(keep):
+        plan = magnus.Plan(dA, dA, params, stream)
+        plan.enable_timing(True)
+        plan.symbolic()
+        c_col, c_val = plan.numeric()
+        keep.append(plan)
+        return plan, c_col, c_val
+
+    # warm-up (also gives the sizes)
+    keep = []
+    for _ in range(args.warmup):
+        plan, c_col, c_val = step(keep)
+    info = plan.info()
+    nnz_c = info["nnz_c"]
+    n_inter = info["n_interprod"]
+    for p in keep:
+        p.free()
+    del c_col, c_val
+    keep = []
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(dev.index).start()
+    dist.barrier()
+    torch.cuda.synchronize()
+    n_launch0 = magnus.magnus_launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        _, c_col, c_val = step(keep)
+        del c_col, c_val
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    n_launch = magnus.magnus_launch_count() - n_launch0
+    clk = clocks.stop()
+    ms_local = ev0.elapsed_time(ev1)
+    stage = {k: [] for k in magnus.STAGES}
+    for p in keep:
+        for k, v in p.stage_times().items():
+            stage[k].append(v)
+        p.free()
+    keep = []
+    ms_max = dist.max(ms_local)
+    total_units = dist.sum(2.0 * n_inter * args.steps)
+    value = total_units / (ms_max * 1e-3) / 1e9
+    stage_ms = {k: (sum(v) / len(v) if v else 0.0) for k, v in stage.items()}
+
+    # roofline of the dominant kernel: the numeric sort-row kernel
+    peak, peak_kind = peak_hbm()
+    kern_ms = stage_ms["num_sort"]
+    alg = numeric_sort_alg_bytes(A.n_rows, A.nnz, n_inter, nnz_c)
+    achieved = alg / (kern_ms * 1e-3) / 1e9 if kern_ms > 0 else 0.0
+    traffic = profiled_traffic("sort_rows_numeric", args.workload)
+    t_ideal_ms = ideal_bytes(A.n_rows, A.nnz, n_inter, nnz_c) / (peak * 1e9) * 1e3
+
+    result = {
+        "metric": "SpGEMM GFLOP/s", "value": value, "unit": "GFLOP/s", "n_gpus": dist.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": workload_config(args, A, dist),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_sort_rows numeric",
+                     "alg_bytes_per_launch": alg, "kernel_ms": kern_ms,
+                     "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
+                     if peak_kind == "measured" else "fallback 6.8 TB/s"},
+        "clocks": clk,
+        "gpu_launches": n_launch,
+        "detail": {"nnz_c": nnz_c, "stage_ms": stage_ms, "t_over_t_ideal": (ms_max / args.steps) / t_ideal_ms,
+                   "t_ideal_ms": t_ideal_ms, "rows_per_category": info["rows_per_category"],
+                   "sort_threshold": info["sort_threshold"]},
+    }
+    if not args.no_e2e:
+        result["e2e"] = run_e2e(args, dist, A, dev, params, n_inter, nnz_c)
+    if not args.no_cpu and dist.rank == 0:
+        threads = os.cpu_count() or 1
+        n = min(A.n_rows, CPU_SAMPLE_ROWS)
+        rate, prods, dt = cpu_oracle_rate(A, np.arange(n, dtype=np.int64), threads)
+        result["cpu_baseline"] = {
+            "value": rate, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+            "sample": "rows 0..%d of the workload (%d products, %.1f s wall)" % (n - 1, prods, dt)}
+    return result
+
+
+def run_e2e(args, dist, A, dev, params, n_inter, nnz_c):
+    """Same metric through the public API with host buffers: every step
+    copies A from pinned host memory to the device, computes C and copies C
+    (row_ptr, col, val) back to pinned host memory."""
+    import torch
+
+    from paper_2501_07056_gb300 import magnus
+    h_rp = torch.from_numpy(A.row_ptr).pin_memory()
+    h_col = torch.from_numpy(A.col).pin_memory()
+    h_val = torch.from_numpy(A.val).pin_memory()
+    o_rp = torch.empty(A.n_rows + 1, dtype=torch.int64).pin_memory()
+    o_col = torch.empty(nnz_c, dtype=torch.int32).pin_memory()
+    o_val = torch.empty(nnz_c, dtype=torch.float64).pin_memory()
+    stream = torch.cuda.current_stream()
+    h2d = h_rp.numel() * 8 + h_col.numel() * 4 + h_val.numel() * 8
+    d2h = o_rp.numel() * 8 + o_col.numel() * 4 + o_val.numel() * 8
+
+    def step():
+        d = magnus.DeviceCSR(A.n_rows, A.n_cols, h_rp.to(dev, non_blocking=True),
+                             h_col.to(dev, non_blocking=True), h_val.to(dev, non_blocking=True))
+        C = magnus.spgemm(d, d, params, stream)
+        o_rp.copy_(C.row_ptr, non_blocking=True)
+        o_col.copy_(C.col, non_blocking=True)
+        o_val.copy_(C.val, non_blocking=True)
+        torch.cuda.synchronize()
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    steps = max(1, min(args.steps, 10))
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    dist.barrier()
+    dt_max = dist.max(dt)
+    units = dist.sum(2.0 * n_inter * steps)
+    return {"value": units / dt_max / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": steps, "ms_per_step": 1e3 * dt_max / steps}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    dist = Dist()
+    try:
+        if args.impl == "reference":
+            res = run_reference(args, dist)
+        else:
+            res = run_ours(args, dist)
+        if dist.rank == 0 and res is not None:
+            print(json.dumps(res), flush=True)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -81,7 +81,8 @@ typedef struct {
  * re-derived for shared memory and L2; see magnus_chunk_model).
  *
  * sort_threshold      rows with P_i < sort_threshold use the sort accumulator
- *                     (Section 3.1, category 1).  Range 1..257; 0 = 257.
+ *                     (Section 3.1, category 1).  Range 1..257; 0 = 256
+ *                     (the threshold of Section 4.1.1).
  * force_category      -1 = automatic; otherwise every non-empty row is put in
  *                     that category (used to exercise each stage).
  * chunk_len_fine_log2 log2 of the fine chunk length (columns) for the numeric
@@ -96,7 +97,11 @@ typedef struct {
  *                     magnus_plan (returns MAGNUS_UNSORTED_OR_DUP on failure).
  * max_scratch_bytes   upper bound on the reorder staging buffer of one batch
  *                     (Section 3.3 batching); 0 = automatic (a fraction of
- *                     the free device memory at plan time).                 */
+ *                     the free device memory at plan time).
+ * l2_fetch_bytes      L2 fetch granularity hint (cudaLimitMaxL2FetchGranularity)
+ *                     applied while magnus_symbolic / magnus_numeric enqueue
+ *                     work and restored before they return (32, 64 or 128);
+ *                     0 = leave the process setting alone.                   */
 typedef struct {
   int32_t sort_threshold;
   int32_t force_category;
@@ -105,6 +110,8 @@ typedef struct {
   int32_t dense_chunk_threshold;
   int32_t validate;
   int64_t max_scratch_bytes;
+  int32_t l2_fetch_bytes;
+  int32_t reserved;
 } magnus_params_t;
 
 /* Fill *p with the automatic values.  Returns MAGNUS_INVALID_ARG on NULL. */

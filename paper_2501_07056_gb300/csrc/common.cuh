@@ -87,43 +87,76 @@ __device__ __forceinline__ T block_sum(T x, T* ws) {
 // q = lane * E + e ("blocked" layout), so the partner of a compare-exchange at
 // distance j < E is in the same lane and at distance j >= E it is lane ^ (j/E).
 // On return the keys are ascending in q.
-template <int E, typename K>
-__device__ __forceinline__ void warp_bitonic_sort(K (&k)[E]) {
-  const int lane = lane_id();
-  constexpr int N = 32 * E;
+//
+// The direction of a compare-exchange depends only on bit `size` of q.  For
+// size >= E that bit comes from the lane alone, for size < E from e alone, so
+// each stage needs one lane predicate (or none) and one min/max per key.
+__device__ __forceinline__ uint32_t kmin(uint32_t a, uint32_t b) { return min(a, b); }
+__device__ __forceinline__ uint32_t kmax(uint32_t a, uint32_t b) { return max(a, b); }
+__device__ __forceinline__ uint64_t kmin(uint64_t a, uint64_t b) { return a < b ? a : b; }
+__device__ __forceinline__ uint64_t kmax(uint64_t a, uint64_t b) { return a < b ? b : a; }
+
+// Bitonic sort over aligned groups of W lanes holding R keys each (W * R
+// keys per group, W a power of two <= 32).  Logical position of (lane l in
+// its group, e) is q = l * R + e; partners at distance j >= R are in lane
+// l ^ (j / R) of the same group.
+template <int R, int W, typename K>
+__device__ __forceinline__ void group_bitonic_sort(K (&k)[R]) {
+  const int l = lane_id() & (W - 1);
+  constexpr int N = W * R;
 #pragma unroll
   for (int size = 2; size <= N; size <<= 1) {
 #pragma unroll
     for (int j = size >> 1; j > 0; j >>= 1) {
-      if (j >= E) {
-        const int pl = j / E;
-        const bool upper = (lane & pl) != 0;  // this lane holds the higher index
+      if (j >= R) {
+        const int pl = j / R;
+        // this lane keeps the max iff (descending block) xor (higher partner)
+        const bool desc = ((l * R) & size) != 0;
+        const bool take_max = desc != ((l & pl) != 0);
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int q = lane * E + e;
-          const bool asc = (q & size) == 0;
-          K other = __shfl_xor_sync(FULL, k[e], pl);
-          // ascending block: lower index keeps min; descending: lower keeps max
-          const bool keep_min = (asc != upper);
-          K mn = other < k[e] ? other : k[e];
-          K mx = other < k[e] ? k[e] : other;
-          k[e] = keep_min ? mn : mx;
+        for (int e = 0; e < R; ++e) {
+          const K other = __shfl_xor_sync(FULL, k[e], pl);
+          k[e] = take_max ? kmax(k[e], other) : kmin(k[e], other);
         }
       } else {
+        const bool lane_desc = (size >= R) && (((l * R) & size) != 0);
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
+        for (int e = 0; e < R; ++e) {
           if ((e & j) == 0) {
-            const int q = lane * E + e;
-            const bool asc = (q & size) == 0;
-            K a = k[e], b = k[e + j];
-            const bool sw = asc ? (b < a) : (a < b);
-            k[e] = sw ? b : a;
-            k[e + j] = sw ? a : b;
+            const bool desc = (size >= R) ? lane_desc : ((e & size) != 0);
+            const K lo = kmin(k[e], k[e + j]);
+            const K hi = kmax(k[e], k[e + j]);
+            k[e] = desc ? hi : lo;
+            k[e + j] = desc ? lo : hi;
           }
         }
       }
     }
   }
+}
+
+template <int E, typename K>
+__device__ __forceinline__ void warp_bitonic_sort(K (&k)[E]) {
+  group_bitonic_sort<E, 32, K>(k);
+}
+
+// Scans and sums inside aligned groups of W lanes (all 32 lanes must call).
+template <int W, typename T>
+__device__ __forceinline__ T group_inclusive_scan(T x) {
+  const int l = lane_id() & (W - 1);
+#pragma unroll
+  for (int d = 1; d < W; d <<= 1) {
+    T y = __shfl_up_sync(FULL, x, d, W);
+    if (l >= d) x += y;
+  }
+  return x;
+}
+
+template <int W, typename T>
+__device__ __forceinline__ T group_sum(T x) {
+#pragma unroll
+  for (int d = W / 2; d > 0; d >>= 1) x += __shfl_xor_sync(FULL, x, d, W);
+  return x;
 }
 
 // Block bitonic sort of n_pow2 keys in shared memory (n_pow2 a power of two,

@@ -50,7 +50,17 @@ struct Csr {
 // cudaGetLastError() of the launch.
 cudaError_t launch_validate(const Csr& M, int* d_flag, cudaStream_t s);
 cudaError_t launch_rowinfo(const Csr& A, const Csr& B, CatParams cp, int64_t* P, uint8_t* bin,
-                           int32_t* lo, int32_t* hi, cudaStream_t s);
+                           int32_t* lo, int32_t* hi, int64_t* seg_bs, int32_t* seg_len,
+                           cudaStream_t s);
+
+// A range and id of a listed row (16 bytes, one vector load).
+struct __align__(16) RowDesc {
+  int64_t as;   // A.rowPtr[row]
+  int32_t na;   // nonzeros of the row of A
+  int32_t row;  // row id
+};
+cudaError_t launch_row_desc(const int32_t* rows, int64_t n, const int64_t* a_rp, RowDesc* desc,
+                            cudaStream_t s);
 cudaError_t launch_bin_partition(const uint8_t* bin, int64_t n, int32_t* rows_out,
                                  int64_t* bin_counts_dev, int64_t* blk_scratch, int64_t nblk_cap,
                                  cudaStream_t s);
@@ -71,9 +81,13 @@ cudaError_t launch_scan_i32_to_i64(const int32_t* in, int64_t n, int64_t* out, i
 // c_row_ptr-like array position row (count stored in out_cnt[row]).
 struct SortArgs {
   Csr A, B;
-  const int32_t* rows;  // row list of the bin
+  const RowDesc* desc;  // descriptors of the bin's rows
+  const int64_t* seg_bs;  // per nonzero of A: B.rowPtr of its B row
+  const int32_t* seg_len; // per nonzero of A: length of its B row
   int64_t n_rows;
   int key32;            // 1: (col << slot_bits | slot) fits 32 bits
+  uint8_t* perm;        // sorted slot order, 32*E bytes per listed row
+                        // (written by the symbolic pass, replayed by the numeric pass)
   // symbolic
   int64_t* out_cnt;     // indexed by row
   // numeric

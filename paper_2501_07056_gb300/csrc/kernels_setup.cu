@@ -54,10 +54,15 @@ cudaError_t launch_validate(const Csr& M, int* d_flag, cudaStream_t s) {
 // Row analysis (Section 3.1): P_i, column range [lo, hi] of the intermediate
 // product (from the first and last column of each referenced B row, which is
 // valid because rows are sorted), and the bin of the row.  V lanes per row.
+// Also writes the segment table: for every nonzero j of A, the start and the
+// length of the B row it selects (seg_bs[j] = B.rowPtr[A.col[j]], seg_len[j] =
+// nnz of that row), so later passes read it as a stream instead of gathering
+// B.rowPtr again.
 template <int V>
 __global__ void k_rowinfo(Csr A, Csr B, CatParams cp, int64_t* __restrict__ P,
                           uint8_t* __restrict__ bin, int32_t* __restrict__ lo_out,
-                          int32_t* __restrict__ hi_out) {
+                          int32_t* __restrict__ hi_out, int64_t* __restrict__ seg_bs,
+                          int32_t* __restrict__ seg_len) {
   const int sub = threadIdx.x & (V - 1);
   const int64_t groups = (int64_t)gridDim.x * (blockDim.x / V);
   const unsigned gmask = (V == 32) ? FULL : (((1u << V) - 1) << ((threadIdx.x & 31) & ~(V - 1)));
@@ -71,7 +76,10 @@ __global__ void k_rowinfo(Csr A, Csr B, CatParams cp, int64_t* __restrict__ P,
     int64_t p = 0;
     for (int64_t j = s + sub; j < e; j += V) {
       const int32_t c = A.col[j];
-      p += B.rp[c + 1] - B.rp[c];
+      const int64_t b0 = B.rp[c], b1 = B.rp[c + 1];
+      p += b1 - b0;
+      seg_bs[j] = b0;
+      seg_len[j] = (int32_t)(b1 - b0);
     }
 #pragma unroll
     for (int d = V / 2; d > 0; d >>= 1) p += __shfl_xor_sync(gmask, p, d, V);
@@ -129,7 +137,8 @@ __global__ void k_rowinfo(Csr A, Csr B, CatParams cp, int64_t* __restrict__ P,
 }
 
 cudaError_t launch_rowinfo(const Csr& A, const Csr& B, CatParams cp, int64_t* P, uint8_t* bin,
-                           int32_t* lo, int32_t* hi, cudaStream_t s) {
+                           int32_t* lo, int32_t* hi, int64_t* seg_bs, int32_t* seg_len,
+                           cudaStream_t s) {
   if (A.n_rows == 0) return cudaSuccess;
   const double avg = A.n_rows ? (double)A.nnz / (double)A.n_rows : 0.0;
   const int nt = 256;
@@ -137,12 +146,12 @@ cudaError_t launch_rowinfo(const Csr& A, const Csr& B, CatParams cp, int64_t* P,
   while (v < 32 && v < avg) v <<= 1;
   unsigned g = grid_cap(cdiv(A.n_rows * v, nt), 1 << 20);
   switch (v) {
-    case 1: k_rowinfo<1><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi); break;
-    case 2: k_rowinfo<2><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi); break;
-    case 4: k_rowinfo<4><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi); break;
-    case 8: k_rowinfo<8><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi); break;
-    case 16: k_rowinfo<16><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi); break;
-    default: k_rowinfo<32><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi); break;
+    case 1: k_rowinfo<1><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg_bs, seg_len); break;
+    case 2: k_rowinfo<2><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg_bs, seg_len); break;
+    case 4: k_rowinfo<4><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg_bs, seg_len); break;
+    case 8: k_rowinfo<8><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg_bs, seg_len); break;
+    case 16: k_rowinfo<16><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg_bs, seg_len); break;
+    default: k_rowinfo<32><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg_bs, seg_len); break;
   }
   count_launch();
   return cudaGetLastError();
@@ -229,6 +238,29 @@ cudaError_t launch_bin_partition(const uint8_t* bin, int64_t n, int32_t* rows_ou
     k_bin_scatter<<<(unsigned)nblk, BP_NT, 0, s>>>(bin, n, blk, nblk, rows_out);
     count_launch();
   }
+  return cudaGetLastError();
+}
+
+// Row descriptors of a row list: the A range and id of every listed row, so
+// per-row kernels start from one coalesced 16-byte load.
+__global__ void k_row_desc(const int32_t* __restrict__ rows, int64_t n,
+                           const int64_t* __restrict__ a_rp, RowDesc* __restrict__ desc) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = rows[t];
+    RowDesc d;
+    d.as = a_rp[r];
+    d.na = (int32_t)(a_rp[r + 1] - d.as);
+    d.row = r;
+    desc[t] = d;
+  }
+}
+
+cudaError_t launch_row_desc(const int32_t* rows, int64_t n, const int64_t* a_rp, RowDesc* desc,
+                            cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_row_desc<<<grid_cap(cdiv(n, 256), 1 << 16), 256, 0, s>>>(rows, n, a_rp, desc);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -1,90 +1,197 @@
-// Sort-category rows (Section 3.1, category 1; Algorithm 2): one warp per
-// row.  The row's intermediate product (at most 32*E products) is generated
-// straight from A and B into registers, sorted by a register bitonic network
-// on packed (column, slot) keys and compressed.  The symbolic pass counts
-// distinct columns (precise prediction); the numeric pass multiplies, merges
-// duplicates in traversal order and writes the row of C.
+// Sort-category rows (Section 3.1, category 1; Algorithm 2).
+//
+// A row of bin E holds at most 32*E products.  It is handled by a group of
+// W = 4*E lanes with R = 8 products per lane, so a warp works on G = 8/E rows
+// at once: every level of the load chain (row id, A.rowPtr, A.col/A.val,
+// B.rowPtr, B.col/B.val) is issued for G rows together, and the sorting
+// network runs mostly inside registers (three of its stage distances stay in
+// a lane).
+//
+// Symbolic: the row's products are generated from A and B into registers,
+// sorted by a bitonic network on packed (column, slot) keys and their
+// distinct columns counted (precise prediction, Section 2.1).  The sorted
+// order of the slots is kept, one byte per product, for the numeric pass.
+//
+// Numeric: the products are generated again with their values
+// A.val * B.val; they are visited in the recorded sorted order, equal
+// columns are summed in slot order (the traversal order of Algorithm 1), and
+// the row of C is written.
 #include "sort_accum.cuh"
 
 namespace magnus {
 
 template <int E, typename K, bool NUMERIC, int NW>
 __global__ void __launch_bounds__(NW * 32) k_sort_rows(SortArgs a) {
-  constexpr int CAP = 32 * E;
+  constexpr int W = 4 * E;    // lanes per row
+  constexpr int G = 32 / W;   // rows per warp
+  constexpr int R = 8;        // products per lane
+  constexpr int CAP = W * R;  // = 32 * E
   constexpr int SB = Log2Cap<E>::v;
+  constexpr int HW = CAP / 32;  // head-bit words per row
   using KT = KeyTraits<K>;
-  __shared__ int32_t s_off[NW][CAP];                 // first slot of each non-empty segment
-  __shared__ int64_t s_bs[NW][CAP];                  // B.rowPtr of the segment's B row
-  __shared__ double s_av[NW][NUMERIC ? CAP : 1];     // A value of the segment
-  __shared__ uint32_t s_head[NW][E];                 // bit s: a segment (other than 0) starts at slot s
-  __shared__ double s_vals[NW][NUMERIC ? CAP : 1];   // product value by slot
-  __shared__ K s_keys[NW][NUMERIC ? CAP : 1];        // sorted keys (run walking)
+  // Per-warp shared arrays, indexed [position][group] so that the lanes of
+  // the G groups interleave and a warp-wide access touches distinct banks.
+  __shared__ uint8_t s_off[NW][CAP][G];    // first slot of each non-empty segment
+  __shared__ int64_t s_bs[NW][CAP][G];     // B.rowPtr of the segment's B row
+  __shared__ double s_av[NW][NUMERIC ? CAP : 1][G];
+  __shared__ uint32_t s_head[NW][HW][G];   // bit s: a segment other than the first starts at slot s
+  __shared__ int32_t s_col[NW][NUMERIC ? CAP : 1][G];
+  __shared__ double s_val[NW][NUMERIC ? CAP : 1][G];
+  __shared__ uint8_t s_perm[NW][NUMERIC ? CAP : 1][G];
   const int lane = lane_id(), w = warp_id();
-  const int64_t stride = (int64_t)gridDim.x * NW;
-  for (int64_t t = (int64_t)blockIdx.x * NW + w; t < a.n_rows; t += stride) {
-    const int32_t row = a.rows[t];
-    const int64_t as = a.A.rp[row], ae = a.A.rp[row + 1];
-    if (lane < E) s_head[w][lane] = 0;
-    // 1. Segments: the non-empty B rows referenced by row `row` of A, in
-    //    stored order, with the first slot of each in the row's product list.
+  const int grp = lane / W, l = lane & (W - 1);
+  const int gshift = grp * W;
+  const unsigned gbits = (W == 32) ? FULL : ((1u << W) - 1u);
+  const int64_t stride = (int64_t)gridDim.x * NW * G;
+  for (int64_t base = ((int64_t)blockIdx.x * NW + w) * G; base < a.n_rows; base += stride) {
+    const int64_t idx = base + grp;
+    const bool valid = idx < a.n_rows;
+    RowDesc d{0, 0, 0};
+    if (valid) d = a.desc[idx];
+    uint64_t perm = 0;
+    if (NUMERIC && valid) perm = *reinterpret_cast<const uint64_t*>(a.perm + idx * CAP + l * R);
+    int64_t crp = 0;
+    if (NUMERIC && valid) crp = a.c_rp[d.row];
+    if (l < HW) s_head[w][l][grp] = 0;
+    // 1. Segments: the non-empty B rows referenced by the row, in stored
+    //    order, each with its first slot in the row's product list.
     int nseg = 0, P = 0;
-    for (int64_t j0 = as; j0 < ae; j0 += 32) {
-      const int64_t j = j0 + lane;
+    for (int j0 = 0; __any_sync(FULL, j0 < d.na); j0 += W) {
+      const int j = j0 + l;
       int64_t bs = 0;
       int L = 0;
       double av = 0.0;
-      if (j < ae) {
-        const int32_t c = a.A.col[j];
-        bs = a.B.rp[c];
-        L = (int)(a.B.rp[c + 1] - bs);
-        if (NUMERIC) av = a.A.val[j];
+      if (j < d.na) {
+        bs = a.seg_bs[d.as + j];
+        L = a.seg_len[d.as + j];
+        if (NUMERIC) av = a.A.val[d.as + j];
       }
-      const unsigned nz = __ballot_sync(FULL, L > 0);
-      const int inc = warp_inclusive_scan(L);
+      const unsigned nz = (__ballot_sync(FULL, L > 0) >> gshift) & gbits;
+      const int inc = group_inclusive_scan<W>(L);
       if (L > 0) {
-        const int g = nseg + __popc(nz & ((1u << lane) - 1));
-        s_off[w][g] = P + inc - L;
-        s_bs[w][g] = bs;
-        if (NUMERIC) s_av[w][g] = av;
+        const int g = nseg + __popc(nz & ((1u << l) - 1u));
+        s_off[w][g][grp] = (uint8_t)(P + inc - L);
+        s_bs[w][g][grp] = bs;
+        if (NUMERIC) s_av[w][g][grp] = av;
       }
       nseg += __popc(nz);
-      P += __shfl_sync(FULL, inc, 31);
+      P += __shfl_sync(FULL, inc, gshift + W - 1);
     }
     __syncwarp();
-    for (int g = 1 + lane; g < nseg; g += 32) {
-      const int off = s_off[w][g];
-      atomicOr(&s_head[w][off >> 5], 1u << (off & 31));
+    for (int g = 1 + l; g < nseg; g += W) {
+      const int off = s_off[w][g][grp];
+      atomicOr(&s_head[w][off >> 5][grp], 1u << (off & 31));
     }
     __syncwarp();
-    // 2. Expand: lane handles slots e*32 + lane (coalesced B reads); the
-    //    segment of a slot is the number of segment starts at or before it.
-    K key[E];
-    int segcum = 0;
+    uint32_t hw[HW];
+    int pw[HW];
+    {
+      int cum = 0;
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int s = e * 32 + lane;
-      const uint32_t hb = s_head[w][e];
-      const int g = segcum + __popc(hb & ((2u << lane) - 1u));
-      segcum += __popc(hb);
+      for (int i = 0; i < HW; ++i) {
+        hw[i] = s_head[w][i][grp];
+        pw[i] = cum;
+        cum += __popc(hw[i]);
+      }
+    }
+    // 2. Expand: slot s = e*W + l (consecutive lanes read consecutive
+    //    entries of a B row).  The segment of s is the number of segment
+    //    starts at or before s.
+    K key[R];
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+      const int s = e * W + l;
+      const int wi = (e * W) >> 5;
+      const int g = pw[wi] + __popc(hw[wi] & ((2u << (s & 31)) - 1u));
       if (s < P) {
-        const int64_t k = s_bs[w][g] + (s - s_off[w][g]);
+        const int64_t k = s_bs[w][g][grp] + (s - s_off[w][g][grp]);
         const int32_t c = a.B.col[k];
-        key[e] = KT::template make<SB>(c, s);
-        if (NUMERIC) s_vals[w][s] = s_av[w][g] * a.B.val[k];
-      } else {
+        if (NUMERIC) {
+          s_col[w][s][grp] = c;
+          s_val[w][s][grp] = s_av[w][g][grp] * a.B.val[k];
+        } else {
+          key[e] = KT::template make<SB>(c, s);
+        }
+      } else if (!NUMERIC) {
         key[e] = ~K(0);
       }
     }
-    // 3. Sort (keys are distinct; padding sorts last).
-    warp_bitonic_sort<E>(key);
-    // 4. Compress.
-    if (NUMERIC) {
-      __syncwarp();
-      const int64_t ob = a.c_rp[row];
-      warp_merge_emit<E, K, true>(key, P, s_vals[w], s_keys[w], 0, a.c_col + ob, a.c_val + ob);
+    if (!NUMERIC) {
+      // 3s. Sort, count distinct columns, record the sorted slot order.
+      group_bitonic_sort<R, W>(key);
+      const K prev_last = __shfl_up_sync(FULL, key[R - 1], 1, W);
+      int h = 0;
+      uint64_t pb = 0;
+#pragma unroll
+      for (int e = 0; e < R; ++e) {
+        const int q = l * R + e;
+        const int32_t c = KT::template col<SB>(key[e]);
+        const int32_t pc = (e == 0) ? ((l == 0) ? -1 : KT::template col<SB>(prev_last))
+                                    : KT::template col<SB>(key[e - 1]);
+        h += ((q < P) && (q == 0 || c != pc)) ? 1 : 0;
+        pb |= (uint64_t)(KT::template slot<SB>(key[e]) & 0xff) << (8 * e);
+      }
+      const int cnt = group_sum<W>(h);
+      if (valid) {
+        if (l == 0) a.out_cnt[d.row] = cnt;
+        *reinterpret_cast<uint64_t*>(a.perm + idx * CAP + l * R) = pb;
+      }
     } else {
-      const int cnt = warp_merge_emit<E, K, false>(key, P, nullptr, nullptr, 0, nullptr, nullptr);
-      if (lane == 0) a.out_cnt[row] = cnt;
+      // 3n. Replay the recorded order and write the row of C.
+      int sl[R];
+#pragma unroll
+      for (int e = 0; e < R; ++e) {
+        sl[e] = (int)((perm >> (8 * e)) & 0xff);
+        s_perm[w][l * R + e][grp] = (uint8_t)sl[e];
+      }
+      __syncwarp();
+      const int prev_slot = __shfl_up_sync(FULL, sl[R - 1], 1, W);
+      bool head[R];
+      int32_t col[R];
+      int h = 0;
+#pragma unroll
+      for (int e = 0; e < R; ++e) {
+        const int q = l * R + e;
+        col[e] = (q < P) ? s_col[w][sl[e]][grp] : 0;
+        int32_t pc = -1;
+        if (q > 0 && q < P) pc = s_col[w][(e == 0) ? prev_slot : sl[e - 1]][grp];
+        head[e] = (q < P) && (q == 0 || col[e] != pc);
+        h += head[e] ? 1 : 0;
+      }
+      const int inc = group_inclusive_scan<W>(h);
+      const int cnt = __shfl_sync(FULL, inc, gshift + W - 1);
+      double acc[R];
+#pragma unroll
+      for (int e = 0; e < R; ++e) {
+        acc[e] = 0.0;
+        if (head[e]) {
+          acc[e] = s_val[w][sl[e]][grp];
+          for (int q2 = l * R + e + 1; q2 < P; ++q2) {
+            const int s2 = s_perm[w][q2][grp];
+            if (s_col[w][s2][grp] != col[e]) break;
+            acc[e] += s_val[w][s2][grp];
+          }
+        }
+      }
+      __syncwarp();
+      // stage the row's entries by output position, then write them with
+      // consecutive lanes on consecutive addresses
+      int pos = inc - h;
+#pragma unroll
+      for (int e = 0; e < R; ++e) {
+        if (head[e]) {
+          s_col[w][pos][grp] = col[e];
+          s_val[w][pos][grp] = acc[e];
+          ++pos;
+        }
+      }
+      __syncwarp();
+      if (valid) {
+        for (int i = l; i < cnt; i += W) {
+          a.c_col[crp + i] = s_col[w][i][grp];
+          a.c_val[crp + i] = s_val[w][i][grp];
+        }
+      }
     }
     __syncwarp();
   }
@@ -92,11 +199,17 @@ __global__ void __launch_bounds__(NW * 32) k_sort_rows(SortArgs a) {
 
 template <int E, typename K, bool NUMERIC>
 static cudaError_t launch_one(const SortArgs& a, int num_sms, cudaStream_t s) {
-  constexpr int NW = (E >= 8) ? 4 : 8;
-  int64_t blocks = (a.n_rows + NW - 1) / NW;
-  const int64_t cap = (int64_t)num_sms * 32;
+  constexpr int NW = NUMERIC ? 4 : 8;
+  constexpr int G = 8 / E;
+  auto kern = k_sort_rows<E, K, NUMERIC, NW>;
+  int per_sm = 0;
+  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NW * 32, 0);
+  if (err != cudaSuccess) return err;
+  if (per_sm < 1) per_sm = 1;
+  int64_t blocks = (a.n_rows + NW * G - 1) / (NW * G);
+  const int64_t cap = (int64_t)num_sms * per_sm;  // one resident wave
   if (blocks > cap) blocks = cap;
-  k_sort_rows<E, K, NUMERIC, NW><<<(unsigned)blocks, NW * 32, 0, s>>>(a);
+  kern<<<(unsigned)blocks, NW * 32, 0, s>>>(a);
   count_launch();
   return cudaGetLastError();
 }
@@ -115,12 +228,9 @@ static cudaError_t launch_bin(int bin, const SortArgs& a, int num_sms, cudaStrea
 cudaError_t launch_sort_rows(int bin, bool numeric, const SortArgs& a, int num_sms,
                              cudaStream_t s) {
   if (a.n_rows == 0) return cudaSuccess;
-  if (a.key32) {
-    return numeric ? launch_bin<uint32_t, true>(bin, a, num_sms, s)
-                   : launch_bin<uint32_t, false>(bin, a, num_sms, s);
-  }
-  return numeric ? launch_bin<uint64_t, true>(bin, a, num_sms, s)
-                 : launch_bin<uint64_t, false>(bin, a, num_sms, s);
+  if (numeric) return launch_bin<uint32_t, true>(bin, a, num_sms, s);  // no keys in the replay
+  if (a.key32) return launch_bin<uint32_t, false>(bin, a, num_sms, s);
+  return launch_bin<uint64_t, false>(bin, a, num_sms, s);
 }
 
 }  // namespace magnus

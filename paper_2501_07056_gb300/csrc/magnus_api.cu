@@ -136,6 +136,9 @@ struct magnus_plan_s {
   int32_t* lo = nullptr;
   int32_t* hi = nullptr;
   int32_t* rows_sorted = nullptr;
+  RowDesc* desc = nullptr;       // per listed row (bin order)
+  int64_t* seg_bs = nullptr;     // per nonzero of A
+  int32_t* seg_len = nullptr;
   int64_t bin_off[NUM_BINS + 1] = {0};
   // fine rows (heaviest first), batches as list index ranges
   std::vector<int32_t> fine_rows;
@@ -152,6 +155,9 @@ struct magnus_plan_s {
   std::vector<int64_t> coarse_batches;
   int32_t* coarse_rows_d = nullptr;
   int32_t* bucket_cnt = nullptr;
+  // sorted slot order of the sort rows (symbolic -> numeric)
+  uint8_t* perm = nullptr;
+  int64_t perm_off[NUM_BINS + 1] = {0};
   // state and statistics
   bool symbolic_done = false;
   int64_t nnz_c = -1;
@@ -217,6 +223,27 @@ void ensure_pool_retains(int dev) {
   }
   done[dev] = true;
 }
+
+// Applies the plan's L2 fetch granularity hint for the duration of a call.
+struct FetchGranularity {
+  bool active = false;
+  size_t prev = 0;
+  explicit FetchGranularity(int bytes) {
+    if (bytes <= 0) return;
+    if (cudaDeviceGetLimit(&prev, cudaLimitMaxL2FetchGranularity) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    const size_t want = (size_t)bytes;
+    if (want != prev && cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, want) == cudaSuccess)
+      active = true;
+    else
+      cudaGetLastError();
+  }
+  ~FetchGranularity() {
+    if (active) cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, prev);
+  }
+};
 
 struct StageTimer {
   magnus_plan_t p;
@@ -371,13 +398,17 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
   MAG_TRY(plan_alloc(pl, &pl->lo, n + 1, s));
   MAG_TRY(plan_alloc(pl, &pl->hi, n + 1, s));
   MAG_TRY(plan_alloc(pl, &pl->rows_sorted, n + 1, s));
+  MAG_TRY(plan_alloc(pl, &pl->desc, n + 1, s));
+  MAG_TRY(plan_alloc(pl, &pl->seg_bs, (size_t)A->nnz + 1, s));
+  MAG_TRY(plan_alloc(pl, &pl->seg_len, (size_t)A->nnz + 1, s));
   CatParams cp;
   cp.sort_threshold = pl->sort_T;
   cp.force = P.force_category;
   cp.dense_cols = pl->dense_cols;
   cp.fine_shift = pl->shift_fine;
   cp.fine_max_chunks = FINE_MAX_CHUNKS;
-  CUDA_TRY(launch_rowinfo(pl->A, pl->B, cp, pl->P, pl->bin, pl->lo, pl->hi, s));
+  CUDA_TRY(launch_rowinfo(pl->A, pl->B, cp, pl->P, pl->bin, pl->lo, pl->hi, pl->seg_bs,
+                          pl->seg_len, s));
   int64_t* stats;
   MAG_TRY(plan_alloc(pl, &stats, 2 + NUM_BINS + 1, s));
   CUDA_TRY(launch_reduce_stats(pl->P, n, stats, s));
@@ -387,6 +418,7 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
   int64_t* blk;
   MAG_TRY(tmp.get(&blk, (size_t)(m + 1 + scan_tmp_elems(m) + 1)));
   CUDA_TRY(launch_bin_partition(pl->bin, n, pl->rows_sorted, stats + 2, blk, nblk, s));
+  CUDA_TRY(launch_row_desc(pl->rows_sorted, n, pl->A.rp, pl->desc, s));
   int64_t hstats[2 + NUM_BINS + 1];
   CUDA_TRY(cudaMemcpyAsync(hstats, stats, sizeof(hstats), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
@@ -422,6 +454,16 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
     return MAGNUS_OK;
   };
 
+  // sorted slot order of the sort rows: 32*E bytes per row of each sort bin
+  {
+    int64_t o = 0;
+    for (int b = 0; b <= NUM_BINS; ++b) {
+      pl->perm_off[b] = o;
+      if (b >= BIN_SORT32 && b <= BIN_SORT256)
+        o += (pl->bin_off[b + 1] - pl->bin_off[b]) * ((int64_t)32 << (b - BIN_SORT32));
+    }
+    MAG_TRY(plan_alloc(pl, &pl->perm, (size_t)o + 16, s));
+  }
   // per-category statistics and the dense row count
   std::vector<int32_t> drows;
   std::vector<int64_t> dP;
@@ -530,9 +572,12 @@ static int run_phase(magnus_plan_t pl, bool numeric, int64_t* out_cnt, const int
       SortArgs a{};
       a.A = A;
       a.B = B;
-      a.rows = pl->rows_sorted + pl->bin_off[b];
+      a.desc = pl->desc + pl->bin_off[b];
+      a.seg_bs = pl->seg_bs;
+      a.seg_len = pl->seg_len;
       a.n_rows = pl->bin_off[b + 1] - pl->bin_off[b];
       a.key32 = pl->key32[b];
+      a.perm = pl->perm + pl->perm_off[b];
       a.out_cnt = out_cnt;
       a.c_rp = c_rp;
       a.c_col = c_col;
@@ -679,6 +724,7 @@ int magnus_symbolic(magnus_plan_t pl, int64_t* c_row_ptr, int64_t* nnz_c, void* 
   pl->symbolic_done = false;
   for (int i = 0; i < MAGNUS_STAGE_COUNT; ++i) pl->ev_used[i] = false;
   const int64_t n = pl->A.n_rows;
+  FetchGranularity fg(pl->params.l2_fetch_bytes);
   CUDA_TRY(cudaMemsetAsync(c_row_ptr, 0, (size_t)(n + 1) * sizeof(int64_t), s));
   MAG_TRY(run_phase(pl, false, c_row_ptr, nullptr, nullptr, nullptr, s));
   {
@@ -708,6 +754,7 @@ int magnus_numeric(magnus_plan_t pl, const double* a_val, const double* b_val,
   for (int i = MAGNUS_STAGE_NUM_SORT; i < MAGNUS_STAGE_COUNT; ++i) pl->ev_used[i] = false;
   pl->A.val = a_val;
   pl->B.val = b_val;
+  FetchGranularity fg(pl->params.l2_fetch_bytes);
   return run_phase(pl, true, nullptr, c_row_ptr, c_col, c_val, s);
 }
 

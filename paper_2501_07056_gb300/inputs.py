@@ -268,6 +268,9 @@ def workload(name: str, seed: int = 0):
     if name == "uniform4096":
         A = uniform(4096, 4096, 8, seed, 0)
         return A, A
+    if name == "uniform2^22":
+        A = uniform(1 << 22, 1 << 22, 8, seed, 0)
+        return A, A
     if name == "uniform2^24":
         A = uniform(1 << 24, 1 << 24, 8, seed, 0)
         return A, A

@@ -35,7 +35,7 @@ class Params(ctypes.Structure):
     _fields_ = [("sort_threshold", c_i32), ("force_category", c_i32),
                 ("chunk_len_fine_log2", c_i32), ("chunk_len_coarse_log2", c_i32),
                 ("dense_chunk_threshold", c_i32), ("validate", c_i32),
-                ("max_scratch_bytes", c_i64)]
+                ("max_scratch_bytes", c_i64), ("l2_fetch_bytes", c_i32), ("reserved", c_i32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -207,7 +207,7 @@ class DeviceCSR:
 
 def make_params(sort_threshold=0, force_category=CAT_AUTO, chunk_len_fine_log2=0,
                 chunk_len_coarse_log2=0, dense_chunk_threshold=0, validate=0,
-                max_scratch_bytes=0) -> Params:
+                max_scratch_bytes=0, l2_fetch_bytes=0) -> Params:
     p = magnus_params_default()
     p.sort_threshold = sort_threshold
     p.force_category = force_category
@@ -216,6 +216,7 @@ def make_params(sort_threshold=0, force_category=CAT_AUTO, chunk_len_fine_log2=0
     p.dense_chunk_threshold = dense_chunk_threshold
     p.validate = validate
     p.max_scratch_bytes = max_scratch_bytes
+    p.l2_fetch_bytes = l2_fetch_bytes
     return p
 
 
