@@ -43,15 +43,40 @@ __global__ void __launch_bounds__(NW * 32) k_sort_rows(SortArgs a) {
   const int gshift = grp * W;
   const unsigned gbits = (W == 32) ? FULL : ((1u << W) - 1u);
   const int64_t stride = (int64_t)gridDim.x * NW * G;
-  for (int64_t base = ((int64_t)blockIdx.x * NW + w) * G; base < a.n_rows; base += stride) {
+  const int64_t n = a.n_rows;
+
+  // Level 1 of the load chain: the row descriptor (and the recorded order).
+  struct Pre1 { RowDesc d; uint64_t perm; };
+  // Level 2: output offset and the first W segment-table entries of the row.
+  struct Pre2 { int64_t crp; int64_t bs; int32_t L; double av; };
+  auto load1 = [&](int64_t base) -> Pre1 {
+    Pre1 p{{0, 0, 0}, 0};
     const int64_t idx = base + grp;
-    const bool valid = idx < a.n_rows;
-    RowDesc d{0, 0, 0};
-    if (valid) d = a.desc[idx];
-    uint64_t perm = 0;
-    if (NUMERIC && valid) perm = *reinterpret_cast<const uint64_t*>(a.perm + idx * CAP + l * R);
-    int64_t crp = 0;
-    if (NUMERIC && valid) crp = a.c_rp[d.row];
+    if (idx < n) {
+      p.d = a.desc[idx];
+      if (NUMERIC) p.perm = *reinterpret_cast<const uint64_t*>(a.perm + idx * CAP + l * R);
+    }
+    return p;
+  };
+  auto load2 = [&](int64_t base, const Pre1& p1) -> Pre2 {
+    Pre2 q{0, 0, 0, 0.0};
+    if (base + grp < n) {
+      if (NUMERIC) q.crp = a.c_rp[p1.d.row];
+      if (l < p1.d.na) {
+        q.bs = a.seg_bs[p1.d.as + l];
+        q.L = a.seg_len[p1.d.as + l];
+        if (NUMERIC) q.av = a.A.val[p1.d.as + l];
+      }
+    }
+    return q;
+  };
+
+  auto process = [&](int64_t base, const Pre1& p1, const Pre2& p2) {
+    const int64_t idx = base + grp;
+    const bool valid = idx < n;
+    const RowDesc d = p1.d;
+    const uint64_t perm = p1.perm;
+    const int64_t crp = p2.crp;
     if (l < HW) s_head[w][l][grp] = 0;
     // 1. Segments: the non-empty B rows referenced by the row, in stored
     //    order, each with its first slot in the row's product list.
@@ -61,7 +86,11 @@ __global__ void __launch_bounds__(NW * 32) k_sort_rows(SortArgs a) {
       int64_t bs = 0;
       int L = 0;
       double av = 0.0;
-      if (j < d.na) {
+      if (j0 == 0) {
+        bs = p2.bs;  // prefetched one iteration ahead
+        L = p2.L;
+        av = p2.av;
+      } else if (j < d.na) {
         bs = a.seg_bs[d.as + j];
         L = a.seg_len[d.as + j];
         if (NUMERIC) av = a.A.val[d.as + j];
@@ -97,23 +126,39 @@ __global__ void __launch_bounds__(NW * 32) k_sort_rows(SortArgs a) {
     // 2. Expand: slot s = e*W + l (consecutive lanes read consecutive
     //    entries of a B row).  The segment of s is the number of segment
     //    starts at or before s.
-    K key[R];
+    // All gathers of the row are issued before any of them is used, so
+    // the R loads of a lane (2R in the numeric pass) are in flight together.
+    int32_t cg[R];
+    double vg[R];
+    double ag[R];
 #pragma unroll
     for (int e = 0; e < R; ++e) {
       const int s = e * W + l;
       const int wi = (e * W) >> 5;
       const int g = pw[wi] + __popc(hw[wi] & ((2u << (s & 31)) - 1u));
+      cg[e] = 0;
+      vg[e] = 0.0;
+      ag[e] = 0.0;
       if (s < P) {
         const int64_t k = s_bs[w][g][grp] + (s - s_off[w][g][grp]);
-        const int32_t c = a.B.col[k];
+        cg[e] = __ldg(a.B.col + k);
         if (NUMERIC) {
-          s_col[w][s][grp] = c;
-          s_val[w][s][grp] = s_av[w][g][grp] * a.B.val[k];
-        } else {
-          key[e] = KT::template make<SB>(c, s);
+          vg[e] = __ldg(a.B.val + k);
+          ag[e] = s_av[w][g][grp];
         }
-      } else if (!NUMERIC) {
-        key[e] = ~K(0);
+      }
+    }
+    K key[R];
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+      const int s = e * W + l;
+      if (NUMERIC) {
+        if (s < P) {
+          s_col[w][s][grp] = cg[e];
+          s_val[w][s][grp] = ag[e] * vg[e];
+        }
+      } else {
+        key[e] = (s < P) ? KT::template make<SB>(cg[e], s) : ~K(0);
       }
     }
     if (!NUMERIC) {
@@ -134,66 +179,84 @@ __global__ void __launch_bounds__(NW * 32) k_sort_rows(SortArgs a) {
       const int cnt = group_sum<W>(h);
       if (valid) {
         if (l == 0) a.out_cnt[d.row] = cnt;
-        *reinterpret_cast<uint64_t*>(a.perm + idx * CAP + l * R) = pb;
+        // Store the order so that the numeric pass, whose lane l visits
+        // sorted positions e*W + l, reads its 8 slots as one 8-byte word:
+        // position q goes to byte (q % W) * 8 + q / W.
+        uint8_t* dst = a.perm + idx * CAP;
+#pragma unroll
+        for (int e = 0; e < R; ++e) {
+          const int q = l * R + e;
+          dst[(q % W) * R + q / W] = (uint8_t)(pb >> (8 * e));
+        }
       }
     } else {
-      // 3n. Replay the recorded order and write the row of C.
+      // 3n. Replay the recorded order: lane l visits sorted positions
+      //     q = e*W + l, so consecutive lanes write consecutive entries of C.
       int sl[R];
 #pragma unroll
       for (int e = 0; e < R; ++e) {
         sl[e] = (int)((perm >> (8 * e)) & 0xff);
-        s_perm[w][l * R + e][grp] = (uint8_t)sl[e];
+        s_perm[w][e * W + l][grp] = (uint8_t)sl[e];
       }
       __syncwarp();
-      const int prev_slot = __shfl_up_sync(FULL, sl[R - 1], 1, W);
-      bool head[R];
-      int32_t col[R];
-      int h = 0;
+      int run = 0;                 // distinct columns before this e-row
+      int32_t last_col = -1;       // column of the position before this e-row
 #pragma unroll
       for (int e = 0; e < R; ++e) {
-        const int q = l * R + e;
-        col[e] = (q < P) ? s_col[w][sl[e]][grp] : 0;
-        int32_t pc = -1;
-        if (q > 0 && q < P) pc = s_col[w][(e == 0) ? prev_slot : sl[e - 1]][grp];
-        head[e] = (q < P) && (q == 0 || col[e] != pc);
-        h += head[e] ? 1 : 0;
-      }
-      const int inc = group_inclusive_scan<W>(h);
-      const int cnt = __shfl_sync(FULL, inc, gshift + W - 1);
-      double acc[R];
-#pragma unroll
-      for (int e = 0; e < R; ++e) {
-        acc[e] = 0.0;
-        if (head[e]) {
-          acc[e] = s_val[w][sl[e]][grp];
-          for (int q2 = l * R + e + 1; q2 < P; ++q2) {
-            const int s2 = s_perm[w][q2][grp];
-            if (s_col[w][s2][grp] != col[e]) break;
-            acc[e] += s_val[w][s2][grp];
+        const int q = e * W + l;
+        const bool in = q < P;
+        const int32_t c = in ? s_col[w][sl[e]][grp] : 0x7fffffff;
+        const int32_t up = __shfl_up_sync(FULL, c, 1, W);
+        const int32_t prev = (l == 0) ? last_col : up;
+        const bool head = in && (q == 0 || c != prev);
+        const unsigned hb = (__ballot_sync(FULL, head) >> gshift) & gbits;
+        const int32_t dn = __shfl_down_sync(FULL, c, 1, W);
+        if (head) {
+          const int o = run + __popc(hb & ((1u << l) - 1u));
+          double acc = s_val[w][sl[e]][grp];
+          // the next sorted position holds the same column: sum the run in
+          // slot order (the recorded order keeps equal columns slot-sorted)
+          const bool more = (l < W - 1) ? (dn == c) : (q + 1 < P);
+          if (more) {
+            for (int q2 = q + 1; q2 < P; ++q2) {
+              const int s2 = s_perm[w][q2][grp];
+              if (s_col[w][s2][grp] != c) break;
+              acc += s_val[w][s2][grp];
+            }
           }
+          a.c_col[crp + o] = c;
+          a.c_val[crp + o] = acc;
         }
-      }
-      __syncwarp();
-      // stage the row's entries by output position, then write them with
-      // consecutive lanes on consecutive addresses
-      int pos = inc - h;
-#pragma unroll
-      for (int e = 0; e < R; ++e) {
-        if (head[e]) {
-          s_col[w][pos][grp] = col[e];
-          s_val[w][pos][grp] = acc[e];
-          ++pos;
-        }
-      }
-      __syncwarp();
-      if (valid) {
-        for (int i = l; i < cnt; i += W) {
-          a.c_col[crp + i] = s_col[w][i][grp];
-          a.c_val[crp + i] = s_val[w][i][grp];
-        }
+        run += __popc(hb);
+        last_col = __shfl_sync(FULL, c, gshift + W - 1);
       }
     }
     __syncwarp();
+  };
+
+  // Two-stage software pipeline over this warp's groups of rows: while a
+  // group is finished, level 2 of the next group and level 1 of the one
+  // after it are in flight.  The loop is written as two halves so that each
+  // stage keeps its own registers (no copies of values still being loaded).
+  int64_t b = ((int64_t)blockIdx.x * NW + w) * G;
+  Pre1 p1a = load1(b), p1b = load1(b + stride);
+  Pre2 p2a = load2(b, p1a), p2b;
+  while (b < n) {
+    p2b = load2(b + stride, p1b);
+    {
+      const Pre1 cur = p1a;
+      p1a = load1(b + 2 * stride);
+      process(b, cur, p2a);
+    }
+    b += stride;
+    if (b >= n) break;
+    p2a = load2(b + stride, p1a);
+    {
+      const Pre1 cur = p1b;
+      p1b = load1(b + 2 * stride);
+      process(b, cur, p2b);
+    }
+    b += stride;
   }
 }
 
