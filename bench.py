@@ -190,13 +190,17 @@ def peak_hbm():
         return 6800.0, "fallback"
 
 
-def csrc_hash() -> str:
+SORT_KERNEL_SOURCES = ("kernels_sort.cu", "sort_accum.cuh", "common.cuh", "internal.h")
+
+
+def csrc_hash(files=SORT_KERNEL_SOURCES) -> str:
+    """Hash of the sources that define the profiled kernel (not of the host
+    orchestration), so a stored ncu figure is used only for that code."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2501_07056_gb300", "csrc")
-    for fn in sorted(os.listdir(d)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(d, fn), "rb") as f:
-                h.update(fn.encode() + b"\0" + f.read())
+    for fn in files:
+        with open(os.path.join(d, fn), "rb") as f:
+            h.update(fn.encode() + b"\0" + f.read())
     return h.hexdigest()[:16]
 
 

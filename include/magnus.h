@@ -98,10 +98,12 @@ typedef struct {
  * max_scratch_bytes   upper bound on the reorder staging buffer of one batch
  *                     (Section 3.3 batching); 0 = automatic (a fraction of
  *                     the free device memory at plan time).
- * l2_fetch_bytes      L2 fetch granularity hint (cudaLimitMaxL2FetchGranularity)
- *                     applied while magnus_symbolic / magnus_numeric enqueue
- *                     work and restored before they return (32, 64 or 128);
- *                     0 = leave the process setting alone.                   */
+ * l2_fetch_bytes      L2 fetch granularity (cudaLimitMaxL2FetchGranularity,
+ *                     32, 64 or 128 bytes) set once by magnus_plan for the
+ *                     calling process and left in place (the limit is a
+ *                     property of the CUDA context, not of the GPU).  32 stops
+ *                     the gathers of short B rows from pulling whole 128-byte
+ *                     lines; 0 = leave the process setting alone.            */
 typedef struct {
   int32_t sort_threshold;
   int32_t force_category;

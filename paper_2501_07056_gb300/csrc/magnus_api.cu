@@ -224,27 +224,6 @@ void ensure_pool_retains(int dev) {
   done[dev] = true;
 }
 
-// Applies the plan's L2 fetch granularity hint for the duration of a call.
-struct FetchGranularity {
-  bool active = false;
-  size_t prev = 0;
-  explicit FetchGranularity(int bytes) {
-    if (bytes <= 0) return;
-    if (cudaDeviceGetLimit(&prev, cudaLimitMaxL2FetchGranularity) != cudaSuccess) {
-      cudaGetLastError();
-      return;
-    }
-    const size_t want = (size_t)bytes;
-    if (want != prev && cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, want) == cudaSuccess)
-      active = true;
-    else
-      cudaGetLastError();
-  }
-  ~FetchGranularity() {
-    if (active) cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, prev);
-  }
-};
-
 struct StageTimer {
   magnus_plan_t p;
   int stage;
@@ -343,6 +322,15 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
   if (params) pl->params = *params; else magnus_params_default(&pl->params);
   const magnus_params_t& P = pl->params;
   if (P.force_category < -1 || P.force_category > 3) return MAGNUS_INVALID_ARG;
+  if (P.l2_fetch_bytes != 0 && P.l2_fetch_bytes != 32 && P.l2_fetch_bytes != 64 &&
+      P.l2_fetch_bytes != 128)
+    return MAGNUS_INVALID_ARG;
+  if (P.l2_fetch_bytes > 0) {
+    size_t cur = 0;
+    CUDA_TRY(cudaDeviceGetLimit(&cur, cudaLimitMaxL2FetchGranularity));
+    if (cur != (size_t)P.l2_fetch_bytes)
+      CUDA_TRY(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)P.l2_fetch_bytes));
+  }
   if (P.sort_threshold < 0 || P.sort_threshold > SORT_MAX + 1) return MAGNUS_INVALID_ARG;
   pl->sort_T = P.sort_threshold > 0 ? P.sort_threshold : 256;
   const int64_t m_c = B->n_cols > 0 ? B->n_cols : 1;
@@ -724,7 +712,6 @@ int magnus_symbolic(magnus_plan_t pl, int64_t* c_row_ptr, int64_t* nnz_c, void* 
   pl->symbolic_done = false;
   for (int i = 0; i < MAGNUS_STAGE_COUNT; ++i) pl->ev_used[i] = false;
   const int64_t n = pl->A.n_rows;
-  FetchGranularity fg(pl->params.l2_fetch_bytes);
   CUDA_TRY(cudaMemsetAsync(c_row_ptr, 0, (size_t)(n + 1) * sizeof(int64_t), s));
   MAG_TRY(run_phase(pl, false, c_row_ptr, nullptr, nullptr, nullptr, s));
   {
@@ -754,7 +741,6 @@ int magnus_numeric(magnus_plan_t pl, const double* a_val, const double* b_val,
   for (int i = MAGNUS_STAGE_NUM_SORT; i < MAGNUS_STAGE_COUNT; ++i) pl->ev_used[i] = false;
   pl->A.val = a_val;
   pl->B.val = b_val;
-  FetchGranularity fg(pl->params.l2_fetch_bytes);
   return run_phase(pl, true, nullptr, c_row_ptr, c_col, c_val, s);
 }
 
