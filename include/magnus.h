@@ -49,7 +49,8 @@ enum magnus_status {
   MAGNUS_CUDA_ERROR = 5,         /* a CUDA runtime call failed; see magnus_last_cuda_error() */
   MAGNUS_TIMEOUT = 6,            /* a bounded device-side wait expired (reserved) */
   MAGNUS_NOT_SYMBOLIC = 7,       /* magnus_numeric called before magnus_symbolic on this plan */
-  MAGNUS_BAD_STATE = 8           /* the plan was built for other inputs or is unusable */
+  MAGNUS_BAD_STATE = 8,          /* the plan was built for other inputs or is unusable */
+  MAGNUS_SCRATCH_LIMIT = 9       /* magnus_numeric_noalloc: the fixed staging buffer is too small */
 };
 
 /* ---- row categories (Section 3.1) ------------------------------------- */
@@ -152,6 +153,34 @@ int magnus_symbolic(magnus_plan_t plan, int64_t* c_row_ptr, int64_t* nnz_c, void
  * magnus_symbolic has not completed on this plan. */
 int magnus_numeric(magnus_plan_t plan, const double* a_val, const double* b_val,
                    const int64_t* c_row_ptr, int32_t* c_col, double* c_val, void* stream);
+
+/* magnus_numeric_noalloc - the numeric phase without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate device memory once they are running, for example a solver that
+ * multiplies the same structure with new values every iteration inside a
+ * framework whose allocator owns the whole device (a cudaMalloc from a library
+ * would exceed its budget or fragment its pool), or a loop that must not let
+ * cudaMalloc/cudaFree synchronise the device.  magnus_plan and magnus_symbolic
+ * still allocate; run them during set-up.
+ *
+ * Arguments, results and tolerance are those of magnus_numeric.  The staging
+ * buffers of the fine-level reorder (12 bytes per product of the largest
+ * fine-row batch that needs a reorder) come from one static device array of
+ * MAGNUS_NOALLOC_SCRATCH_BYTES, which every GPU that loads this library holds
+ * until the process exits.  Plans whose batches need more, or that contain
+ * coarse rows (force_category or very wide C), are rejected with
+ * MAGNUS_SCRATCH_LIMIT before any work is enqueued; building the plan with
+ * max_scratch_bytes <= MAGNUS_NOALLOC_SCRATCH_BYTES keeps batches small enough.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * All calls share the one array: calls that may overlap on the GPU (other
+ * streams, other host threads) race on it and must be serialised by the
+ * caller.  Nothing in it needs to start at zero (every staged entry is
+ * written before it is read). */
+#define MAGNUS_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+int magnus_numeric_noalloc(magnus_plan_t plan, const double* a_val, const double* b_val,
+                           const int64_t* c_row_ptr, int32_t* c_col, double* c_val,
+                           void* stream);
 
 /* Release the plan and all device memory it owns.  Safe on NULL.  Work the
  * plan enqueued must be complete or ordered before any reuse of that memory

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -290,6 +291,9 @@ const char* magnus_strerror(int s) {
     case MAGNUS_TIMEOUT: return "device wait timed out";
     case MAGNUS_NOT_SYMBOLIC: return "numeric called before symbolic";
     case MAGNUS_BAD_STATE: return "plan in a bad state";
+    case MAGNUS_SCRATCH_LIMIT:
+      return "the allocation-free numeric entry point needs more staging than its fixed buffer "
+             "(MAGNUS_NOALLOC_SCRATCH_BYTES) holds, or the plan has coarse rows";
     default: return "unknown status";
   }
 }
@@ -742,6 +746,107 @@ int magnus_numeric(magnus_plan_t pl, const double* a_val, const double* b_val,
   pl->A.val = a_val;
   pl->B.val = b_val;
   return run_phase(pl, true, nullptr, c_row_ptr, c_col, c_val, s);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free numeric phase: the fine-level staging lives in this static
+// device array instead of the stream-ordered pool.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MAGNUS_NOALLOC_SCRATCH_BYTES];
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (host code may not use the symbol itself as a device pointer).
+static int noalloc_scratch_address(unsigned char** out) {
+  static std::mutex mu;
+  static void* addr[128] = {};
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 128) return MAGNUS_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e,
+                                                  "cudaGetSymbolAddress(g_noalloc_scratch)");
+    addr[dev] = p;
+  }
+  *out = reinterpret_cast<unsigned char*>(addr[dev]);
+  return MAGNUS_OK;
+}
+
+int magnus_numeric_noalloc(magnus_plan_t pl, const double* a_val, const double* b_val,
+                           const int64_t* c_row_ptr, int32_t* c_col, double* c_val, void* stream) {
+  if (!pl || !c_row_ptr) return MAGNUS_INVALID_ARG;
+  if (!pl->symbolic_done) return MAGNUS_NOT_SYMBOLIC;
+  if ((pl->A.nnz > 0 && !a_val) || (pl->B.nnz > 0 && !b_val)) return MAGNUS_INVALID_ARG;
+  if (pl->nnz_c > 0 && (!c_col || !c_val)) return MAGNUS_INVALID_ARG;
+  if (!pl->coarse_rows.empty()) return MAGNUS_SCRATCH_LIMIT;
+  // staging of the largest fine batch (only rows spanning several chunks reorder)
+  const int shift = pl->shift_fine;
+  const size_t nbat = pl->fine_batches.empty() ? 0 : pl->fine_batches.size() - 1;
+  int64_t need = 0;
+  for (size_t bi = 0; bi < nbat; ++bi)
+    for (int64_t i = pl->fine_batches[bi]; i < pl->fine_batches[bi + 1]; ++i)
+      if ((pl->fine_hi[i] >> shift) - (pl->fine_lo[i] >> shift) + 1 > 1)
+        need = std::max(need, pl->fine_stage_off[i] + pl->fine_P[i]);
+  const size_t col_bytes = (((size_t)need * sizeof(int32_t)) + 255) & ~(size_t)255;
+  if (col_bytes + (size_t)need * sizeof(double) > MAGNUS_NOALLOC_SCRATCH_BYTES)
+    return MAGNUS_SCRATCH_LIMIT;
+  unsigned char* scratch = nullptr;
+  MAG_TRY(noalloc_scratch_address(&scratch));
+  cudaStream_t s = (cudaStream_t)stream;
+  pl->last_stream = s;
+  Csr A = pl->A, B = pl->B;
+  A.val = a_val;
+  B.val = b_val;
+  for (int b = BIN_SORT32; b <= BIN_SORT256; ++b) {
+    SortArgs a{};
+    a.A = A;
+    a.B = B;
+    a.desc = pl->desc + pl->bin_off[b];
+    a.seg_bs = pl->seg_bs;
+    a.seg_len = pl->seg_len;
+    a.n_rows = pl->bin_off[b + 1] - pl->bin_off[b];
+    a.key32 = pl->key32[b];
+    a.perm = pl->perm + pl->perm_off[b];
+    a.c_rp = c_row_ptr;
+    a.c_col = c_col;
+    a.c_val = c_val;
+    CUDA_TRY(launch_sort_rows(b, true, a, pl->num_sms, s));
+  }
+  {
+    DenseArgs a{};
+    a.A = A;
+    a.B = B;
+    a.rows = pl->rows_sorted + pl->bin_off[BIN_DENSE];
+    a.n_rows = pl->bin_off[BIN_DENSE + 1] - pl->bin_off[BIN_DENSE];
+    a.lo = pl->lo;
+    a.hi = pl->hi;
+    a.dense_cols = pl->dense_cols;
+    a.c_rp = c_row_ptr;
+    a.c_col = c_col;
+    a.c_val = c_val;
+    CUDA_TRY(launch_dense_rows(true, a, pl->num_sms, s));
+  }
+  for (size_t bi = 0; bi < nbat; ++bi) {
+    const int64_t r0 = pl->fine_batches[bi], r1 = pl->fine_batches[bi + 1];
+    FineArgs a{};
+    a.A = A;
+    a.B = B;
+    a.rows = pl->fine_rows_d + r0;
+    a.n_rows = r1 - r0;
+    a.stage_off = pl->fine_stage_off_d + r0;
+    a.lo = pl->lo;
+    a.hi = pl->hi;
+    a.shift = shift;
+    a.dense_chunk_threshold = pl->dthr;
+    a.stage_col = reinterpret_cast<int32_t*>(scratch);
+    a.stage_val = reinterpret_cast<double*>(scratch + col_bytes);
+    a.c_rp = c_row_ptr;
+    a.c_col = c_col;
+    a.c_val = c_val;
+    CUDA_TRY(launch_fine_rows(true, a, s));
+  }
+  return MAGNUS_OK;
 }
 
 int magnus_plan_info(magnus_plan_t pl, magnus_plan_info_t* info) {

@@ -82,6 +82,7 @@ SIGNATURES = {
                             ctypes.POINTER(Params), c_p]),
     "magnus_symbolic": (c_i32, [c_p, c_p, ctypes.POINTER(c_i64), c_p]),
     "magnus_numeric": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_p, c_p]),
+    "magnus_numeric_noalloc": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_p, c_p]),
     "magnus_free": (None, [c_p]),
     "magnus_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "magnus_last_cuda_error": (ctypes.c_char_p, []),
@@ -141,6 +142,16 @@ def magnus_numeric(plan: int, a_val: int, b_val: int, c_row_ptr: int, c_col: int
                    stream: int) -> None:
     _check(_lib().magnus_numeric(c_p(plan), c_p(a_val), c_p(b_val), c_p(c_row_ptr), c_p(c_col),
                                  c_p(c_val), c_p(stream)), "magnus_numeric")
+
+
+def magnus_numeric_noalloc(plan: int, a_val: int, b_val: int, c_row_ptr: int, c_col: int,
+                           c_val: int, stream: int) -> None:
+    """Numeric phase that allocates no device memory (staging in the
+    library's fixed static buffer); for callers that may not allocate once
+    running.  Same arguments and results as magnus_numeric."""
+    _check(_lib().magnus_numeric_noalloc(c_p(plan), c_p(a_val), c_p(b_val), c_p(c_row_ptr),
+                                         c_p(c_col), c_p(c_val), c_p(stream)),
+           "magnus_numeric_noalloc")
 
 
 def magnus_free(plan: int) -> None:
