@@ -29,8 +29,10 @@ def _worker(rank, world, port, q):
     d.barrier()
     mx = d.max(10.0 + rank)
     sm = d.sum(1.0 + rank)
-    q.put((rank, mx, sm))
     d.close()
+    q.put((rank, mx, sm))
+    q.close()
+    q.join_thread()
 
 
 def test_dist_reductions_gloo():
