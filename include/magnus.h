@@ -97,8 +97,8 @@ typedef struct {
  * validate            1 = check the input CSR structure on the device in
  *                     magnus_plan (returns MAGNUS_UNSORTED_OR_DUP on failure).
  * max_scratch_bytes   upper bound on the reorder staging buffer of one batch
- *                     (Section 3.3 batching); 0 = automatic (a fraction of
- *                     the free device memory at plan time).
+ *                     (Section 3.3 batching); 0 = automatic (1/8 of the free
+ *                     device memory at plan time, at most 8 GB).
  * l2_fetch_bytes      L2 fetch granularity (cudaLimitMaxL2FetchGranularity,
  *                     32, 64 or 128 bytes) set once by magnus_plan for the
  *                     calling process and left in place (the limit is a

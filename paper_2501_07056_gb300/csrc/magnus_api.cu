@@ -217,9 +217,12 @@ struct Scratch {
 void ensure_pool_retains(int dev) {
   static bool done[64] = {false};
   if (dev < 0 || dev >= 64 || done[dev]) return;
+  // Keep up to 16 GB of freed scratch for reuse by later calls (a plan's
+  // arrays and staging are freed and reallocated every product); larger
+  // transient staging goes back to the device at the next synchronisation.
   cudaMemPool_t pool;
   if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-    uint64_t thr = UINT64_MAX;
+    uint64_t thr = (uint64_t)16 << 30;
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
   }
   done[dev] = true;
@@ -369,7 +372,7 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
   if (P.max_scratch_bytes > 0) {
     pl->scratch_cap = P.max_scratch_bytes;
   } else {
-    pl->scratch_cap = std::min<int64_t>((int64_t)(free_b / 4), (int64_t)32 << 30);
+    pl->scratch_cap = std::min<int64_t>((int64_t)(free_b / 8), (int64_t)8 << 30);
     if (pl->scratch_cap < ((int64_t)64 << 20)) pl->scratch_cap = (int64_t)64 << 20;
   }
 

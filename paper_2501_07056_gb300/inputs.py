@@ -274,7 +274,7 @@ def workload(name: str, seed: int = 0):
     if name == "uniform2^24":
         A = uniform(1 << 24, 1 << 24, 8, seed, 0)
         return A, A
-    if name == "rmat20":
-        A = rmat(20, 16, seed=seed, matrix_id=0)
+    if name.startswith("rmat"):
+        A = rmat(int(name[4:]), 16, seed=seed, matrix_id=0)
         return A, A
     raise KeyError(name)
