@@ -97,8 +97,8 @@ typedef struct {
  * validate            1 = check the input CSR structure on the device in
  *                     magnus_plan (returns MAGNUS_UNSORTED_OR_DUP on failure).
  * max_scratch_bytes   upper bound on the reorder staging buffer of one batch
- *                     (Section 3.3 batching); 0 = automatic (1/8 of the free
- *                     device memory at plan time, at most 8 GB).
+ *                     (Section 3.3 batching); 0 = automatic (1/6 of the free
+ *                     device memory at plan time, at most 16 GB).
  * l2_fetch_bytes      L2 fetch granularity (cudaLimitMaxL2FetchGranularity,
  *                     32, 64 or 128 bytes) set once by magnus_plan for the
  *                     calling process and left in place (the limit is a
@@ -163,20 +163,22 @@ int magnus_numeric(magnus_plan_t plan, const double* a_val, const double* b_val,
  * cudaMalloc/cudaFree synchronise the device.  magnus_plan and magnus_symbolic
  * still allocate; run them during set-up.
  *
- * Arguments, results and tolerance are those of magnus_numeric.  The staging
- * buffers of the fine-level reorder (12 bytes per product of the largest
- * fine-row batch that needs a reorder) come from one static device array of
- * MAGNUS_NOALLOC_SCRATCH_BYTES, which every GPU that loads this library holds
- * until the process exits.  Plans whose batches need more, or that contain
- * coarse rows (force_category or very wide C), are rejected with
- * MAGNUS_SCRATCH_LIMIT before any work is enqueued; building the plan with
- * max_scratch_bytes <= MAGNUS_NOALLOC_SCRATCH_BYTES keeps batches small enough.
+ * Arguments, results and tolerance are those of magnus_numeric.  The fine
+ * level stages one row per thread block in a slab of 12 bytes per product;
+ * here the slabs, and the counter through which blocks take rows, come from
+ * one static device array of MAGNUS_NOALLOC_SCRATCH_BYTES, which every GPU
+ * that loads this library holds until the process exits, and the fine kernel
+ * runs with as many blocks as slabs fit in it.  Plans that contain coarse
+ * rows (force_category, very wide C, or rows with more products than a
+ * slab), or whose slab alone exceeds the array, are rejected with
+ * MAGNUS_SCRATCH_LIMIT before any work is enqueued.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress), so make that first call before any stream capture.
  * All calls share the one array: calls that may overlap on the GPU (other
  * streams, other host threads) race on it and must be serialised by the
- * caller.  Nothing in it needs to start at zero (every staged entry is
- * written before it is read). */
+ * caller.  The row counter is cleared by every call (stream-ordered
+ * cudaMemsetAsync, no allocation); the slabs need no clearing (every staged
+ * entry is written before it is read). */
 #define MAGNUS_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 int magnus_numeric_noalloc(magnus_plan_t plan, const double* a_val, const double* b_val,
                            const int64_t* c_row_ptr, int32_t* c_col, double* c_val,

@@ -1,152 +1,166 @@
-// Fine-level chunk accumulation shared by fine rows and coarse chunks
-// (Algorithm 3 accumulation step with the Section 3.4 hybrid).
+// Fine-level chunk accumulation shared by fine rows and large coarse chunks
+// (Algorithm 3 accumulation step with the Section 3.4 dense accumulator).
+//
+// The staged products of a row (or coarse chunk) are grouped by fine chunk;
+// each warp of the block owns a private dense accumulator of one chunk's
+// columns in shared memory (FP64 values and a bitmap in the numeric phase,
+// the bitmap alone in the symbolic phase).  Warps take consecutive chunks, a
+// round of FNW chunks at a time, so a round needs two block barriers for the
+// prefix of its chunk counts instead of barriers per chunk.  Emission walks
+// the bitmap in column order and resets exactly the entries it touched, as
+// Algorithm 1's output loop resets its bitmap, so the accumulators are clean
+// for the next chunk without clearing the whole array.
 #pragma once
 
 #include "block_accum.cuh"
 
 namespace magnus {
 
-constexpr int FNT = DENSE_NT;
+constexpr int FNT = DENSE_NT;      // threads per block
+constexpr int FNW = FNT / 32;      // warps per block
+constexpr int WARP_ACC_LOG2 = 10;  // numeric: 1024 FP64 columns per warp accumulator
+constexpr int WARP_BITS_LOG2 = 13; // symbolic: 8192 columns per warp bitmap
+constexpr int DIRECT_BITS_LOG2 = 19;  // symbolic: block bitmap for a whole row's range
 
 struct FineSmem {
-  int32_t* cnt;
-  int32_t* off;
-  double* acc;
-  uint32_t* bits;
-  uint64_t* keys;
-  double* vals;
+  int32_t* cnt;     // [FINE_MAX_CHUNKS]     chunk histogram, then reorder cursor
+  int32_t* off;     // [FINE_MAX_CHUNKS + 1] chunk offsets in staging
+  double* acc;      // [FNW << shift]        warp accumulators (numeric)
+  uint32_t* bits;   // [FNW][words]          warp bitmaps
+  int words;        // bitmap words per warp
+  uint32_t* direct; // symbolic: block bitmap of a whole row (aliases the above)
+  int64_t* wcnt;    // [FNW + 1]             chunk counts of the current round
 };
 
-__host__ __device__ inline size_t fine_smem_bytes(bool numeric, int shift, int max_chunks) {
-  const size_t cl = (size_t)1 << shift;
-  size_t b = (size_t)max_chunks * 4 + (size_t)(max_chunks + 1) * 4;
+__host__ __device__ inline int fine_words(int shift) { return shift >= 5 ? (1 << (shift - 5)) : 1; }
+
+// Shared memory of the fine kernels for a chunk shift (numeric: shift <=
+// WARP_ACC_LOG2; symbolic: shift <= WARP_BITS_LOG2).
+__host__ __device__ inline size_t fine_smem_bytes(bool numeric, int shift) {
+  size_t b = (size_t)FINE_MAX_CHUNKS * 4 + (size_t)(FINE_MAX_CHUNKS + 1) * 4;
   b = (b + 15) & ~(size_t)15;
-  if (numeric) b += cl * 8;
-  b += ((cl + 31) / 32) * 4;
+  if (numeric) b += (size_t)FNW * ((size_t)1 << shift) * 8;
+  b += (size_t)FNW * fine_words(shift) * 4;
   b = (b + 15) & ~(size_t)15;
-  b += (size_t)GROUP_SORT_CAP * 8;
-  if (numeric) b += (size_t)GROUP_SORT_CAP * 8;
+  if (!numeric) {
+    const size_t direct = ((size_t)1 << DIRECT_BITS_LOG2) / 8;
+    if (direct > b) b = direct;
+  }
+  b = (b + 15) & ~(size_t)15;
+  b += (FNW + 1) * 8;
   return b;
 }
 
-__device__ inline FineSmem fine_carve(unsigned char* base, bool numeric, int shift, int max_chunks) {
+__device__ inline FineSmem fine_carve(unsigned char* base, bool numeric, int shift) {
   FineSmem f;
-  const size_t cl = (size_t)1 << shift;
   size_t o = 0;
   f.cnt = reinterpret_cast<int32_t*>(base + o);
-  o += (size_t)max_chunks * 4;
+  o += (size_t)FINE_MAX_CHUNKS * 4;
   f.off = reinterpret_cast<int32_t*>(base + o);
-  o += (size_t)(max_chunks + 1) * 4;
+  o += (size_t)(FINE_MAX_CHUNKS + 1) * 4;
   o = (o + 15) & ~(size_t)15;
   f.acc = reinterpret_cast<double*>(base + o);
-  if (numeric) o += cl * 8;
+  if (numeric) o += (size_t)FNW * ((size_t)1 << shift) * 8;
+  f.words = fine_words(shift);
   f.bits = reinterpret_cast<uint32_t*>(base + o);
-  o += ((cl + 31) / 32) * 4;
+  o += (size_t)FNW * f.words * 4;
   o = (o + 15) & ~(size_t)15;
-  f.keys = reinterpret_cast<uint64_t*>(base + o);
-  o += (size_t)GROUP_SORT_CAP * 8;
-  f.vals = reinterpret_cast<double*>(base + o);
+  f.direct = reinterpret_cast<uint32_t*>(base);
+  if (!numeric) {
+    const size_t direct = ((size_t)1 << DIRECT_BITS_LOG2) / 8;
+    if (direct > o) o = direct;
+  }
+  o = (o + 15) & ~(size_t)15;
+  f.wcnt = reinterpret_cast<int64_t*>(base + o);
   return f;
 }
 
-// Accumulates the staged chunks [0, nch) of one row (or one coarse chunk).
-// stage_col/stage_val point at the row's staging region; off[] are the chunk
-// offsets inside it.  Columns in staging are relative to col_base.  Writes
-// sorted unique entries at out_col/out_val[0..) (numeric) and returns the
-// number of distinct columns.  All threads must call.
+// Zeroes every warp accumulator and bitmap (once per block; emission keeps
+// them clean afterwards).  All threads must call; ends with a barrier.
 template <bool NUMERIC>
-__device__ int64_t fine_accumulate_chunks(const FineSmem& f, int nch, int shift, int dthr,
-                                          const int32_t* __restrict__ stage_col,
-                                          const double* __restrict__ stage_val, int64_t col_base,
-                                          int32_t* __restrict__ out_col,
-                                          double* __restrict__ out_val, int64_t* ws) {
+__device__ inline void fine_clear(const FineSmem& f, int shift) {
   const int cl = 1 << shift;
-  const int cl_words = (cl + 31) >> 5;
-  // a chunk below the threshold must fit one sort group
-  if (dthr > GROUP_SORT_CAP) dthr = GROUP_SORT_CAP;
-  if (dthr < 1) dthr = 1;
+  if (NUMERIC)
+    for (int i = threadIdx.x; i < FNW * cl; i += FNT) f.acc[i] = 0.0;
+  for (int i = threadIdx.x; i < FNW * f.words; i += FNT) f.bits[i] = 0u;
+  __syncthreads();
+}
+
+// Accumulates the staged chunks [0, nch): chunk ch holds
+// stage_col/stage_val[off[ch] .. off[ch + 1]), columns relative to col_base
+// (chunk index << shift | column inside the chunk).  Writes the sorted unique
+// entries to out_col/out_val[0..) (numeric) and returns their number.  All
+// threads must call; the warp accumulators must be clean on entry and are
+// clean on exit.
+template <bool NUMERIC>
+__device__ int64_t warp_chunks_accumulate(const FineSmem& f, int nch, int shift,
+                                          const int32_t* __restrict__ stage_col,
+                                          const double* __restrict__ stage_val,
+                                          int64_t col_base, int32_t* __restrict__ out_col,
+                                          double* __restrict__ out_val) {
+  const int lane = lane_id(), w = warp_id();
+  const int cl = 1 << shift;
+  const int words = f.words;
+  double* acc = f.acc + (size_t)w * cl;
+  uint32_t* bits = f.bits + (size_t)w * words;
+  const int wpl = (words + 31) / 32;  // bitmap words per lane, in column order
   int64_t outp = 0;
-  int ch = 0;
-  while (ch < nch) {
-    const int n = f.off[ch + 1] - f.off[ch];
-    if (n == 0) {
-      ++ch;
-      continue;
-    }
-    if (n >= dthr) {
-      // dense accumulator over the chunk's 2^shift columns (Algorithm 1)
-      for (int i = threadIdx.x; i < cl_words; i += FNT) f.bits[i] = 0u;
-      if (NUMERIC)
-        for (int i = threadIdx.x; i < cl; i += FNT) f.acc[i] = 0.0;
-      __syncthreads();
+  for (int r0 = 0; r0 < nch; r0 += FNW) {
+    const int ch = r0 + w;
+    int cnt = 0;
+    if (ch < nch) {
       const int p0 = f.off[ch], p1 = f.off[ch + 1];
-      for (int p = p0 + threadIdx.x; p < p1; p += FNT) {
+      for (int p = p0 + lane; p < p1; p += 32) {
         const int idx = stage_col[p] & (cl - 1);
-        atomicOr(&f.bits[idx >> 5], 1u << (idx & 31));
-        if (NUMERIC) atomicAdd(&f.acc[idx], stage_val[p]);
+        atomicOr(&bits[idx >> 5], 1u << (idx & 31));
+        if (NUMERIC) atomicAdd(&acc[idx], stage_val[p]);
       }
-      __syncthreads();
-      const int64_t cb = col_base + ((int64_t)ch << shift);
-      outp += block_emit_bitmap<FNT, NUMERIC>(f.bits, cl_words, f.acc, cb,
-                                             out_col, out_val, outp, ws);
-      __syncthreads();  // emission reads acc/bits before the next chunk clears them
-      ++ch;
-    } else {
-      // merge consecutive small chunks and sort them together (Algorithm 2)
-      int g = ch;
-      int tot = 0;
-      while (g < nch) {
-        const int m = f.off[g + 1] - f.off[g];
-        if (m >= dthr || tot + m > GROUP_SORT_CAP) break;
-        tot += m;
-        ++g;
+      __syncwarp();
+      for (int k = 0; k < wpl; ++k) {
+        const int wd = lane * wpl + k;
+        if (wd < words) cnt += __popc(bits[wd]);
       }
-      int np2 = 1;
-      while (np2 < tot) np2 <<= 1;
-      const int p0 = f.off[ch];
-      const int32_t rel0 = ch << shift;
-      for (int i = threadIdx.x; i < np2; i += FNT) {
-        if (i < tot) {
-          const int32_t rel = stage_col[p0 + i] - rel0;
-          f.keys[i] = ((uint64_t)(uint32_t)rel << 32) | (uint32_t)i;
-          if (NUMERIC) f.vals[i] = stage_val[p0 + i];
-        } else {
-          f.keys[i] = ~0ull;
-        }
-      }
-      __syncthreads();
-      block_bitonic_sort<FNT>(f.keys, np2);
-      // compress: each thread takes IPT consecutive sorted keys
-      constexpr int IPT = GROUP_SORT_CAP / FNT;
-      int h = 0;
-      bool head[IPT];
-#pragma unroll
-      for (int r = 0; r < IPT; ++r) {
-        const int i = threadIdx.x * IPT + r;
-        head[r] = (i < tot) && (i == 0 || (f.keys[i] >> 32) != (f.keys[i - 1] >> 32));
-        h += head[r] ? 1 : 0;
-      }
-      int64_t gtot;
-      int64_t pos = block_exclusive_scan<FNT>((int64_t)h, ws, &gtot);
-      if (NUMERIC) {
-        const int64_t cb = col_base + rel0;
-#pragma unroll
-        for (int r = 0; r < IPT; ++r) {
-          if (!head[r]) continue;
-          const int i = threadIdx.x * IPT + r;
-          const uint32_t c = (uint32_t)(f.keys[i] >> 32);
-          double acc = f.vals[(uint32_t)f.keys[i]];
-          for (int i2 = i + 1; i2 < tot && (uint32_t)(f.keys[i2] >> 32) == c; ++i2)
-            acc += f.vals[(uint32_t)f.keys[i2]];
-          out_col[outp + pos] = (int32_t)(cb + c);
-          out_val[outp + pos] = acc;
-          ++pos;
-        }
-      }
-      outp += gtot;
-      __syncthreads();
-      ch = g;
     }
+    const int lane_cnt = cnt;
+    cnt = warp_sum(cnt);
+    if (lane == 0) f.wcnt[w] = cnt;
+    __syncthreads();
+    int64_t before = 0, total = 0;
+#pragma unroll
+    for (int i = 0; i < FNW; ++i) {
+      const int64_t c = f.wcnt[i];
+      before += (i < w) ? c : 0;
+      total += c;
+    }
+    if (ch < nch && cnt > 0) {
+      if (NUMERIC) {
+        const int inc = warp_inclusive_scan(lane_cnt);
+        int64_t o = outp + before + inc - lane_cnt;
+        const int64_t cb = col_base + ((int64_t)ch << shift);
+        for (int k = 0; k < wpl; ++k) {
+          const int wd = lane * wpl + k;
+          if (wd >= words) break;
+          uint32_t m = bits[wd];
+          bits[wd] = 0u;
+          while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            const int idx = wd * 32 + b;
+            out_col[o] = (int32_t)(cb + idx);
+            out_val[o] = acc[idx];
+            acc[idx] = 0.0;
+            ++o;
+          }
+        }
+      } else {
+        for (int k = 0; k < wpl; ++k) {
+          const int wd = lane * wpl + k;
+          if (wd < words) bits[wd] = 0u;
+        }
+      }
+    }
+    outp += total;
+    __syncthreads();
   }
   return outp;
 }

@@ -37,6 +37,9 @@ struct CatParams {
   int32_t dense_cols;         // dense iff column range <= dense_cols
   int32_t fine_shift;         // fine chunk = col >> fine_shift (numeric)
   int32_t fine_max_chunks;    // fine iff the row spans <= this many fine chunks
+  int64_t fine_max_products;  // ... and its products fit one block's staging slab
+  int32_t prefer_fine;        // automatic mode: fine level (1) or coarse level (0) for
+                              // rows wider than the dense accumulator
 };
 
 struct Csr {
@@ -112,12 +115,16 @@ struct DenseArgs {
 };
 cudaError_t launch_dense_rows(bool numeric, const DenseArgs& a, int num_sms, cudaStream_t s);
 
-// Fine rows (block per row, products staged in global scratch).
+// Fine rows: a persistent grid whose blocks take rows (heaviest first) from
+// a device counter; each block stages its current row in its own slab of
+// slab_elems products (stage_col/stage_val + blockIdx.x * slab_elems).
 struct FineArgs {
   Csr A, B;
-  const int32_t* rows;      // rows of this batch
+  const int32_t* rows;      // fine rows, heaviest first
   int64_t n_rows;
-  const int64_t* stage_off; // per batch row: offset into the staging buffers
+  int64_t slab_elems;       // staging capacity per block (products)
+  int32_t* queue;           // zeroed counter of taken rows
+  const int64_t* row_products;  // P of each listed row
   const int32_t* lo;
   const int32_t* hi;
   int32_t shift;            // fine chunk shift for this phase
@@ -129,7 +136,9 @@ struct FineArgs {
   int32_t* c_col;
   double* c_val;
 };
-cudaError_t launch_fine_rows(bool numeric, const FineArgs& a, cudaStream_t s);
+cudaError_t launch_fine_rows(bool numeric, const FineArgs& a, int grid, cudaStream_t s);
+// Resident blocks per SM of the fine-row kernel for a phase and chunk shift.
+int fine_rows_blocks_per_sm(bool numeric, int shift);
 
 // Coarse level (Algorithm 4) for one batch of coarse rows.
 struct CoarseArgs {
@@ -146,6 +155,7 @@ struct CoarseArgs {
   int64_t* col_ptr;          // n_B + 1
   int32_t* csc_row;          // nnz of the batch rows
   double* csc_val;
+  int64_t* item_off;         // n_B + 1: outer-product work items per B row, then offsets
   int32_t* rows_b;           // coarseRowsB list
   int32_t* n_rows_b;         // device counter
   int64_t* counts;           // n_rows * n_chunks + 1 (becomes offsetsCoarse)

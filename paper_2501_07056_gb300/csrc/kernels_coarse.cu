@@ -52,55 +52,79 @@ __global__ void k_csc_fill(Csr A, const int32_t* __restrict__ rows, int64_t nb,
   }
 }
 
-// Outer-product traversal.  Warp per B row of coarseRowsB; the lanes hold 32
-// consecutive entries of the B row and loop over the A^CSC column of that B
-// row.  Lanes hitting the same (row, chunk) are combined with match_any so
-// one atomic serves them all.
+// Outer-product traversal, load balanced.  The work of B row b is
+// nnz(B_b) x nnz(column b of A^CSC) products; it is cut into items of
+// 32 consecutive entries of the B row times OUTER_ET consecutive entries of
+// the A^CSC column (at most 1024 products), and every warp takes an equal
+// contiguous range of items.  Lanes hold one entry of the B row each and
+// reuse it for every A^CSC entry of the item; lanes hitting the same
+// (row, chunk) are combined with match_any so one atomic serves them all.
+constexpr int OUTER_ET = 32;
+
+__global__ void k_outer_items(const int64_t* __restrict__ b_rp, const int64_t* __restrict__ col_ptr,
+                              int64_t nB, int64_t* __restrict__ items) {
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nB;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t L = b_rp[b + 1] - b_rp[b];
+    const int64_t C = col_ptr[b + 1] - col_ptr[b];
+    items[b] = (L > 0 && C > 0) ? ((L + 31) / 32) * ((C + OUTER_ET - 1) / OUTER_ET) : 0;
+  }
+}
+
 template <bool REORDER, bool NUMERIC>
-__global__ void k_coarse_outer(Csr B, const int32_t* __restrict__ rows_b,
-                               const int32_t* __restrict__ n_rows_b,
+__global__ void k_coarse_outer(Csr B, const int64_t* __restrict__ item_off, int64_t nB,
                                const int64_t* __restrict__ col_ptr,
                                const int32_t* __restrict__ csc_row,
                                const double* __restrict__ csc_val, int sc, int nc,
                                int64_t* __restrict__ counts, int32_t* __restrict__ cursor,
                                int32_t* __restrict__ chunk_col, double* __restrict__ chunk_val) {
   const int lane = lane_id();
-  const int nrb = *n_rows_b;
-  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nrb; w += nw) {
-    const int32_t b = rows_b[w];
+  const int64_t total = item_off[nB];
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t per = (total + nwarps - 1) / nwarps;
+  int64_t it = wid * per;
+  const int64_t it_end = (it + per < total) ? it + per : total;
+  if (it >= it_end) return;
+  int64_t b = upper_bound_i64(item_off, (int)(nB + 1), it) - 1;
+  while (it < it_end) {
+    if (item_off[b + 1] <= it) b = upper_bound_i64(item_off, (int)(nB + 1), it) - 1;
     const int64_t bs = B.rp[b];
     const int64_t L = B.rp[b + 1] - bs;
-    const int64_t cs = col_ptr[b], ce = col_ptr[b + 1];
-    for (int64_t k0 = 0; k0 < L; k0 += 32) {
-      const int64_t k = k0 + lane;
-      const bool valid = k < L;
-      const int32_t col = valid ? B.col[bs + k] : 0;
-      const double bv = (NUMERIC && valid) ? B.val[bs + k] : 0.0;
-      const int chunk = col >> sc;
-      const unsigned active = __ballot_sync(FULL, valid);
-      for (int64_t e = cs; e < ce; ++e) {
-        const int32_t t = csc_row[e];
-        const double av = NUMERIC ? csc_val[e] : 0.0;
-        if (valid) {
-          const int64_t slot = (int64_t)t * nc + chunk;
-          const unsigned m = __match_any_sync(active, chunk);
-          const int leader = __ffs(m) - 1;
-          if (!REORDER) {
-            if (lane == leader)
-              atomicAdd(reinterpret_cast<unsigned long long*>(&counts[slot]),
-                        (unsigned long long)__popc(m));
-          } else {
-            int base = 0;
-            if (lane == leader) base = atomicAdd(&cursor[slot], __popc(m));
-            base = __shfl_sync(m, base, leader);
-            const int64_t pos = counts[slot] + base + __popc(m & ((1u << lane) - 1));
-            st_stream(&chunk_col[pos], col - (chunk << sc));
-            if (NUMERIC) st_stream(&chunk_val[pos], av * bv);
-          }
+    const int64_t cs = col_ptr[b], C = col_ptr[b + 1] - cs;
+    const int64_t EB = (L + 31) / 32;
+    const int64_t li = it - item_off[b];
+    const int64_t et = li / EB, eb = li - et * EB;
+    const int64_t k = eb * 32 + lane;
+    const bool valid = k < L;
+    const int32_t col = valid ? B.col[bs + k] : 0;
+    const double bv = (NUMERIC && valid) ? B.val[bs + k] : 0.0;
+    const int chunk = col >> sc;
+    const unsigned active = __ballot_sync(FULL, valid);
+    const int64_t e0 = cs + et * OUTER_ET;
+    const int64_t e1 = (e0 + OUTER_ET < cs + C) ? e0 + OUTER_ET : cs + C;
+    for (int64_t e = e0; e < e1; ++e) {
+      const int32_t t = csc_row[e];
+      const double av = NUMERIC ? csc_val[e] : 0.0;
+      if (valid) {
+        const int64_t slot = (int64_t)t * nc + chunk;
+        const unsigned m = __match_any_sync(active, chunk);
+        const int leader = __ffs(m) - 1;
+        if (!REORDER) {
+          if (lane == leader)
+            atomicAdd(reinterpret_cast<unsigned long long*>(&counts[slot]),
+                      (unsigned long long)__popc(m));
+        } else {
+          int base = 0;
+          if (lane == leader) base = atomicAdd(&cursor[slot], __popc(m));
+          base = __shfl_sync(m, base, leader);
+          const int64_t pos = counts[slot] + base + __popc(m & ((1u << lane) - 1));
+          st_stream(&chunk_col[pos], col - (chunk << sc));
+          if (NUMERIC) st_stream(&chunk_val[pos], av * bv);
         }
       }
     }
+    ++it;
   }
 }
 
@@ -206,23 +230,26 @@ __global__ void __launch_bounds__(BK_NW * 32)
 }
 
 // Large coarse chunks: one block runs the fine level (Algorithm 3) on the
-// chunk's staged products, reordering into the second staging buffer.
+// chunk's staged products: histogram and reorder into the second staging
+// buffer by fine chunk, then warp-private dense accumulation.  The fine
+// shift is min(sc, sf) (the launch sizes shared memory with it).
 template <bool NUMERIC>
 __global__ void __launch_bounds__(FNT)
     k_bucket_big(const int64_t* __restrict__ offs, const int32_t* __restrict__ big_list,
                  const int32_t* __restrict__ n_big, const int32_t* __restrict__ chunk_col,
                  const double* __restrict__ chunk_val, int32_t* __restrict__ fine_col,
-                 double* __restrict__ fine_val, int sc, int sf, int nc, int dthr,
+                 double* __restrict__ fine_val, int sc, int sf, int nc,
                  int64_t list_base, const int32_t* __restrict__ rows,
                  int32_t* __restrict__ bucket_cnt, const int64_t* __restrict__ bucket_out,
                  const int64_t* __restrict__ c_rp, int32_t* __restrict__ c_col,
                  double* __restrict__ c_val) {
   extern __shared__ __align__(16) unsigned char fsm[];
-  const int shift = sf < sc ? sf : sc;  // the launch sizes shared memory with this shift
-  const FineSmem f = fine_carve(fsm, NUMERIC, shift, FINE_MAX_CHUNKS);
+  const int shift = sf < sc ? sf : sc;
+  const FineSmem f = fine_carve(fsm, NUMERIC, shift);
   __shared__ int64_t ws[FNT / 32 + 1];
   const int nbig = *n_big;
   const int nch = 1 << (sc - shift);
+  fine_clear<NUMERIC>(f, shift);
   for (int q = blockIdx.x; q < nbig; q += gridDim.x) {
     const int64_t id = big_list[q];
     const int64_t p0 = offs[id];
@@ -239,38 +266,117 @@ __global__ void __launch_bounds__(FNT)
     }
     const int32_t* cc = chunk_col + p0;
     const double* cv = NUMERIC ? chunk_val + p0 : nullptr;
-    // histogram over fine chunks of the coarse chunk
-    for (int i = threadIdx.x; i < nch; i += FNT) f.cnt[i] = 0;
-    __syncthreads();
-    for (int p = threadIdx.x; p < n; p += FNT) atomicAdd(&f.cnt[cc[p] >> shift], 1);
-    __syncthreads();
-    int32_t run = 0;
-    for (int i0 = 0; i0 < nch; i0 += FNT) {
-      const int i = i0 + threadIdx.x;
-      const int64_t v = (i < nch) ? f.cnt[i] : 0;
-      int64_t tot;
-      const int64_t ex = block_exclusive_scan<FNT>(v, ws, &tot);
-      if (i < nch) {
-        f.off[i] = run + (int32_t)ex;
-        f.cnt[i] = 0;
+    int64_t cnt;
+    if (nch == 1) {
+      if (threadIdx.x == 0) {
+        f.off[0] = 0;
+        f.off[1] = n;
       }
-      run += (int32_t)tot;
+      __syncthreads();
+      cnt = warp_chunks_accumulate<NUMERIC>(f, 1, shift, cc, cv, col_base, oc, ov);
+    } else {
+      // histogram over the fine chunks of the coarse chunk
+      for (int i = threadIdx.x; i < nch; i += FNT) f.cnt[i] = 0;
+      __syncthreads();
+      for (int p = threadIdx.x; p < n; p += FNT) atomicAdd(&f.cnt[cc[p] >> shift], 1);
+      __syncthreads();
+      int32_t run = 0;
+      for (int i0 = 0; i0 < nch; i0 += FNT) {
+        const int i = i0 + threadIdx.x;
+        const int64_t v = (i < nch) ? f.cnt[i] : 0;
+        int64_t tot;
+        const int64_t ex = block_exclusive_scan<FNT>(v, ws, &tot);
+        if (i < nch) {
+          f.off[i] = run + (int32_t)ex;
+          f.cnt[i] = 0;
+        }
+        run += (int32_t)tot;
+      }
+      if (threadIdx.x == 0) f.off[nch] = run;
+      __syncthreads();
+      int32_t* fc = fine_col + p0;
+      double* fv = NUMERIC ? fine_val + p0 : nullptr;
+      for (int p = threadIdx.x; p < n; p += FNT) {
+        const int32_t col = cc[p];
+        const int ch = col >> shift;
+        const int pos = f.off[ch] + atomicAdd(&f.cnt[ch], 1);
+        st_stream(&fc[pos], col);
+        if (NUMERIC) st_stream(&fv[pos], cv[p]);
+      }
+      __syncthreads();
+      cnt = warp_chunks_accumulate<NUMERIC>(f, nch, shift, fc, fv, col_base, oc, ov);
     }
-    if (threadIdx.x == 0) f.off[nch] = run;
-    __syncthreads();
-    int32_t* fc = fine_col + p0;
-    double* fv = NUMERIC ? fine_val + p0 : nullptr;
-    for (int p = threadIdx.x; p < n; p += FNT) {
-      const int32_t col = cc[p];
-      const int ch = col >> shift;
-      const int pos = f.off[ch] + atomicAdd(&f.cnt[ch], 1);
-      st_stream(&fc[pos], col);
-      if (NUMERIC) st_stream(&fv[pos], cv[p]);
-    }
-    __syncthreads();
-    const int64_t cnt = fine_accumulate_chunks<NUMERIC>(f, nch, shift, dthr, fc, fv, col_base,
-                                                        oc, ov, ws);
     if (!NUMERIC && threadIdx.x == 0) bucket_cnt[(list_base + t) * nc + c] = (int32_t)cnt;
+    __syncthreads();
+  }
+}
+
+// Large coarse chunks whose column range (2^sc <= 2^13) fits one block's
+// dense accumulator: Algorithm 1 straight from the coarse staging, with no
+// second reorder.  FP64 values and the bitmap live in shared memory; emission
+// scans the bitmap in column order and clears exactly what it touched.
+constexpr int BUCKET_DENSE_LOG2 = 13;
+
+template <bool NUMERIC>
+__global__ void __launch_bounds__(FNT)
+    k_bucket_dense(const int64_t* __restrict__ offs, const int32_t* __restrict__ big_list,
+                   const int32_t* __restrict__ n_big, const int32_t* __restrict__ chunk_col,
+                   const double* __restrict__ chunk_val, int sc, int nc, int64_t list_base,
+                   const int32_t* __restrict__ rows, int32_t* __restrict__ bucket_cnt,
+                   const int64_t* __restrict__ bucket_out, const int64_t* __restrict__ c_rp,
+                   int32_t* __restrict__ c_col, double* __restrict__ c_val) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  const int cl = 1 << sc;
+  const int words = cl >= 32 ? cl >> 5 : 1;
+  double* acc = reinterpret_cast<double*>(dsm);
+  uint32_t* bits = reinterpret_cast<uint32_t*>(dsm + (NUMERIC ? (size_t)cl * 8 : 0));
+  __shared__ int64_t ws[FNT / 32 + 1];
+  if (NUMERIC)
+    for (int i = threadIdx.x; i < cl; i += FNT) acc[i] = 0.0;
+  for (int i = threadIdx.x; i < words; i += FNT) bits[i] = 0u;
+  __syncthreads();
+  const int nbig = *n_big;
+  for (int q = blockIdx.x; q < nbig; q += gridDim.x) {
+    const int64_t id = big_list[q];
+    const int64_t p0 = offs[id];
+    const int n = (int)(offs[id + 1] - p0);
+    const int64_t t = id / nc;
+    const int c = (int)(id - t * nc);
+    const int32_t* cc = chunk_col + p0;
+    const double* cv = NUMERIC ? chunk_val + p0 : nullptr;
+    for (int p = threadIdx.x; p < n; p += FNT) {
+      const int idx = cc[p];
+      atomicOr(&bits[idx >> 5], 1u << (idx & 31));
+      if (NUMERIC) atomicAdd(&acc[idx], cv[p]);
+    }
+    __syncthreads();
+    int64_t o0 = 0;
+    if (NUMERIC) o0 = c_rp[rows[t]] + bucket_out[id];
+    const int64_t col_base = (int64_t)c << sc;
+    int64_t total = 0;
+    for (int w0 = 0; w0 < words; w0 += FNT) {
+      const int wd = w0 + threadIdx.x;
+      uint32_t m = (wd < words) ? bits[wd] : 0u;
+      int64_t tot;
+      int64_t pos = block_exclusive_scan<FNT>((int64_t)__popc(m), ws, &tot);
+      if (wd < words && m) {
+        bits[wd] = 0u;
+        if (NUMERIC) {
+          int64_t o = o0 + total + pos;
+          while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            const int idx = wd * 32 + b;
+            c_col[o] = (int32_t)(col_base + idx);
+            c_val[o] = acc[idx];
+            acc[idx] = 0.0;
+            ++o;
+          }
+        }
+      }
+      total += tot;
+    }
+    if (!NUMERIC && threadIdx.x == 0) bucket_cnt[(list_base + t) * nc + c] = (int32_t)total;
     __syncthreads();
   }
 }
@@ -295,10 +401,15 @@ static cudaError_t coarse_impl(CoarseArgs& a, cudaStream_t s) {
                                         a.csc_val);
   count_launch();
   CK(cudaGetLastError());
-  // 2. histogram
+  // 2. histogram over balanced work items of the outer product
+  k_outer_items<<<grid_cap_c((nB + 255) / 256, (int64_t)a.num_sms * 32), nt, 0, s>>>(
+      a.B.rp, a.col_ptr, nB, a.item_off);
+  count_launch();
+  CK(cudaGetLastError());
+  CK(launch_exclusive_scan_i64(a.item_off, nB, a.scan_tmp, s));
   CK(cudaMemsetAsync(a.counts, 0, (size_t)(nbk + 1) * sizeof(int64_t), s));
   const unsigned go = (unsigned)a.num_sms * 16;
-  k_coarse_outer<false, false><<<go, nt, 0, s>>>(a.B, a.rows_b, a.n_rows_b, a.col_ptr, a.csc_row,
+  k_coarse_outer<false, false><<<go, nt, 0, s>>>(a.B, a.item_off, nB, a.col_ptr, a.csc_row,
                                                  a.csc_val, a.shift_coarse, a.n_chunks, a.counts,
                                                  a.cursor, a.chunk_col, a.chunk_val);
   count_launch();
@@ -307,7 +418,7 @@ static cudaError_t coarse_impl(CoarseArgs& a, cudaStream_t s) {
   CK(launch_exclusive_scan_i64(a.counts, nbk, a.scan_tmp, s));
   // 4. reorder
   CK(cudaMemsetAsync(a.cursor, 0, (size_t)nbk * sizeof(int32_t), s));
-  k_coarse_outer<true, NUMERIC><<<go, nt, 0, s>>>(a.B, a.rows_b, a.n_rows_b, a.col_ptr, a.csc_row,
+  k_coarse_outer<true, NUMERIC><<<go, nt, 0, s>>>(a.B, a.item_off, nB, a.col_ptr, a.csc_row,
                                                   a.csc_val, a.shift_coarse, a.n_chunks, a.counts,
                                                   a.cursor, a.chunk_col, a.chunk_val);
   count_launch();
@@ -332,13 +443,25 @@ static cudaError_t coarse_impl(CoarseArgs& a, cudaStream_t s) {
         a.bucket_cnt, a.bucket_out, a.c_rp, a.c_col, a.c_val, a.big_list, a.n_big);
   count_launch();
   CK(cudaGetLastError());
-  const size_t smem = fine_smem_bytes(NUMERIC, a.shift_fine < a.shift_coarse ? a.shift_fine : a.shift_coarse,
-                                      FINE_MAX_CHUNKS);
-  CK(cudaFuncSetAttribute(k_bucket_big<NUMERIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_bucket_big<NUMERIC><<<(unsigned)a.num_sms * 2, FNT, smem, s>>>(
-      a.counts, a.big_list, a.n_big, a.chunk_col, a.chunk_val, a.fine_col, a.fine_val,
-      a.shift_coarse, a.shift_fine, a.n_chunks, a.dense_chunk_threshold, a.list_base, a.rows,
-      a.bucket_cnt, a.bucket_out, a.c_rp, a.c_col, a.c_val);
+  if (a.shift_coarse <= BUCKET_DENSE_LOG2) {
+    const size_t cl = (size_t)1 << a.shift_coarse;
+    const size_t smem = (NUMERIC ? cl * 8 : 0) + (cl >= 32 ? cl / 8 : 4);
+    CK(cudaFuncSetAttribute(k_bucket_dense<NUMERIC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)smem));
+    int per_sm = 1;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bucket_dense<NUMERIC>, FNT, smem));
+    if (per_sm < 1) per_sm = 1;
+    k_bucket_dense<NUMERIC><<<(unsigned)(a.num_sms * per_sm), FNT, smem, s>>>(
+        a.counts, a.big_list, a.n_big, a.chunk_col, a.chunk_val, a.shift_coarse, a.n_chunks,
+        a.list_base, a.rows, a.bucket_cnt, a.bucket_out, a.c_rp, a.c_col, a.c_val);
+  } else {
+    const size_t smem = fine_smem_bytes(NUMERIC, a.shift_fine < a.shift_coarse ? a.shift_fine : a.shift_coarse);
+    CK(cudaFuncSetAttribute(k_bucket_big<NUMERIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_bucket_big<NUMERIC><<<(unsigned)a.num_sms * 2, FNT, smem, s>>>(
+        a.counts, a.big_list, a.n_big, a.chunk_col, a.chunk_val, a.fine_col, a.fine_val,
+        a.shift_coarse, a.shift_fine, a.n_chunks, a.list_base, a.rows,
+        a.bucket_cnt, a.bucket_out, a.c_rp, a.c_col, a.c_val);
+  }
   count_launch();
   CK(cudaGetLastError());
   if (!NUMERIC) {

@@ -61,94 +61,123 @@ cudaError_t launch_dense_rows(bool numeric, const DenseArgs& a, int num_sms, cud
 }
 
 // ---------------------------------------------------------------------------
-// Fine level (Algorithm 3) for one row per block.
-//   histogram:   counts of products per fine chunk (col >> shift)
-//   prefix sum:  chunk offsets (offsetsFine, n_chunks + 1 entries)
-//   reorder:     products written to the staging buffers at
-//                offset[chunk] + running count, with the column made
-//                relative to the row's first chunk (chunk-local column plus
-//                chunk index << shift, so merged chunks sort without a search)
-//   accumulate:  chunks in ascending order; a chunk with at least
-//                dense_chunk_threshold products uses the dense accumulator
-//                over its 2^shift columns, otherwise consecutive small chunks
-//                are merged (up to GROUP_SORT_CAP products) and sorted
-//                together (Section 3.4 hybrid; Section 4.1.1 chunk merging).
-// A row spanning a single chunk is accumulated directly, without reorder.
+// Fine level (Algorithm 3), one row per block at a time; a persistent grid
+// whose blocks take rows (heaviest first) from a device counter.
+//   histogram:   products per fine chunk (col >> shift), in shared memory
+//   prefix sum:  chunk offsets (n_chunks + 1 entries)
+//   reorder:     products written to the block's staging slab at
+//                offset[chunk] + running count; columns are kept relative to
+//                the row's first chunk (chunk << shift | column in chunk)
+//   accumulate:  warp-private dense accumulators, one chunk per warp
+//                (warp_chunks_accumulate), chunks emitted in column order.
+// Symbolic phase: a row dense enough for one block bitmap over its whole
+// column range (range <= 2^19, range / 32 <= 4 * P) is counted directly from
+// A and B without a reorder; other rows take the chunked path with bitmaps
+// only.
 template <bool NUMERIC>
 __global__ void __launch_bounds__(NT) k_fine_rows(FineArgs a) {
   extern __shared__ __align__(16) unsigned char fsm[];
-  const FineSmem f = fine_carve(fsm, NUMERIC, a.shift, FINE_MAX_CHUNKS);
+  const FineSmem f = fine_carve(fsm, NUMERIC, a.shift);
   __shared__ TileSmem<NT> ts;
-  const int cl = 1 << a.shift;
-  for (int64_t t = blockIdx.x; t < a.n_rows; t += gridDim.x) {
+  __shared__ int64_t s_next;
+  int32_t* const slab_col = a.stage_col ? a.stage_col + (int64_t)blockIdx.x * a.slab_elems : nullptr;
+  double* const slab_val = a.stage_val ? a.stage_val + (int64_t)blockIdx.x * a.slab_elems : nullptr;
+  fine_clear<NUMERIC>(f, a.shift);
+  for (;;) {
+    // rows are listed heaviest first; blocks take the next one when free
+    if (threadIdx.x == 0) s_next = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int64_t t = s_next;
+    __syncthreads();
+    if (t >= a.n_rows) break;
     const int32_t row = a.rows[t];
     const int32_t lo = a.lo[row], hi = a.hi[row];
+    const int64_t as = a.A.rp[row], ae = a.A.rp[row + 1];
+    if (!NUMERIC) {
+      const int64_t range = (int64_t)hi - lo + 1;
+      const int64_t words = (range + 31) >> 5;
+      if (range <= ((int64_t)1 << DIRECT_BITS_LOG2) && words <= 4 * a.row_products[t]) {
+        // direct count: one bitmap over [lo, hi], then the bitmap is cleared
+        // again so the chunked path finds its warp bitmaps zero
+        for (int64_t i = threadIdx.x; i < words; i += NT) f.direct[i] = 0u;
+        __syncthreads();
+        block_for_each_product<NT, false>(a.A, a.B, as, ae, ts, [&](int32_t col, double, int64_t) {
+          const int idx = col - lo;
+          atomicOr(&f.direct[idx >> 5], 1u << (idx & 31));
+        });
+        int64_t c = 0;
+        for (int64_t i = threadIdx.x; i < words; i += NT) c += __popc(f.direct[i]);
+        c = block_sum<NT>(c, ts.ws);
+        if (threadIdx.x == 0) a.out_cnt[row] = c;
+        for (int64_t i = threadIdx.x; i < words; i += NT) f.direct[i] = 0u;
+        fine_clear<false>(f, a.shift);
+        continue;
+      }
+    }
     const int32_t c0 = lo >> a.shift;
     const int nch = (hi >> a.shift) - c0 + 1;
     const int64_t col_base = (int64_t)c0 << a.shift;
-    const int64_t as = a.A.rp[row], ae = a.A.rp[row + 1];
+    for (int i = threadIdx.x; i < nch; i += NT) f.cnt[i] = 0;
+    __syncthreads();
+    // histogram
+    block_for_each_product<NT, false>(a.A, a.B, as, ae, ts, [&](int32_t col, double, int64_t) {
+      atomicAdd(&f.cnt[(col >> a.shift) - c0], 1);
+    });
+    // prefix sum -> offsets; counts become the reorder cursors
+    int32_t run = 0;
+    for (int i0 = 0; i0 < nch; i0 += NT) {
+      const int i = i0 + threadIdx.x;
+      const int64_t c = (i < nch) ? f.cnt[i] : 0;
+      int64_t tot;
+      const int64_t ex = block_exclusive_scan<NT>(c, ts.ws, &tot);
+      if (i < nch) {
+        f.off[i] = run + (int32_t)ex;
+        f.cnt[i] = 0;
+      }
+      run += (int32_t)tot;
+    }
+    if (threadIdx.x == 0) f.off[nch] = run;
+    __syncthreads();
+    // reorder into the block's slab
+    block_for_each_product<NT, NUMERIC>(a.A, a.B, as, ae, ts, [&](int32_t col, double v, int64_t) {
+      const int ch = (col >> a.shift) - c0;
+      const int pos = f.off[ch] + atomicAdd(&f.cnt[ch], 1);
+      st_stream(&slab_col[pos], (int32_t)(col - col_base));
+      if (NUMERIC) st_stream(&slab_val[pos], v);
+    });
     int32_t* oc = NUMERIC ? a.c_col + a.c_rp[row] : nullptr;
     double* ov = NUMERIC ? a.c_val + a.c_rp[row] : nullptr;
-    int64_t count;
-    if (nch == 1) {
-      // single chunk: accumulate straight from A and B
-      const int range = hi - (int32_t)col_base + 1;
-      const int nwords = (range + 31) >> 5;
-      for (int i = threadIdx.x; i < nwords; i += NT) f.bits[i] = 0u;
-      if (NUMERIC)
-        for (int i = threadIdx.x; i < range; i += NT) f.acc[i] = 0.0;
-      __syncthreads();
-      block_for_each_product<NT, NUMERIC>(a.A, a.B, as, ae, ts, [&](int32_t col, double v, int64_t) {
-        const int idx = col - (int32_t)col_base;
-        atomicOr(&f.bits[idx >> 5], 1u << (idx & 31));
-        if (NUMERIC) atomicAdd(&f.acc[idx], v);
-      });
-      count = block_emit_bitmap<NT, NUMERIC>(f.bits, nwords, f.acc, col_base, oc, ov, 0, ts.ws);
-    } else {
-      int32_t* scol = a.stage_col + a.stage_off[t];
-      double* sval = NUMERIC ? a.stage_val + a.stage_off[t] : nullptr;
-      for (int i = threadIdx.x; i < nch; i += NT) f.cnt[i] = 0;
-      __syncthreads();
-      // histogram
-      block_for_each_product<NT, false>(a.A, a.B, as, ae, ts, [&](int32_t col, double, int64_t) {
-        atomicAdd(&f.cnt[(col >> a.shift) - c0], 1);
-      });
-      // prefix sum -> offsets; counts become the reorder cursors
-      int32_t run = 0;
-      for (int i0 = 0; i0 < nch; i0 += NT) {
-        const int i = i0 + threadIdx.x;
-        const int64_t c = (i < nch) ? f.cnt[i] : 0;
-        int64_t tot;
-        const int64_t ex = block_exclusive_scan<NT>(c, ts.ws, &tot);
-        if (i < nch) {
-          f.off[i] = run + (int32_t)ex;
-          f.cnt[i] = 0;
-        }
-        run += (int32_t)tot;
-      }
-      if (threadIdx.x == 0) f.off[nch] = run;
-      __syncthreads();
-      // reorder
-      block_for_each_product<NT, NUMERIC>(a.A, a.B, as, ae, ts, [&](int32_t col, double v, int64_t) {
-        const int ch = (col >> a.shift) - c0;
-        const int pos = f.off[ch] + atomicAdd(&f.cnt[ch], 1);
-        st_stream(&scol[pos], (int32_t)(col - col_base));
-        if (NUMERIC) st_stream(&sval[pos], v);
-      });
-      count = fine_accumulate_chunks<NUMERIC>(f, nch, a.shift, a.dense_chunk_threshold, scol, sval,
-                                              col_base, oc, ov, ts.ws);
-    }
+    const int64_t count = warp_chunks_accumulate<NUMERIC>(f, nch, a.shift, slab_col, slab_val,
+                                                          col_base, oc, ov);
     if (!NUMERIC && threadIdx.x == 0) a.out_cnt[row] = count;
     __syncthreads();
-    (void)cl;
   }
 }
 
-cudaError_t launch_fine_rows(bool numeric, const FineArgs& a, cudaStream_t s) {
+int fine_rows_blocks_per_sm(bool numeric, int shift) {
+  const size_t smem = fine_smem_bytes(numeric, shift);
+  int n = 0;
+  cudaError_t e;
+  if (numeric) {
+    e = cudaFuncSetAttribute(k_fine_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fine_rows<true>, NT, smem);
+  } else {
+    e = cudaFuncSetAttribute(k_fine_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fine_rows<false>, NT, smem);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n < 1 ? 1 : n;
+}
+
+cudaError_t launch_fine_rows(bool numeric, const FineArgs& a, int grid, cudaStream_t s) {
   if (a.n_rows == 0) return cudaSuccess;
-  const size_t smem = fine_smem_bytes(numeric, a.shift, FINE_MAX_CHUNKS);
-  int64_t blocks = a.n_rows;
-  if (blocks > (1 << 20)) blocks = 1 << 20;
+  const size_t smem = fine_smem_bytes(numeric, a.shift);
+  int64_t blocks = grid;
+  if (blocks > a.n_rows) blocks = a.n_rows;
+  if (blocks < 1) blocks = 1;
   cudaError_t e;
   if (numeric) {
     e = cudaFuncSetAttribute(k_fine_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -163,6 +192,6 @@ cudaError_t launch_fine_rows(bool numeric, const FineArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-size_t fine_smem_for(bool numeric, int shift) { return fine_smem_bytes(numeric, shift, FINE_MAX_CHUNKS); }
+size_t fine_smem_for(bool numeric, int shift) { return fine_smem_bytes(numeric, shift); }
 
 }  // namespace magnus

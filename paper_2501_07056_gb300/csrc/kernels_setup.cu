@@ -122,10 +122,12 @@ __global__ void k_rowinfo(Csr A, Csr B, CatParams cp, int64_t* __restrict__ P,
       const int64_t range = (int64_t)hi - lo + 1;
       const int64_t nfine = (int64_t)(hi >> cp.fine_shift) - (lo >> cp.fine_shift) + 1;
       const bool dense_ok = range <= cp.dense_cols;
-      const bool fine_ok = nfine <= cp.fine_max_chunks && p < ((int64_t)1 << 31);
+      const bool fine_ok = nfine <= cp.fine_max_chunks && p <= cp.fine_max_products &&
+                           p < ((int64_t)1 << 31);
       if (cp.force == MAGNUS_CAT_COARSE) b = BIN_COARSE;
       else if (cp.force == MAGNUS_CAT_FINE) b = fine_ok ? BIN_FINE : BIN_COARSE;
-      else b = dense_ok ? BIN_DENSE : (fine_ok ? BIN_FINE : BIN_COARSE);
+      else if (dense_ok) b = BIN_DENSE;
+      else b = (cp.prefer_fine && fine_ok) ? BIN_FINE : BIN_COARSE;
     }
     if (active && sub == 0) {
       P[i] = p;

@@ -145,10 +145,11 @@ struct magnus_plan_s {
   std::vector<int32_t> fine_rows;
   std::vector<int64_t> fine_P;
   std::vector<int32_t> fine_lo, fine_hi;
-  std::vector<int64_t> fine_batches;  // boundaries, size nb+1
   int32_t* fine_rows_d = nullptr;
-  int64_t* fine_stage_off_d = nullptr;
-  std::vector<int64_t> fine_stage_off;
+  int64_t* fine_P_d = nullptr;
+  int64_t fine_slab = 0;      // staging capacity (products) of one fine block
+  int fine_grid_num = 0;      // resident blocks of the numeric fine kernel
+  int fine_grid_sym = 0;      // resident blocks of the symbolic fine kernel
   // coarse rows
   std::vector<int32_t> coarse_rows;
   std::vector<int64_t> coarse_P;
@@ -348,13 +349,17 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
   MAG_TRY(magnus_chunk_model(m_c, 64 * 1024, pl->l2_bytes, pl->num_sms * 2, &cm));
   MAG_TRY(magnus_chunk_model(m_c, 128 * 1024, pl->l2_bytes, pl->num_sms, &cms));
   pl->dense_cols = 8192;
+  // Fine chunks are accumulated by one warp each: a numeric chunk is at most
+  // 2^10 columns (8 KB of FP64 per warp), a symbolic chunk 2^13 columns (a
+  // 1 KB bitmap per warp).
   pl->shift_fine = P.chunk_len_fine_log2 > 0 ? P.chunk_len_fine_log2 : cm.chunk_len_fine_log2;
-  if (pl->shift_fine > 13) pl->shift_fine = 13;  // 2^13 doubles = 64 KB accumulator
+  if (pl->shift_fine > 10) pl->shift_fine = 10;
   if (pl->shift_fine < 5) pl->shift_fine = 5;
-  pl->shift_fine_sym = cms.chunk_len_fine_sym_log2;
-  if (pl->shift_fine_sym > 20) pl->shift_fine_sym = 20;  // 128 KB bitmap
-  if (pl->shift_fine_sym < pl->shift_fine) pl->shift_fine_sym = pl->shift_fine;
-  int sc = P.chunk_len_coarse_log2 > 0 ? P.chunk_len_coarse_log2 : cm.m_c_max_log2;
+  pl->shift_fine_sym = std::min(13, pl->shift_fine + 3);
+  (void)cms;
+  // Coarse chunks of 2^13 columns split a heavy row into independent
+  // (row, chunk) work items of eight warp chunks each.
+  int sc = P.chunk_len_coarse_log2 > 0 ? P.chunk_len_coarse_log2 : std::min(cm.m_c_max_log2, 13);
   if (sc > pl->col_bits) sc = pl->col_bits;
   if (sc < pl->shift_fine) sc = pl->shift_fine;
   if (sc - pl->shift_fine > 12) sc = pl->shift_fine + 12;  // fine chunks per coarse chunk
@@ -372,7 +377,7 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
   if (P.max_scratch_bytes > 0) {
     pl->scratch_cap = P.max_scratch_bytes;
   } else {
-    pl->scratch_cap = std::min<int64_t>((int64_t)(free_b / 8), (int64_t)8 << 30);
+    pl->scratch_cap = std::min<int64_t>((int64_t)(free_b / 6), (int64_t)16 << 30);
     if (pl->scratch_cap < ((int64_t)64 << 20)) pl->scratch_cap = (int64_t)64 << 20;
   }
 
@@ -402,6 +407,20 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
   cp.dense_cols = pl->dense_cols;
   cp.fine_shift = pl->shift_fine;
   cp.fine_max_chunks = FINE_MAX_CHUNKS;
+  // A fine row is staged whole in its block's slab; the slabs of all resident
+  // blocks share the staging budget.  Rows with more products than a slab
+  // are split across blocks by the coarse level instead.
+  pl->fine_grid_num = fine_rows_blocks_per_sm(true, pl->shift_fine) * pl->num_sms;
+  pl->fine_grid_sym = fine_rows_blocks_per_sm(false, pl->shift_fine_sym) * pl->num_sms;
+  pl->fine_slab = std::min<int64_t>((int64_t)1 << 20,
+                                    pl->scratch_cap / (12 * (int64_t)pl->fine_grid_num));
+  if (pl->fine_slab < 256) pl->fine_slab = 256;
+  cp.fine_max_products = pl->fine_slab;
+  // On GB300 a fine-level row runs on one block (one SM) while the coarse
+  // level spreads every row over the whole GPU in (row, chunk) work items;
+  // rows wider than the dense accumulator use the coarse level unless the
+  // fine level is forced.
+  cp.prefer_fine = 0;
   CUDA_TRY(launch_rowinfo(pl->A, pl->B, cp, pl->P, pl->bin, pl->lo, pl->hi, pl->seg_bs,
                           pl->seg_len, s));
   int64_t* stats;
@@ -476,7 +495,7 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
   pl->prods_cat[MAGNUS_CAT_COARSE] = sum(pl->coarse_P);
   pl->prods_cat[MAGNUS_CAT_SORT] = pl->n_interprod - pl->prods_cat[1] - pl->prods_cat[2] - pl->prods_cat[3];
 
-  // fine rows: heaviest first, batched by staging capacity (12 B/product)
+  // fine rows: heaviest first (taken in this order by the persistent fine kernel)
   if (!pl->fine_rows.empty()) {
     const size_t nf = pl->fine_rows.size();
     std::vector<size_t> order(nf);
@@ -495,27 +514,19 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
     pl->fine_P.swap(p2);
     pl->fine_lo.swap(l2);
     pl->fine_hi.swap(h2);
-    const int64_t cap = std::max<int64_t>(pl->scratch_cap / 12, pl->max_P);
-    pl->fine_batches = make_batches(pl->fine_P, cap, (int64_t)1 << 30);
-    pl->fine_stage_off.resize(nf);
-    for (size_t bi = 0; bi + 1 < pl->fine_batches.size(); ++bi) {
-      int64_t o = 0;
-      for (int64_t i = pl->fine_batches[bi]; i < pl->fine_batches[bi + 1]; ++i) {
-        pl->fine_stage_off[i] = o;
-        o += pl->fine_P[i];
-      }
-    }
     MAG_TRY(plan_alloc(pl, &pl->fine_rows_d, nf, s));
-    MAG_TRY(plan_alloc(pl, &pl->fine_stage_off_d, nf, s));
+    MAG_TRY(plan_alloc(pl, &pl->fine_P_d, nf, s));
     CUDA_TRY(cudaMemcpyAsync(pl->fine_rows_d, pl->fine_rows.data(), nf * 4, cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(pl->fine_stage_off_d, pl->fine_stage_off.data(), nf * 8,
-                             cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(pl->fine_P_d, pl->fine_P.data(), nf * 8, cudaMemcpyHostToDevice, s));
   }
   // coarse rows: batched by staging capacity (two 12 B/product buffers) and
   // by the size of the (row, chunk) bookkeeping
   if (!pl->coarse_rows.empty()) {
     const size_t nc = pl->coarse_rows.size();
-    const int64_t cap = std::max<int64_t>(pl->scratch_cap / 24, pl->max_P);
+    // coarse staging: 12 B per product, plus 12 B for the fine level inside
+    // coarse chunks wider than one block's dense accumulator
+    const int64_t per = pl->shift_coarse <= 13 ? 12 : 24;
+    const int64_t cap = std::max<int64_t>(pl->scratch_cap / per, pl->max_P);
     const int64_t max_rows = std::max<int64_t>(1, ((int64_t)1 << 28) / pl->n_chunks_coarse);
     pl->coarse_batches = make_batches(pl->coarse_P, cap, max_rows);
     MAG_TRY(plan_alloc(pl, &pl->coarse_rows_d, nc, s));
@@ -598,50 +609,54 @@ static int run_phase(magnus_plan_t pl, bool numeric, int64_t* out_cnt, const int
     CUDA_TRY(launch_dense_rows(numeric, a, pl->num_sms, s));
   }
   int64_t staged = 0;
-  // fine rows, batch by batch
-  {
+  // fine rows: one persistent launch; each block stages its row in its slab
+  if (!pl->fine_rows.empty()) {
     StageTimer tm(pl, st_base + 2, s);
     const int shift = numeric ? pl->shift_fine : pl->shift_fine_sym;
-    const size_t nbat = pl->fine_batches.empty() ? 0 : pl->fine_batches.size() - 1;
+    const int grid = numeric ? pl->fine_grid_num : pl->fine_grid_sym;
+    // The numeric pass stages every fine row.  The symbolic pass counts a
+    // row directly (no staging) when one bitmap over its range is small
+    // enough and dense enough; the kernel applies the same test.
+    bool need_stage = false;
+    for (size_t i = 0; i < pl->fine_rows.size(); ++i) {
+      const int64_t range = (int64_t)pl->fine_hi[i] - pl->fine_lo[i] + 1;
+      const bool direct = !numeric && range <= ((int64_t)1 << 19) &&
+                          ((range + 31) >> 5) <= 4 * pl->fine_P[i];
+      if (!direct) {
+        need_stage = true;
+        if (numeric) staged += pl->fine_P[i];
+      }
+    }
     int32_t* scol = nullptr;
     double* sval = nullptr;
-    int64_t cap = 0;
-    for (size_t bi = 0; bi < nbat; ++bi) {
-      const int64_t r0 = pl->fine_batches[bi], r1 = pl->fine_batches[bi + 1];
-      int64_t need = 0;
-      for (int64_t i = r0; i < r1; ++i) {
-        const int nch = (pl->fine_hi[i] >> shift) - (pl->fine_lo[i] >> shift) + 1;
-        if (nch > 1) need = std::max(need, pl->fine_stage_off[i] + pl->fine_P[i]);
-      }
-      if (need > cap) {
-        // staging covers the batch's rows that reorder (offsets are per batch)
-        MAG_TRY(scr.get(&scol, (size_t)need));
-        if (numeric) MAG_TRY(scr.get(&sval, (size_t)need));
-        cap = need;
-        pl->scratch_used = std::max<int64_t>(pl->scratch_used, need * (numeric ? 12 : 4));
-      }
-      for (int64_t i = r0; i < r1; ++i) {
-        const int nch = (pl->fine_hi[i] >> shift) - (pl->fine_lo[i] >> shift) + 1;
-        if (nch > 1) staged += pl->fine_P[i];
-      }
-      FineArgs a{};
-      a.A = A;
-      a.B = B;
-      a.rows = pl->fine_rows_d + r0;
-      a.n_rows = r1 - r0;
-      a.stage_off = pl->fine_stage_off_d + r0;
-      a.lo = pl->lo;
-      a.hi = pl->hi;
-      a.shift = shift;
-      a.dense_chunk_threshold = pl->dthr;
-      a.stage_col = scol;
-      a.stage_val = sval;
-      a.out_cnt = out_cnt;
-      a.c_rp = c_rp;
-      a.c_col = c_col;
-      a.c_val = c_val;
-      CUDA_TRY(launch_fine_rows(numeric, a, s));
+    int32_t* queue = nullptr;
+    MAG_TRY(scr.get(&queue, 1));
+    CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(int32_t), s));
+    if (need_stage) {
+      MAG_TRY(scr.get(&scol, (size_t)grid * pl->fine_slab));
+      if (numeric) MAG_TRY(scr.get(&sval, (size_t)grid * pl->fine_slab));
+      pl->scratch_used = std::max<int64_t>(pl->scratch_used,
+                                           (int64_t)grid * pl->fine_slab * (numeric ? 12 : 4));
     }
+    FineArgs a{};
+    a.A = A;
+    a.B = B;
+    a.rows = pl->fine_rows_d;
+    a.n_rows = (int64_t)pl->fine_rows.size();
+    a.slab_elems = pl->fine_slab;
+    a.queue = queue;
+    a.row_products = pl->fine_P_d;
+    a.lo = pl->lo;
+    a.hi = pl->hi;
+    a.shift = shift;
+    a.dense_chunk_threshold = pl->dthr;
+    a.stage_col = scol;
+    a.stage_val = sval;
+    a.out_cnt = out_cnt;
+    a.c_rp = c_rp;
+    a.c_col = c_col;
+    a.c_val = c_val;
+    CUDA_TRY(launch_fine_rows(numeric, a, grid, s));
   }
   // coarse rows, batch by batch
   {
@@ -674,20 +689,23 @@ static int run_phase(magnus_plan_t pl, bool numeric, int64_t* out_cnt, const int
       MAG_TRY(scr.get(&a.csc_row, (size_t)maxNnz));
       if (numeric) MAG_TRY(scr.get(&a.csc_val, (size_t)maxNnz));
       MAG_TRY(scr.get(&a.rows_b, (size_t)nB + 1));
+      MAG_TRY(scr.get(&a.item_off, (size_t)nB + 1));
       MAG_TRY(scr.get(&a.n_rows_b, 2));
       MAG_TRY(scr.get(&a.counts, (size_t)nbk + 1));
       MAG_TRY(scr.get(&a.cursor, (size_t)nbk));
+      const bool fine_inside = pl->shift_coarse > 13;
       MAG_TRY(scr.get(&a.chunk_col, (size_t)maxP));
-      MAG_TRY(scr.get(&a.fine_col, (size_t)maxP));
+      if (fine_inside) MAG_TRY(scr.get(&a.fine_col, (size_t)maxP));
       if (numeric) {
         MAG_TRY(scr.get(&a.chunk_val, (size_t)maxP));
-        MAG_TRY(scr.get(&a.fine_val, (size_t)maxP));
+        if (fine_inside) MAG_TRY(scr.get(&a.fine_val, (size_t)maxP));
         MAG_TRY(scr.get(&a.bucket_out, (size_t)nbk));
       }
       MAG_TRY(scr.get(&a.scan_tmp, (size_t)scan_tmp_elems(std::max<int64_t>(nB, nbk)) + 2));
       MAG_TRY(scr.get(&a.big_list, (size_t)nbk));
       MAG_TRY(scr.get(&a.n_big, 2));
-      pl->scratch_used = std::max<int64_t>(pl->scratch_used, maxP * (numeric ? 24 : 8));
+      pl->scratch_used = std::max<int64_t>(pl->scratch_used,
+                                           maxP * (numeric ? 12 : 4) * (fine_inside ? 2 : 1));
       a.bucket_cnt = pl->bucket_cnt;
       a.out_cnt = out_cnt;
       a.c_rp = c_rp;
@@ -783,17 +801,14 @@ int magnus_numeric_noalloc(magnus_plan_t pl, const double* a_val, const double* 
   if ((pl->A.nnz > 0 && !a_val) || (pl->B.nnz > 0 && !b_val)) return MAGNUS_INVALID_ARG;
   if (pl->nnz_c > 0 && (!c_col || !c_val)) return MAGNUS_INVALID_ARG;
   if (!pl->coarse_rows.empty()) return MAGNUS_SCRATCH_LIMIT;
-  // staging of the largest fine batch (only rows spanning several chunks reorder)
+  // The fine kernel stages one row per block in a slab of fine_slab products;
+  // the fixed buffer holds the row counter and as many slabs as fit, and the
+  // persistent grid is limited to that many blocks.
   const int shift = pl->shift_fine;
-  const size_t nbat = pl->fine_batches.empty() ? 0 : pl->fine_batches.size() - 1;
-  int64_t need = 0;
-  for (size_t bi = 0; bi < nbat; ++bi)
-    for (int64_t i = pl->fine_batches[bi]; i < pl->fine_batches[bi + 1]; ++i)
-      if ((pl->fine_hi[i] >> shift) - (pl->fine_lo[i] >> shift) + 1 > 1)
-        need = std::max(need, pl->fine_stage_off[i] + pl->fine_P[i]);
-  const size_t col_bytes = (((size_t)need * sizeof(int32_t)) + 255) & ~(size_t)255;
-  if (col_bytes + (size_t)need * sizeof(double) > MAGNUS_NOALLOC_SCRATCH_BYTES)
-    return MAGNUS_SCRATCH_LIMIT;
+  const size_t slab_bytes = (((size_t)pl->fine_slab * 12) + 255) & ~(size_t)255;
+  const size_t avail = MAGNUS_NOALLOC_SCRATCH_BYTES - 512;  // counter + alignment
+  if (!pl->fine_rows.empty() && slab_bytes > avail) return MAGNUS_SCRATCH_LIMIT;
+  const int grid = (int)std::min<size_t>((size_t)pl->fine_grid_num, avail / slab_bytes);
   unsigned char* scratch = nullptr;
   MAG_TRY(noalloc_scratch_address(&scratch));
   cudaStream_t s = (cudaStream_t)stream;
@@ -830,24 +845,31 @@ int magnus_numeric_noalloc(magnus_plan_t pl, const double* a_val, const double* 
     a.c_val = c_val;
     CUDA_TRY(launch_dense_rows(true, a, pl->num_sms, s));
   }
-  for (size_t bi = 0; bi < nbat; ++bi) {
-    const int64_t r0 = pl->fine_batches[bi], r1 = pl->fine_batches[bi + 1];
+  if (!pl->fine_rows.empty()) {
+    // byte 0..255: row counter (cleared here: every call starts from row 0);
+    // then grid slabs, columns of all slabs first, values after them
+    int32_t* queue = reinterpret_cast<int32_t*>(scratch);
+    CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(int32_t), s));
+    unsigned char* base = scratch + 256;
+    const size_t col_bytes = (((size_t)grid * pl->fine_slab * 4) + 255) & ~(size_t)255;
     FineArgs a{};
     a.A = A;
     a.B = B;
-    a.rows = pl->fine_rows_d + r0;
-    a.n_rows = r1 - r0;
-    a.stage_off = pl->fine_stage_off_d + r0;
+    a.rows = pl->fine_rows_d;
+    a.n_rows = (int64_t)pl->fine_rows.size();
+    a.slab_elems = pl->fine_slab;
+    a.queue = queue;
+    a.row_products = pl->fine_P_d;
     a.lo = pl->lo;
     a.hi = pl->hi;
     a.shift = shift;
     a.dense_chunk_threshold = pl->dthr;
-    a.stage_col = reinterpret_cast<int32_t*>(scratch);
-    a.stage_val = reinterpret_cast<double*>(scratch + col_bytes);
+    a.stage_col = reinterpret_cast<int32_t*>(base);
+    a.stage_val = reinterpret_cast<double*>(base + col_bytes);
     a.c_rp = c_row_ptr;
     a.c_col = c_col;
     a.c_val = c_val;
-    CUDA_TRY(launch_fine_rows(true, a, s));
+    CUDA_TRY(launch_fine_rows(true, a, grid, s));
   }
   return MAGNUS_OK;
 }
@@ -875,7 +897,7 @@ int magnus_plan_info(magnus_plan_t pl, magnus_plan_info_t* info) {
   info->dense_cols = pl->dense_cols;
   info->dense_chunk_threshold = pl->dthr;
   info->key_bits32 = pl->key32[BIN_SORT256];
-  info->n_batches_fine = pl->fine_batches.empty() ? 0 : (int)pl->fine_batches.size() - 1;
+  info->n_batches_fine = pl->fine_rows.empty() ? 0 : 1;
   info->n_batches_coarse = pl->coarse_batches.empty() ? 0 : (int)pl->coarse_batches.size() - 1;
   return MAGNUS_OK;
 }

@@ -80,15 +80,20 @@ def test_hybrid_threshold_extremes(dthr, force):
 
 
 @pytest.mark.parametrize("force", [FINE, COARSE])
-def test_multiple_batches(force):
+def test_small_staging_budget(force):
+    # An 8 MB staging budget: fine rows with more products than one block's
+    # slab (about 1500 here) are split by the coarse level, and coarse rows
+    # run in several batches.
     A = inputs.ragged(2000, 5000, 20, 60, seed=3, matrix_id=1)
     B = inputs.ragged(5000, 30000, 10, 50, seed=3, matrix_id=2)
-    got = run_gpu(A, B, P(force_category=force, max_scratch_bytes=1 << 20,
+    got = run_gpu(A, B, P(force_category=force, max_scratch_bytes=8 << 20,
                           chunk_len_coarse_log2=12))
     assert_parity(got, A, B)
     info = got["info"]
-    nb = info["n_batches_fine"] if force == FINE else info["n_batches_coarse"]
-    assert nb > 1
+    if force == FINE:
+        assert info["rows_per_category"][FINE] > 0 and info["rows_per_category"][COARSE] > 0
+    else:
+        assert info["n_batches_coarse"] > 1
 
 
 def _csr(n_rows, n_cols, rows_cols, vals=None):
@@ -196,3 +201,13 @@ def test_launch_counter_advances():
     n0 = magnus.magnus_launch_count()
     run_gpu(A, B, same=True)
     assert magnus.magnus_launch_count() > n0
+
+
+def test_wide_coarse_chunks_use_fine_level():
+    # Coarse chunks of 2^16 columns are wider than one block's dense
+    # accumulator, so each large (row, chunk) runs the fine level inside it.
+    A = inputs.ragged(1500, 1 << 17, 5, 40, seed=8, matrix_id=1)
+    B = inputs.ragged(1 << 17, 1 << 18, 20, 200, seed=8, matrix_id=2)
+    got = run_gpu(A, B, P(force_category=COARSE, chunk_len_coarse_log2=16, chunk_len_fine_log2=8))
+    assert_parity(got, A, B)
+    assert got["info"]["chunk_len_coarse_log2"] == 16

@@ -70,11 +70,15 @@ def test_noalloc_matches_numeric_on_two_calls():
     plan.free()
 
 
-def test_noalloc_refuses_oversized_plan():
+def test_noalloc_refuses_plan_with_coarse_rows():
     import torch
     from paper_2501_07056_gb300 import magnus
-    # ~9.5e6 products in one batch: 114 MB of staging, above the 64 MB buffer
-    plan, (dA, dB), nnz, _ = _fine_plan(1 << 30, n_rows=12000)
+    # coarse rows need several staging buffers the fixed array cannot hold
+    A = inputs.ragged(500, 4000, 10, 40, seed=12, matrix_id=1)
+    B = inputs.ragged(4000, 9000, 5, 20, seed=12, matrix_id=2)
+    dA, dB = magnus.DeviceCSR.from_host(A), magnus.DeviceCSR.from_host(B)
+    plan = magnus.Plan(dA, dB, magnus.make_params(force_category=3))
+    nnz = plan.symbolic()
     c_col = torch.empty(nnz, dtype=torch.int32, device="cuda")
     c_val = torch.empty(nnz, dtype=torch.float64, device="cuda")
     with pytest.raises(magnus.MagnusError) as ei:
