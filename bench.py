@@ -52,6 +52,8 @@ WORKLOADS = {
               "duplicates merged, FP64 U(0,1), seed 0",
     "rmat18": "C=A*A, A R-MAT scale 18, edge factor 16, (a,b,c)=(.57,.19,.19), "
               "duplicates merged, FP64 U(0,1), seed 0",
+    "rmat16": "C=A*A, A R-MAT scale 16, edge factor 16, (a,b,c)=(.57,.19,.19), "
+              "duplicates merged, FP64 U(0,1), seed 0 (profiling size)",
 }
 CPU_SAMPLE_ROWS = 1 << 21
 REF_STEP_ROWS = 1 << 18
@@ -69,6 +71,10 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--force-category", type=int, default=-1)
     p.add_argument("--sort-threshold", type=int, default=0)
+    p.add_argument("--chunk-coarse", type=int, default=0,
+                   help="log2 of the coarse chunk length (0 = planner's choice)")
+    p.add_argument("--chunk-fine", type=int, default=0,
+                   help="log2 of the fine chunk length (0 = planner's choice)")
     p.add_argument("--l2-fetch", type=int, default=0,
                    help="L2 fetch granularity hint in bytes (0 = leave the setting alone)")
     return p.parse_args(argv)
@@ -193,6 +199,8 @@ def peak_hbm():
 
 
 SORT_KERNEL_SOURCES = ("kernels_sort.cu", "sort_accum.cuh", "common.cuh", "internal.h")
+COARSE_KERNEL_SOURCES = ("kernels_coarse.cu", "fine_level.cuh", "block_accum.cuh",
+                         "sort_accum.cuh", "common.cuh", "internal.h")
 
 
 def csrc_hash(files=SORT_KERNEL_SOURCES) -> str:
@@ -206,7 +214,7 @@ def csrc_hash(files=SORT_KERNEL_SOURCES) -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel_tag: str, workload: str):
+def profiled_traffic(kernel_tag: str, workload: str, sources=SORT_KERNEL_SOURCES):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel sources (else None)."""
     path = os.path.join(PROFILE_DIR, "%s_%s.md" % (kernel_tag, workload.replace("^", "")))
@@ -219,7 +227,7 @@ def profiled_traffic(kernel_tag: str, workload: str):
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("csrc_sha256") != csrc_hash():
+    if vals.get("csrc_sha256") != csrc_hash(sources):
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -234,6 +242,15 @@ def numeric_sort_alg_bytes(n_rows, nnz_a, n_inter, nnz_c):
     B.val per intermediate product (12 B), C.col + C.val per nonzero of C
     (12 B)."""
     return 16 * (n_rows + 1) + 28 * nnz_a + 12 * n_inter + 12 * nnz_c
+
+
+def coarse_big_alg_bytes(products, nnz, buckets):
+    """Algorithmic bytes of the large-bucket accumulator of the coarse level:
+    every staged product of those buckets is read once (4 B chunk-local
+    column + 8 B value), every entry of C they produce is written once
+    (12 B), and each bucket reads its staging offsets, output offset and row
+    pointer (24 B)."""
+    return 12 * products + 12 * nnz + 24 * buckets
 
 
 def ideal_bytes(n_rows, nnz_a, n_inter, nnz_c):
@@ -311,6 +328,8 @@ def run_ours(args, dist):
     torch.cuda.synchronize()
     params = magnus.make_params(force_category=args.force_category,
                                 sort_threshold=args.sort_threshold,
+                                chunk_len_coarse_log2=args.chunk_coarse,
+                                chunk_len_fine_log2=args.chunk_fine,
                                 l2_fetch_bytes=args.l2_fetch)
     stream = torch.cuda.current_stream()
 
@@ -366,12 +385,21 @@ def run_ours(args, dist):
     value = total_units / (ms_max * 1e-3) / 1e9
     stage_ms = {k: (sum(v) / len(v) if v else 0.0) for k, v in stage.items()}
 
-    # roofline of the dominant kernel: the numeric sort-row kernel
+    # roofline of the dominant kernel: the numeric sort-row kernel, or the
+    # large-bucket accumulator when the coarse level carries the work
     peak, peak_kind = peak_hbm()
-    kern_ms = stage_ms["num_sort"]
-    alg = numeric_sort_alg_bytes(A.n_rows, A.nnz, n_inter, nnz_c)
+    if stage_ms["num_coarse"] > stage_ms["num_sort"]:
+        kern_ms = stage_ms["num_coarse_big"]
+        alg = coarse_big_alg_bytes(info["coarse_dense_products"], info["coarse_dense_nnz"],
+                                   info["coarse_dense_buckets"])
+        kernel = "k_bucket_dense numeric (coarse buckets of > 256 products)"
+        traffic = profiled_traffic("bucket_dense_numeric", args.workload, COARSE_KERNEL_SOURCES)
+    else:
+        kern_ms = stage_ms["num_sort"]
+        alg = numeric_sort_alg_bytes(A.n_rows, A.nnz, n_inter, nnz_c)
+        kernel = "k_sort_rows numeric"
+        traffic = profiled_traffic("sort_rows_numeric", args.workload)
     achieved = alg / (kern_ms * 1e-3) / 1e9 if kern_ms > 0 else 0.0
-    traffic = profiled_traffic("sort_rows_numeric", args.workload)
     t_ideal_ms = ideal_bytes(A.n_rows, A.nnz, n_inter, nnz_c) / (peak * 1e9) * 1e3
 
     result = {
@@ -381,7 +409,7 @@ def run_ours(args, dist):
         "data": "synthetic",
         "config": workload_config(args, A, dist),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_sort_rows numeric",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
                      "alg_bytes_per_launch": alg, "kernel_ms": kern_ms,
                      "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
                      if peak_kind == "measured" else "fallback 6.8 TB/s"},

@@ -219,6 +219,13 @@ typedef struct {
   int32_t key_bits32;           /* 1 if sort keys fit in 32 bits */
   int32_t n_batches_fine;
   int32_t n_batches_coarse;
+  int64_t coarse_dense_products; /* last numeric call: products of the coarse
+                                    (row, chunk) buckets too large for a warp
+                                    sort, accumulated by the block-wide dense
+                                    (or fine-level) kernel */
+  int64_t coarse_dense_nnz;      /* last numeric call: entries of C those
+                                    buckets produced */
+  int64_t coarse_dense_buckets;  /* last numeric call: number of such buckets */
 } magnus_plan_info_t;
 
 int magnus_plan_info(magnus_plan_t plan, magnus_plan_info_t* info);
@@ -232,7 +239,11 @@ enum magnus_stage {
   MAGNUS_STAGE_SYM_SORT = 0, MAGNUS_STAGE_SYM_DENSE = 1, MAGNUS_STAGE_SYM_FINE = 2,
   MAGNUS_STAGE_SYM_COARSE = 3, MAGNUS_STAGE_SYM_SCAN = 4,
   MAGNUS_STAGE_NUM_SORT = 5, MAGNUS_STAGE_NUM_DENSE = 6, MAGNUS_STAGE_NUM_FINE = 7,
-  MAGNUS_STAGE_NUM_COARSE = 8, MAGNUS_STAGE_COUNT = 9
+  MAGNUS_STAGE_NUM_COARSE = 8,
+  /* subsets of the coarse stages: the accumulation of the large (row, chunk)
+   * buckets (block-wide dense accumulator), summed over the coarse batches */
+  MAGNUS_STAGE_SYM_COARSE_BIG = 9, MAGNUS_STAGE_NUM_COARSE_BIG = 10,
+  MAGNUS_STAGE_COUNT = 11
 };
 int magnus_enable_timing(magnus_plan_t plan, int enable);
 int magnus_stage_times(magnus_plan_t plan, double* ms, int n);

@@ -176,6 +176,8 @@ struct CoarseArgs {
   double* c_val;
   int num_sms;
   int64_t nnz_batch;         // nnz of A over the batch rows
+  unsigned long long* big_stats;  // optional [3]: products, C entries, count of large buckets
+  cudaEvent_t big_ev0, big_ev1;   // optional: recorded around the large-bucket kernel
 };
 cudaError_t run_coarse_batch(bool numeric, CoarseArgs& a, cudaStream_t s);
 

@@ -54,12 +54,24 @@ __global__ void k_csc_fill(Csr A, const int32_t* __restrict__ rows, int64_t nb,
 
 // Outer-product traversal, load balanced.  The work of B row b is
 // nnz(B_b) x nnz(column b of A^CSC) products; it is cut into items of
-// 32 consecutive entries of the B row times OUTER_ET consecutive entries of
-// the A^CSC column (at most 1024 products), and every warp takes an equal
+// 32 consecutive entries of the B row times outer_et(L) consecutive entries
+// of the A^CSC column (at most 1024 products), and every warp takes an equal
 // contiguous range of items.  Lanes hold one entry of the B row each and
-// reuse it for every A^CSC entry of the item; lanes hitting the same
-// (row, chunk) are combined with match_any so one atomic serves them all.
+// reuse it for every A^CSC entry of the item.  A B row of L < 32 entries
+// takes Lp = next power of two >= L lanes, so 32 / Lp A^CSC entries share
+// one warp step, and its items are 32 / Lp times longer.  Lanes hitting the
+// same (row, chunk) are combined with match_any so one atomic serves them.
 constexpr int OUTER_ET = 32;
+
+__device__ __forceinline__ int outer_lanes(int64_t L) {
+  int lp = 1;
+  while (lp < L && lp < 32) lp <<= 1;
+  return lp;
+}
+
+__device__ __forceinline__ int64_t outer_et(int64_t L) {
+  return (int64_t)OUTER_ET * (32 / outer_lanes(L));
+}
 
 __global__ void k_outer_items(const int64_t* __restrict__ b_rp, const int64_t* __restrict__ col_ptr,
                               int64_t nB, int64_t* __restrict__ items) {
@@ -67,7 +79,8 @@ __global__ void k_outer_items(const int64_t* __restrict__ b_rp, const int64_t* _
        b += (int64_t)gridDim.x * blockDim.x) {
     const int64_t L = b_rp[b + 1] - b_rp[b];
     const int64_t C = col_ptr[b + 1] - col_ptr[b];
-    items[b] = (L > 0 && C > 0) ? ((L + 31) / 32) * ((C + OUTER_ET - 1) / OUTER_ET) : 0;
+    const int64_t et = outer_et(L);
+    items[b] = (L > 0 && C > 0) ? ((L + 31) / 32) * ((C + et - 1) / et) : 0;
   }
 }
 
@@ -95,20 +108,27 @@ __global__ void k_coarse_outer(Csr B, const int64_t* __restrict__ item_off, int6
     const int64_t EB = (L + 31) / 32;
     const int64_t li = it - item_off[b];
     const int64_t et = li / EB, eb = li - et * EB;
-    const int64_t k = eb * 32 + lane;
-    const bool valid = k < L;
+    const int Lt = (int)((L - eb * 32) < 32 ? (L - eb * 32) : 32);
+    const int Lp = outer_lanes(Lt);
+    const int G = 32 / Lp;
+    const int64_t ET = outer_et(L);
+    const int sub = lane / Lp, kk = lane & (Lp - 1);
+    const bool valid = kk < Lt;
+    const int64_t k = eb * 32 + kk;
     const int32_t col = valid ? B.col[bs + k] : 0;
     const double bv = (NUMERIC && valid) ? B.val[bs + k] : 0.0;
     const int chunk = col >> sc;
-    const unsigned active = __ballot_sync(FULL, valid);
-    const int64_t e0 = cs + et * OUTER_ET;
-    const int64_t e1 = (e0 + OUTER_ET < cs + C) ? e0 + OUTER_ET : cs + C;
-    for (int64_t e = e0; e < e1; ++e) {
-      const int32_t t = csc_row[e];
-      const double av = NUMERIC ? csc_val[e] : 0.0;
-      if (valid) {
+    const int64_t e0 = cs + et * ET;
+    const int64_t e1 = (e0 + ET < cs + C) ? e0 + ET : cs + C;
+    for (int64_t eg = e0; eg < e1; eg += G) {
+      const int64_t e = eg + sub;
+      const bool on = valid && e < e1;
+      const unsigned active = __ballot_sync(FULL, on);
+      if (on) {
+        const int32_t t = csc_row[e];
+        const double av = NUMERIC ? csc_val[e] : 0.0;
         const int64_t slot = (int64_t)t * nc + chunk;
-        const unsigned m = __match_any_sync(active, chunk);
+        const unsigned m = __match_any_sync(active, (unsigned long long)slot);
         const int leader = __ffs(m) - 1;
         if (!REORDER) {
           if (lane == leader)
@@ -192,18 +212,25 @@ __global__ void __launch_bounds__(BK_NW * 32)
                    const int32_t* __restrict__ rows, int32_t* __restrict__ bucket_cnt,
                    const int64_t* __restrict__ bucket_out, const int64_t* __restrict__ c_rp,
                    int32_t* __restrict__ c_col, double* __restrict__ c_val,
-                   int32_t* __restrict__ big_list, int32_t* __restrict__ n_big) {
+                   int32_t* __restrict__ big_list, int32_t* __restrict__ n_big,
+                   unsigned long long* __restrict__ big_stats) {
   __shared__ double s_vals[BK_NW][NUMERIC ? SORT_MAX : 1];
   __shared__ K s_keys[BK_NW][NUMERIC ? SORT_MAX : 1];
   const int lane = lane_id(), w = warp_id();
   const int64_t nw = (int64_t)gridDim.x * BK_NW;
+  unsigned long long big_p = 0, big_z = 0, big_n = 0;  // lane 0's tallies
   for (int64_t id = (int64_t)blockIdx.x * BK_NW + w; id < nbk; id += nw) {
     const int64_t p0 = offs[id];
     const int n = (int)(offs[id + 1] - p0);
     const int64_t t = id / nc;
     const int c = (int)(id - t * nc);
     if (n > SORT_MAX) {
-      if (lane == 0) big_list[atomicAdd(n_big, 1)] = (int32_t)id;
+      if (lane == 0) {
+        big_list[atomicAdd(n_big, 1)] = (int32_t)id;
+        big_p += (unsigned long long)n;
+        big_n += 1;
+        if (NUMERIC) big_z += (unsigned long long)bucket_cnt[(list_base + t) * nc + c];
+      }
       continue;
     }
     int32_t* oc = nullptr;
@@ -226,6 +253,11 @@ __global__ void __launch_bounds__(BK_NW * 32)
     }
     if (!NUMERIC && lane == 0) bucket_cnt[(list_base + t) * nc + c] = cnt;
     __syncwarp();
+  }
+  if (big_stats && lane == 0 && big_n > 0) {
+    atomicAdd(&big_stats[0], big_p);
+    atomicAdd(&big_stats[1], big_z);
+    atomicAdd(&big_stats[2], big_n);
   }
 }
 
@@ -313,9 +345,15 @@ __global__ void __launch_bounds__(FNT)
 
 // Large coarse chunks whose column range (2^sc <= 2^13) fits one block's
 // dense accumulator: Algorithm 1 straight from the coarse staging, with no
-// second reorder.  FP64 values and the bitmap live in shared memory; emission
-// scans the bitmap in column order and clears exactly what it touched.
+// second reorder.  FP64 values and the bitmap live in shared memory.  The
+// scatter loop issues BD_UNROLL loads per thread before its atomics.
+// Emission is warp-cooperative: warp w owns a contiguous range of bitmap
+// words; each non-zero word is expanded by a ballot so the warp writes its
+// set columns as one coalesced run, reading (and re-zeroing) the 32
+// accumulator slots of the word together.  The words are cleared after use,
+// so the accumulator is clean for the next chunk.
 constexpr int BUCKET_DENSE_LOG2 = 13;
+constexpr int BD_UNROLL = 4;
 
 template <bool NUMERIC>
 __global__ void __launch_bounds__(FNT)
@@ -328,14 +366,19 @@ __global__ void __launch_bounds__(FNT)
   extern __shared__ __align__(16) unsigned char dsm[];
   const int cl = 1 << sc;
   const int words = cl >= 32 ? cl >> 5 : 1;
+  const int wpw = (words + FNW - 1) / FNW;  // words per warp (<= 32 for sc <= 13)
+  const int lane = lane_id(), w = warp_id();
   double* acc = reinterpret_cast<double*>(dsm);
   uint32_t* bits = reinterpret_cast<uint32_t*>(dsm + (NUMERIC ? (size_t)cl * 8 : 0));
-  __shared__ int64_t ws[FNT / 32 + 1];
+  __shared__ int32_t wcnt[FNW];
   if (NUMERIC)
     for (int i = threadIdx.x; i < cl; i += FNT) acc[i] = 0.0;
   for (int i = threadIdx.x; i < words; i += FNT) bits[i] = 0u;
   __syncthreads();
   const int nbig = *n_big;
+  const int wd0 = w * wpw;
+  const int my_wd = wd0 + lane;
+  const bool own = lane < wpw && my_wd < words;
   for (int q = blockIdx.x; q < nbig; q += gridDim.x) {
     const int64_t id = big_list[q];
     const int64_t p0 = offs[id];
@@ -344,39 +387,51 @@ __global__ void __launch_bounds__(FNT)
     const int c = (int)(id - t * nc);
     const int32_t* cc = chunk_col + p0;
     const double* cv = NUMERIC ? chunk_val + p0 : nullptr;
-    for (int p = threadIdx.x; p < n; p += FNT) {
-      const int idx = cc[p];
-      atomicOr(&bits[idx >> 5], 1u << (idx & 31));
-      if (NUMERIC) atomicAdd(&acc[idx], cv[p]);
-    }
-    __syncthreads();
-    int64_t o0 = 0;
-    if (NUMERIC) o0 = c_rp[rows[t]] + bucket_out[id];
-    const int64_t col_base = (int64_t)c << sc;
-    int64_t total = 0;
-    for (int w0 = 0; w0 < words; w0 += FNT) {
-      const int wd = w0 + threadIdx.x;
-      uint32_t m = (wd < words) ? bits[wd] : 0u;
-      int64_t tot;
-      int64_t pos = block_exclusive_scan<FNT>((int64_t)__popc(m), ws, &tot);
-      if (wd < words && m) {
-        bits[wd] = 0u;
-        if (NUMERIC) {
-          int64_t o = o0 + total + pos;
-          while (m) {
-            const int b = __ffs(m) - 1;
-            m &= m - 1;
-            const int idx = wd * 32 + b;
-            c_col[o] = (int32_t)(col_base + idx);
-            c_val[o] = acc[idx];
-            acc[idx] = 0.0;
-            ++o;
-          }
+    for (int p = threadIdx.x; p < n; p += BD_UNROLL * FNT) {
+      int idx[BD_UNROLL];
+      double v[BD_UNROLL];
+#pragma unroll
+      for (int u = 0; u < BD_UNROLL; ++u) {
+        const int pu = p + u * FNT;
+        idx[u] = pu < n ? cc[pu] : -1;
+        if (NUMERIC) v[u] = pu < n ? cv[pu] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < BD_UNROLL; ++u) {
+        if (idx[u] >= 0) {
+          atomicOr(&bits[idx[u] >> 5], 1u << (idx[u] & 31));
+          if (NUMERIC) atomicAdd(&acc[idx[u]], v[u]);
         }
       }
-      total += tot;
     }
-    if (!NUMERIC && threadIdx.x == 0) bucket_cnt[(list_base + t) * nc + c] = (int32_t)total;
+    __syncthreads();
+    const uint32_t mine = own ? bits[my_wd] : 0u;
+    const int cnt = warp_sum(__popc(mine));
+    if (lane == 0) wcnt[w] = cnt;
+    __syncthreads();
+    if (NUMERIC) {
+      int64_t o = c_rp[rows[t]] + bucket_out[id];
+      for (int i = 0; i < w; ++i) o += wcnt[i];
+      const int64_t col_base = (int64_t)c << sc;
+      const unsigned below = (1u << lane) - 1u;
+      for (int j = 0; j < wpw; ++j) {
+        const uint32_t m = __shfl_sync(FULL, mine, j);
+        if (m == 0u) continue;
+        const int idx = (wd0 + j) * 32 + lane;
+        if ((m >> lane) & 1u) {
+          const int64_t pos = o + __popc(m & below);
+          c_col[pos] = (int32_t)(col_base + idx);
+          c_val[pos] = acc[idx];
+          acc[idx] = 0.0;
+        }
+        o += __popc(m);
+      }
+    } else if (threadIdx.x == 0) {
+      int total = 0;
+      for (int i = 0; i < FNW; ++i) total += wcnt[i];
+      bucket_cnt[(list_base + t) * nc + c] = total;
+    }
+    if (own) bits[my_wd] = 0u;
     __syncthreads();
   }
 }
@@ -436,13 +491,14 @@ static cudaError_t coarse_impl(CoarseArgs& a, cudaStream_t s) {
   if (k32)
     k_bucket_small<uint32_t, NUMERIC><<<gb, BK_NW * 32, 0, s>>>(
         a.counts, nbk, a.chunk_col, a.chunk_val, a.shift_coarse, a.n_chunks, a.list_base, a.rows,
-        a.bucket_cnt, a.bucket_out, a.c_rp, a.c_col, a.c_val, a.big_list, a.n_big);
+        a.bucket_cnt, a.bucket_out, a.c_rp, a.c_col, a.c_val, a.big_list, a.n_big, a.big_stats);
   else
     k_bucket_small<uint64_t, NUMERIC><<<gb, BK_NW * 32, 0, s>>>(
         a.counts, nbk, a.chunk_col, a.chunk_val, a.shift_coarse, a.n_chunks, a.list_base, a.rows,
-        a.bucket_cnt, a.bucket_out, a.c_rp, a.c_col, a.c_val, a.big_list, a.n_big);
+        a.bucket_cnt, a.bucket_out, a.c_rp, a.c_col, a.c_val, a.big_list, a.n_big, a.big_stats);
   count_launch();
   CK(cudaGetLastError());
+  if (a.big_ev0) CK(cudaEventRecord(a.big_ev0, s));
   if (a.shift_coarse <= BUCKET_DENSE_LOG2) {
     const size_t cl = (size_t)1 << a.shift_coarse;
     const size_t smem = (NUMERIC ? cl * 8 : 0) + (cl >= 32 ? cl / 8 : 4);
@@ -464,6 +520,7 @@ static cudaError_t coarse_impl(CoarseArgs& a, cudaStream_t s) {
   }
   count_launch();
   CK(cudaGetLastError());
+  if (a.big_ev1) CK(cudaEventRecord(a.big_ev1, s));
   if (!NUMERIC) {
     k_row_totals<<<gw, nt, 0, s>>>(a.bucket_cnt, a.rows, a.n_rows, a.n_chunks, a.list_base,
                                    a.out_cnt);

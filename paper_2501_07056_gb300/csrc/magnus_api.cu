@@ -157,6 +157,7 @@ struct magnus_plan_s {
   std::vector<int64_t> coarse_batches;
   int32_t* coarse_rows_d = nullptr;
   int32_t* bucket_cnt = nullptr;
+  unsigned long long* big_stats = nullptr;  // [3] of the last numeric call (coarse large buckets)
   // sorted slot order of the sort rows (symbolic -> numeric)
   uint8_t* perm = nullptr;
   int64_t perm_off[NUM_BINS + 1] = {0};
@@ -171,6 +172,8 @@ struct magnus_plan_s {
   bool timing = false;
   cudaEvent_t ev[2 * MAGNUS_STAGE_COUNT] = {};
   bool ev_used[MAGNUS_STAGE_COUNT] = {};
+  std::vector<cudaEvent_t> big_ev[2];  // per phase: event pairs around each batch's large-bucket kernel
+  int big_ev_used[2] = {0, 0};
   cudaStream_t last_stream = nullptr;
 };
 
@@ -312,6 +315,8 @@ void magnus_free(magnus_plan_t p) {
   for (void* v : p->owned) cudaFreeAsync(v, s);
   for (int i = 0; i < 2 * MAGNUS_STAGE_COUNT; ++i)
     if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+  for (int ph = 0; ph < 2; ++ph)
+    for (cudaEvent_t e : p->big_ev[ph]) cudaEventDestroy(e);
   delete p;
 }
 
@@ -539,6 +544,8 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
     pl->coarse_nnz.resize(nc);
     for (size_t i = 0; i < nc; ++i) pl->coarse_nnz[i] = rp[pl->coarse_rows[i] + 1] - rp[pl->coarse_rows[i]];
     MAG_TRY(plan_alloc(pl, &pl->bucket_cnt, nc * (size_t)pl->n_chunks_coarse, s));
+    MAG_TRY(plan_alloc(pl, &pl->big_stats, 3, s));
+    CUDA_TRY(cudaMemsetAsync(pl->big_stats, 0, 3 * sizeof(unsigned long long), s));
   }
   CUDA_TRY(cudaStreamSynchronize(s));
   return MAGNUS_OK;
@@ -707,6 +714,19 @@ static int run_phase(magnus_plan_t pl, bool numeric, int64_t* out_cnt, const int
       pl->scratch_used = std::max<int64_t>(pl->scratch_used,
                                            maxP * (numeric ? 12 : 4) * (fine_inside ? 2 : 1));
       a.bucket_cnt = pl->bucket_cnt;
+      if (numeric) {
+        a.big_stats = pl->big_stats;
+        CUDA_TRY(cudaMemsetAsync(pl->big_stats, 0, 3 * sizeof(unsigned long long), s));
+      }
+      const int ph = numeric ? 1 : 0;
+      pl->big_ev_used[ph] = 0;
+      if (pl->timing) {
+        while (pl->big_ev[ph].size() < 2 * nbat) {
+          cudaEvent_t e;
+          CUDA_TRY(cudaEventCreate(&e));
+          pl->big_ev[ph].push_back(e);
+        }
+      }
       a.out_cnt = out_cnt;
       a.c_rp = c_rp;
       a.c_col = c_col;
@@ -722,6 +742,11 @@ static int run_phase(magnus_plan_t pl, bool numeric, int64_t* out_cnt, const int
           staged += pl->coarse_P[i];
         }
         a.nnz_batch = z;
+        if (pl->timing) {
+          a.big_ev0 = pl->big_ev[ph][2 * bi];
+          a.big_ev1 = pl->big_ev[ph][2 * bi + 1];
+          pl->big_ev_used[ph] = (int)bi + 1;
+        }
         CUDA_TRY(run_coarse_batch(numeric, a, s));
       }
     }
@@ -736,6 +761,7 @@ int magnus_symbolic(magnus_plan_t pl, int64_t* c_row_ptr, int64_t* nnz_c, void* 
   pl->last_stream = s;
   pl->symbolic_done = false;
   for (int i = 0; i < MAGNUS_STAGE_COUNT; ++i) pl->ev_used[i] = false;
+  pl->big_ev_used[0] = pl->big_ev_used[1] = 0;
   const int64_t n = pl->A.n_rows;
   CUDA_TRY(cudaMemsetAsync(c_row_ptr, 0, (size_t)(n + 1) * sizeof(int64_t), s));
   MAG_TRY(run_phase(pl, false, c_row_ptr, nullptr, nullptr, nullptr, s));
@@ -763,7 +789,8 @@ int magnus_numeric(magnus_plan_t pl, const double* a_val, const double* b_val,
   if (pl->nnz_c > 0 && (!c_col || !c_val)) return MAGNUS_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   pl->last_stream = s;
-  for (int i = MAGNUS_STAGE_NUM_SORT; i < MAGNUS_STAGE_COUNT; ++i) pl->ev_used[i] = false;
+  for (int i = MAGNUS_STAGE_NUM_SORT; i <= MAGNUS_STAGE_NUM_COARSE; ++i) pl->ev_used[i] = false;
+  pl->big_ev_used[1] = 0;
   pl->A.val = a_val;
   pl->B.val = b_val;
   return run_phase(pl, true, nullptr, c_row_ptr, c_col, c_val, s);
@@ -899,6 +926,13 @@ int magnus_plan_info(magnus_plan_t pl, magnus_plan_info_t* info) {
   info->key_bits32 = pl->key32[BIN_SORT256];
   info->n_batches_fine = pl->fine_rows.empty() ? 0 : 1;
   info->n_batches_coarse = pl->coarse_batches.empty() ? 0 : (int)pl->coarse_batches.size() - 1;
+  if (pl->big_stats) {
+    unsigned long long h[3] = {0, 0, 0};
+    CUDA_TRY(cudaMemcpy(h, pl->big_stats, sizeof(h), cudaMemcpyDeviceToHost));
+    info->coarse_dense_products = (int64_t)h[0];
+    info->coarse_dense_nnz = (int64_t)h[1];
+    info->coarse_dense_buckets = (int64_t)h[2];
+  }
   return MAGNUS_OK;
 }
 
@@ -915,6 +949,17 @@ int magnus_stage_times(magnus_plan_t pl, double* ms, int n) {
   if (!pl || !ms || n < 0) return MAGNUS_INVALID_ARG;
   for (int i = 0; i < n && i < MAGNUS_STAGE_COUNT; ++i) {
     ms[i] = 0.0;
+    if (i == MAGNUS_STAGE_SYM_COARSE_BIG || i == MAGNUS_STAGE_NUM_COARSE_BIG) {
+      const int ph = i == MAGNUS_STAGE_NUM_COARSE_BIG ? 1 : 0;
+      if (!pl->timing) continue;
+      for (int b = 0; b < pl->big_ev_used[ph]; ++b) {
+        CUDA_TRY(cudaEventSynchronize(pl->big_ev[ph][2 * b + 1]));
+        float f = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&f, pl->big_ev[ph][2 * b], pl->big_ev[ph][2 * b + 1]));
+        ms[i] += f;
+      }
+      continue;
+    }
     if (pl->timing && pl->ev_used[i]) {
       CUDA_TRY(cudaEventSynchronize(pl->ev[2 * i + 1]));
       float f = 0.f;

@@ -23,7 +23,8 @@ c_i32, c_i64, c_p, c_u64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctyp
 
 CAT_AUTO, CAT_SORT, CAT_DENSE, CAT_FINE, CAT_COARSE = -1, 0, 1, 2, 3
 STAGES = ["sym_sort", "sym_dense", "sym_fine", "sym_coarse", "sym_scan",
-          "num_sort", "num_dense", "num_fine", "num_coarse"]
+          "num_sort", "num_dense", "num_fine", "num_coarse",
+          "sym_coarse_big", "num_coarse_big"]
 
 
 class CsrDesc(ctypes.Structure):
@@ -47,7 +48,9 @@ class PlanInfo(ctypes.Structure):
                 ("chunk_len_fine_sym_log2", c_i32), ("chunk_len_coarse_log2", c_i32),
                 ("n_chunks_coarse", c_i32), ("dense_cols", c_i32),
                 ("dense_chunk_threshold", c_i32), ("key_bits32", c_i32),
-                ("n_batches_fine", c_i32), ("n_batches_coarse", c_i32)]
+                ("n_batches_fine", c_i32), ("n_batches_coarse", c_i32),
+                ("coarse_dense_products", c_i64), ("coarse_dense_nnz", c_i64),
+                ("coarse_dense_buckets", c_i64)]
 
     def as_dict(self):
         d = {}
