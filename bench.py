@@ -54,6 +54,9 @@ WORKLOADS = {
               "duplicates merged, FP64 U(0,1), seed 0",
     "rmat16": "C=A*A, A R-MAT scale 16, edge factor 16, (a,b,c)=(.57,.19,.19), "
               "duplicates merged, FP64 U(0,1), seed 0 (profiling size)",
+    "batched4096": "4096 independent products C_i=A_i*B_i, n_i log-uniform in [256, 65536], "
+                   "A_i and B_i n_i x n_i with nnz/row uniform in {2..32} (counter-based "
+                   "generator, drawn on the device), FP64 U(-1,1), seed 0",
 }
 CPU_SAMPLE_ROWS = 1 << 21
 REF_STEP_ROWS = 1 << 18
@@ -75,6 +78,12 @@ def parse_args(argv=None):
                    help="log2 of the coarse chunk length (0 = planner's choice)")
     p.add_argument("--chunk-fine", type=int, default=0,
                    help="log2 of the fine chunk length (0 = planner's choice)")
+    p.add_argument("--batch-count", type=int, default=4096,
+                   help="batched workload: number of products")
+    p.add_argument("--batch-waves", type=int, default=4,
+                   help="batched workload: products are planned in this many waves")
+    p.add_argument("--numeric-graph", type=int, default=0,
+                   help="1 = capture the numeric phase in a CUDA graph")
     p.add_argument("--l2-fetch", type=int, default=0,
                    help="L2 fetch granularity hint in bytes (0 = leave the setting alone)")
     return p.parse_args(argv)
@@ -431,6 +440,106 @@ def run_ours(args, dist):
     return result
 
 
+def run_batched(args, dist):
+    """Batched workload: every step computes all products, wave by wave
+    (one batched plan, symbolic and numeric per wave, C freed after the
+    wave).  Beside it, the same products one call per product."""
+    import torch
+
+    from paper_2501_07056_gb300 import gen_device, inputs, magnus
+
+    dev = torch.device("cuda", dist.local_rank if dist.world > 1 else 0)
+    torch.cuda.set_device(dev)
+    magnus._lib()
+    count = args.batch_count
+    ns = inputs.batched_sizes(count, seed=0)
+    # replicas: each rank runs the whole batch
+    As = [gen_device.ragged(int(n), int(n), 2, 32, 0, 2 * i + 1, device=dev) for i, n in enumerate(ns)]
+    Bs = [gen_device.ragged(int(n), int(n), 2, 32, 0, 2 * i + 2, device=dev) for i, n in enumerate(ns)]
+    torch.cuda.synchronize()
+    params = magnus.make_params(sort_threshold=args.sort_threshold,
+                                force_category=args.force_category,
+                                chunk_len_coarse_log2=args.chunk_coarse,
+                                chunk_len_fine_log2=args.chunk_fine)
+    stream = torch.cuda.current_stream()
+    nw = max(1, min(args.batch_waves, count))
+    bounds = [round(w * count / nw) for w in range(nw + 1)]
+    stats = {"n_inter": 0, "nnz_c": 0}
+
+    def step(record=False):
+        tot_i = tot_c = 0
+        for w in range(nw):
+            lo, hi = bounds[w], bounds[w + 1]
+            bp = magnus.BatchPlan(As[lo:hi], Bs[lo:hi], params, stream)
+            off = bp.symbolic()
+            col, val = bp.numeric()
+            del col, val
+            bp.c_col = bp.c_val = None
+            if record:
+                tot_i += bp.info()["n_interprod"]
+                tot_c += off[-1]
+            bp.free()
+        if record:
+            stats["n_inter"], stats["nnz_c"] = tot_i, tot_c
+
+    step(record=True)
+    for _ in range(args.warmup - 1):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index).start()
+    dist.barrier()
+    torch.cuda.synchronize()
+    n_launch0 = magnus.magnus_launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    n_launch = magnus.magnus_launch_count() - n_launch0
+    clk = clocks.stop()
+    ms = dist.max(ev0.elapsed_time(ev1)) / args.steps
+    n_inter = stats["n_inter"]
+    value = dist.sum(2.0 * n_inter) / (ms * 1e-3) / 1e9
+
+    # one call per product (plan, symbolic, allocate C, numeric, free)
+    def one_by_one(k):
+        for i in range(k):
+            C = magnus.spgemm(As[i], Bs[i], params, stream)
+            del C
+    one_by_one(min(count, 64))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    one_by_one(count)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_one = e0.elapsed_time(e1)
+    wall_one = time.perf_counter() - t0
+    return {
+        "metric": "SpGEMM GFLOP/s", "value": value, "unit": "GFLOP/s", "n_gpus": dist.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS["batched4096"].replace("4096", str(count), 1),
+                   "products": count, "waves": nw, "n_interprod": n_inter,
+                   "nnz_c": stats["nnz_c"],
+                   "parallelism": "replicas" if dist.world > 1 else "single",
+                   "l2": "inputs larger than L2, no flush",
+                   "step": "per wave: batched plan+symbolic+alloc C+numeric"},
+        "products_per_s": count / (ms * 1e-3),
+        "one_call_per_product": {"ms": ms_one, "wall_s": wall_one,
+                                 "products_per_s": count / (ms_one * 1e-3),
+                                 "gflops": 2.0 * n_inter / (ms_one * 1e-3) / 1e9},
+        "clocks": clk,
+        "gpu_launches": n_launch,
+    }
+
+
 def run_e2e(args, dist, A, dev, params, n_inter, nnz_c):
     """Same metric through the public API with host buffers: every step
     copies A from pinned host memory to the device, computes C and copies C
@@ -482,6 +591,8 @@ def main(argv=None):
     try:
         if args.impl == "reference":
             res = run_reference(args, dist)
+        elif args.workload == "batched4096":
+            res = run_batched(args, dist)
         else:
             res = run_ours(args, dist)
         if dist.rank == 0 and res is not None:

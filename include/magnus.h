@@ -104,7 +104,16 @@ typedef struct {
  *                     calling process and left in place (the limit is a
  *                     property of the CUDA context, not of the GPU).  32 stops
  *                     the gathers of short B rows from pulling whole 128-byte
- *                     lines; 0 = leave the process setting alone.            */
+ *                     lines; 0 = leave the process setting alone.
+ * numeric_graph       1 = magnus_numeric (and magnus_numeric_batched)
+ *                     captures its launches in a CUDA graph on the first call
+ *                     and replays the graph on later calls with the same
+ *                     value and output pointers (plan reuse with new values
+ *                     costs one graph launch instead of one launch per
+ *                     kernel).  Needs a stream other than the legacy default
+ *                     stream (NULL), else the launches run uncaptured; stage
+ *                     timing (magnus_enable_timing) also runs uncaptured.
+ *                     0 = no graph.                                          */
 typedef struct {
   int32_t sort_threshold;
   int32_t force_category;
@@ -114,7 +123,7 @@ typedef struct {
   int32_t validate;
   int64_t max_scratch_bytes;
   int32_t l2_fetch_bytes;
-  int32_t reserved;
+  int32_t numeric_graph;
 } magnus_params_t;
 
 /* Fill *p with the automatic values.  Returns MAGNUS_INVALID_ARG on NULL. */
@@ -196,6 +205,50 @@ const char* magnus_strerror(int status);
  * (empty string if none). */
 const char* magnus_last_cuda_error(void);
 
+/* ---- batched products ----------------------------------------------------
+ * Many independent products C_i = A_i * B_i (i < count) planned and run
+ * together, so that every launch serves the rows of all products.  The paper
+ * computes one product at a time; the batch is a packing of the inputs, not a
+ * change of the arithmetic: the operands are gathered into one block-diagonal
+ * problem (A_i's columns shifted past the rows of B_1..B_{i-1}, B_i's columns
+ * unchanged), whose row r of product i is row r of C_i in C_i's own columns.
+ *
+ * Layout of C: one packed CSR over the rows of all products in order.
+ * Product i owns packed rows [row_offsets[i], row_offsets[i+1]) and packed
+ * entries [c_offsets[i], c_offsets[i+1]); its own row pointers are
+ * c_row_ptr[row_offsets[i] .. row_offsets[i+1]] - c_offsets[i].
+ *
+ * magnus_plan_batched  A, B: host arrays of `count` descriptors of device CSR
+ *                      operands (A[i].n_cols == B[i].n_rows).  The operands
+ *                      must stay alive and unchanged in structure until
+ *                      magnus_free_batched; values are read by every
+ *                      magnus_numeric_batched call.  The batch holds a packed
+ *                      copy of both operands (16 B per row and 12 B per
+ *                      nonzero) and the inner plan.  Totals of rows must stay
+ *                      below 2^31.  Synchronises `stream`.
+ * magnus_batch_layout  row_offsets (host, count+1) and the total number of
+ *                      rows of C; either pointer may be NULL.
+ * magnus_symbolic_batched
+ *                      c_row_ptr: device, total_rows+1 int64 (written);
+ *                      c_offsets: host, count+1 int64 (written; c_offsets[count]
+ *                      is nnz of all products).  Synchronises `stream`.
+ * magnus_numeric_batched
+ *                      c_col / c_val: device, c_offsets[count] entries each.
+ *                      With params.numeric_graph = 1 the value packing and the
+ *                      numeric phase are captured in one CUDA graph and
+ *                      replayed on later calls with the same output pointers.
+ * magnus_batch_info    the inner plan's magnus_plan_info.
+ * Status codes as for the single-product calls. */
+typedef struct magnus_batch_s* magnus_batch_t;
+int magnus_plan_batched(magnus_batch_t* batch, int32_t count, const magnus_csr_t* A,
+                        const magnus_csr_t* B, const magnus_params_t* params, void* stream);
+int magnus_batch_layout(magnus_batch_t batch, int64_t* row_offsets, int64_t* total_rows);
+int magnus_symbolic_batched(magnus_batch_t batch, int64_t* c_row_ptr, int64_t* c_offsets,
+                            void* stream);
+int magnus_numeric_batched(magnus_batch_t batch, const int64_t* c_row_ptr, int32_t* c_col,
+                           double* c_val, void* stream);
+void magnus_free_batched(magnus_batch_t batch);
+
 /* ---- plan introspection ------------------------------------------------ */
 typedef struct {
   int64_t n_rows;               /* rows of A (= rows of C) */
@@ -229,6 +282,7 @@ typedef struct {
 } magnus_plan_info_t;
 
 int magnus_plan_info(magnus_plan_t plan, magnus_plan_info_t* info);
+int magnus_batch_info(magnus_batch_t batch, magnus_plan_info_t* info);
 
 /* ---- device timing of the stages --------------------------------------
  * When enabled on a plan, every later magnus_symbolic / magnus_numeric call

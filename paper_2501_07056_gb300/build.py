@@ -15,6 +15,9 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libmagnus.so")
+# input generators (no SpGEMM code): a library of their own
+CSRC_INPUTS = os.path.join(HERE, "csrc_inputs")
+OUT_INPUTS = os.path.join(HERE, "libmagnus_inputs.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
@@ -35,13 +38,12 @@ def _stale(out: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    hdrs = sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
+def _build_lib(src_dir: str, out: str, objdir: str, force: bool, verbose: bool) -> str:
+    srcs = sorted(glob.glob(os.path.join(src_dir, "*.cu")))
+    hdrs = sorted(glob.glob(os.path.join(src_dir, "*.cuh")) + glob.glob(os.path.join(src_dir, "*.h"))
                   + glob.glob(os.path.join(INCLUDE, "*.h")))
-    if not force and not _stale(OUT, srcs + hdrs + [os.path.abspath(__file__)]):
-        return OUT
-    objdir = os.path.join(HERE, "_build")
+    if not force and not _stale(out, srcs + hdrs + [os.path.abspath(__file__)]):
+        return out
     os.makedirs(objdir, exist_ok=True)
     nvcc = _nvcc()
 
@@ -57,14 +59,25 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = OUT + ".tmp%d" % os.getpid()
+    tmp = out + ".tmp%d" % os.getpid()
     cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
            "-Xlinker", "-rpath", "-Xlinker", "/usr/local/cuda/lib64"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, OUT)
-    return OUT
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Builds libmagnus.so and libmagnus_inputs.so (in parallel); returns
+    the path of libmagnus.so."""
+    with cf.ThreadPoolExecutor(max_workers=2) as ex:
+        main = ex.submit(_build_lib, CSRC, OUT, os.path.join(HERE, "_build"), force, verbose)
+        gen = ex.submit(_build_lib, CSRC_INPUTS, OUT_INPUTS, os.path.join(HERE, "_build_inputs"),
+                        force, verbose)
+        gen.result()
+        return main.result()
 
 
 if __name__ == "__main__":

@@ -184,4 +184,50 @@ cudaError_t run_coarse_batch(bool numeric, CoarseArgs& a, cudaStream_t s);
 // Process-wide kernel launch counter.
 void count_launch(int n = 1);
 
+// Records a CUDA error for magnus_last_cuda_error and maps it to a status.
+int api_cuda_fail(cudaError_t e, const char* where);
+
+// A CUDA graph of a stream-ordered sequence, captured on first use and
+// replayed while the pointers it was captured with (its key) stay the same.
+struct GraphSlot {
+  cudaGraphExec_t exec = nullptr;
+  const void* key[8] = {};
+  int nkey = 0;
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    nkey = 0;
+  }
+  // body() enqueues the work on s and returns a magnus status.
+  template <class F>
+  int run(const void* const* k, int nk, cudaStream_t s, F&& body) {
+    bool same = exec != nullptr && nk == nkey;
+    for (int i = 0; same && i < nk; ++i) same = key[i] == k[i];
+    if (!same) {
+      reset();
+      cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+      if (e != cudaSuccess) return api_cuda_fail(e, "cudaStreamBeginCapture");
+      int st = body();
+      cudaGraph_t g = nullptr;
+      e = cudaStreamEndCapture(s, &g);
+      if (st != 0) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      if (e != cudaSuccess) return api_cuda_fail(e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        exec = nullptr;
+        return api_cuda_fail(e, "cudaGraphInstantiate");
+      }
+      for (int i = 0; i < nk; ++i) key[i] = k[i];
+      nkey = nk;
+    }
+    cudaError_t e = cudaGraphLaunch(exec, s);
+    if (e != cudaSuccess) return api_cuda_fail(e, "cudaGraphLaunch");
+    return 0;
+  }
+};
+
 }  // namespace magnus

@@ -27,6 +27,10 @@ static int cuda_fail(cudaError_t e, const char* where) {
   return MAGNUS_CUDA_ERROR;
 }
 
+namespace magnus {
+int api_cuda_fail(cudaError_t e, const char* where) { return cuda_fail(e, where); }
+}
+
 #define CUDA_TRY(x)                                   \
   do {                                                \
     cudaError_t _e = (x);                             \
@@ -172,6 +176,8 @@ struct magnus_plan_s {
   bool timing = false;
   cudaEvent_t ev[2 * MAGNUS_STAGE_COUNT] = {};
   bool ev_used[MAGNUS_STAGE_COUNT] = {};
+  bool use_graph = false;
+  GraphSlot graph;                     // numeric phase (numeric_graph = 1)
   std::vector<cudaEvent_t> big_ev[2];  // per phase: event pairs around each batch's large-bucket kernel
   int big_ev_used[2] = {0, 0};
   cudaStream_t last_stream = nullptr;
@@ -317,6 +323,7 @@ void magnus_free(magnus_plan_t p) {
     if (p->ev[i]) cudaEventDestroy(p->ev[i]);
   for (int ph = 0; ph < 2; ++ph)
     for (cudaEvent_t e : p->big_ev[ph]) cudaEventDestroy(e);
+  p->graph.reset();
   delete p;
 }
 
@@ -335,6 +342,8 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
   if (params) pl->params = *params; else magnus_params_default(&pl->params);
   const magnus_params_t& P = pl->params;
   if (P.force_category < -1 || P.force_category > 3) return MAGNUS_INVALID_ARG;
+  if (P.numeric_graph != 0 && P.numeric_graph != 1) return MAGNUS_INVALID_ARG;
+  pl->use_graph = P.numeric_graph == 1;
   if (P.l2_fetch_bytes != 0 && P.l2_fetch_bytes != 32 && P.l2_fetch_bytes != 64 &&
       P.l2_fetch_bytes != 128)
     return MAGNUS_INVALID_ARG;
@@ -793,6 +802,10 @@ int magnus_numeric(magnus_plan_t pl, const double* a_val, const double* b_val,
   pl->big_ev_used[1] = 0;
   pl->A.val = a_val;
   pl->B.val = b_val;
+  if (pl->use_graph && !pl->timing && s != nullptr) {
+    const void* key[5] = {a_val, b_val, c_row_ptr, c_col, c_val};
+    return pl->graph.run(key, 5, s, [&]() { return run_phase(pl, true, nullptr, c_row_ptr, c_col, c_val, s); });
+  }
   return run_phase(pl, true, nullptr, c_row_ptr, c_col, c_val, s);
 }
 

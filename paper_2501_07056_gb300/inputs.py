@@ -18,6 +18,10 @@ Workloads (the shapes of the paper's test sets, Section 4.2-4.3):
                     (batched products).
   * ``stencil27`` - 27-point stencil on a k^3 grid, truncated at the boundary
                     (served requests).
+  * ``ragged_ctr`` - ragged rows from a counter-based generator (SplitMix64
+                    output function); the on-device generator in
+                    libmagnus_inputs.so implements the same definition, so
+                    matrices drawn on the GPU are reproduced here bit for bit.
 """
 from __future__ import annotations
 
@@ -28,8 +32,8 @@ import numpy as np
 
 __all__ = [
     "CSR", "rng_for", "uniform", "ragged", "rmat", "stencil27", "identity",
-    "permutation", "from_dense", "batched_problems", "served_stream",
-    "workload",
+    "permutation", "from_dense", "batched_sizes", "batched_problems", "served_stream",
+    "workload", "ctr_key", "ctr_u64", "ragged_ctr", "ragged_ctr_nnz",
 ]
 
 
@@ -160,6 +164,93 @@ def ragged(n_rows: int, n_cols: int, kmin: int, kmax: int, seed: int = 0,
     return _csr_from_lengths(n_rows, n_cols, lengths, cols, vals)
 
 
+# ---------------------------------------------------------------------------
+# counter-based generator (definition in include/magnus_inputs.h)
+
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def _mix64(z):
+    z = np.asarray(z, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = z ^ (z >> np.uint64(30))
+        z = z * np.uint64(0xBF58476D1CE4E5B9)
+        z = z ^ (z >> np.uint64(27))
+        z = z * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def ctr_u64(key, i):
+    """ctr(key, i) = mix64(key + (i + 1) * golden), arithmetic mod 2^64."""
+    i = np.asarray(i, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        return _mix64(np.uint64(key) + (i + np.uint64(1)) * np.uint64(0x9E3779B97F4A7C15))
+
+
+def ctr_key(seed: int, matrix_id: int, stream: int) -> np.uint64:
+    with np.errstate(over="ignore"):
+        a = _mix64(np.uint64(seed) * np.uint64(0x9E3779B97F4A7C15)
+                   + np.uint64(0xD1B54A32D192ED03))
+        b = np.uint64(matrix_id) * np.uint64(0xA24BAED4963EE407) + np.uint64(stream)
+        return np.uint64(_mix64(a ^ b))
+
+
+def _scale32(x, m: int):
+    return ((x >> np.uint64(32)) * np.uint64(m)) >> np.uint64(32)
+
+
+def _ragged_ctr_lengths(n_rows, n_cols, kmin, kmax, seed, matrix_id):
+    kl = ctr_key(seed, matrix_id, 1)
+    L = kmin + _scale32(ctr_u64(kl, np.arange(n_rows, dtype=np.uint64)), kmax - kmin + 1)
+    return np.minimum(L.astype(np.int64), n_cols)
+
+
+def ragged_ctr_nnz(n_rows: int, n_cols: int, kmin: int, kmax: int, seed: int = 0,
+                   matrix_id: int = 0) -> int:
+    return int(_ragged_ctr_lengths(n_rows, n_cols, kmin, kmax, seed, matrix_id).sum())
+
+
+def ragged_ctr(n_rows: int, n_cols: int, kmin: int, kmax: int, seed: int = 0,
+               matrix_id: int = 0, lo: float = -1.0, hi: float = 1.0) -> CSR:
+    """Ragged matrix from the counter-based generator: the host twin of
+    magnus_gen_ragged_rowptr/_fill (definition in include/magnus_inputs.h)."""
+    if not (1 <= kmin <= kmax <= 64) or n_cols < 1:
+        raise ValueError("need 1 <= kmin <= kmax <= 64 and n_cols >= 1")
+    L = _ragged_ctr_lengths(n_rows, n_cols, kmin, kmax, seed, matrix_id)
+    kc = ctr_key(seed, matrix_id, 2)
+    kv = ctr_key(seed, matrix_id, 3)
+    acc = np.full((n_rows, kmax), -1, dtype=np.int64)
+    cnt = np.zeros(n_rows, dtype=np.int64)
+    rows_all = np.arange(n_rows, dtype=np.int64)
+    for j in range(1024):
+        act = rows_all[cnt < L]
+        if act.size == 0:
+            break
+        x = ctr_u64(kc, act.astype(np.uint64) * np.uint64(1024) + np.uint64(j))
+        cand = _scale32(x, n_cols).astype(np.int64)
+        present = (acc[act] == cand[:, None]).any(axis=1)
+        take = act[~present]
+        acc[take, cnt[take]] = cand[~present]
+        cnt[take] += 1
+    for r in rows_all[cnt < L]:  # smallest unused columns complete the row
+        v = 0
+        while cnt[r] < L[r]:
+            if not (acc[r, :cnt[r]] == v).any():
+                acc[r, cnt[r]] = v
+                cnt[r] += 1
+            v += 1
+    big = np.int64(1) << np.int64(40)
+    acc[np.arange(kmax)[None, :] >= L[:, None]] = big
+    acc.sort(axis=1)
+    mask = np.arange(kmax)[None, :] < L[:, None]
+    cols = acc[mask].astype(np.int32)
+    k = np.nonzero(mask)[1].astype(np.uint64)
+    r = np.nonzero(mask)[0].astype(np.uint64)
+    u = (ctr_u64(kv, r * np.uint64(64) + k) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    vals = lo + (hi - lo) * u
+    return _csr_from_lengths(n_rows, n_cols, L, cols, vals)
+
+
 def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19,
          c: float = 0.19, seed: int = 0, matrix_id: int = 0) -> CSR:
     """Square R-MAT matrix with 2^scale rows and edge_factor * 2^scale drawn
@@ -235,13 +326,18 @@ def from_dense(d: np.ndarray, pattern: np.ndarray | None = None) -> CSR:
                              d[rows, cols].astype(np.float64))
 
 
+def batched_sizes(count: int, seed: int = 0, n_lo: int = 256, n_hi: int = 65536) -> np.ndarray:
+    """n_i = round(exp(U(ln n_lo, ln n_hi))) for the batched workload."""
+    rng = rng_for(seed, 1_000_000)
+    return np.rint(np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=count))).astype(np.int64)
+
+
 def batched_problems(count: int, seed: int = 0, n_lo: int = 256, n_hi: int = 65536,
                      kmin: int = 2, kmax: int = 32):
     """Independent products C_i = A_i B_i: n_i = round(exp(U(ln n_lo, ln n_hi))),
     A_i and B_i square n_i x n_i with per-row nnz uniform in {kmin..kmax},
     values U(-1, 1)."""
-    rng = rng_for(seed, 1_000_000)
-    ns = np.rint(np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=count))).astype(np.int64)
+    ns = batched_sizes(count, seed, n_lo, n_hi)
     out = []
     for i, n in enumerate(ns):
         A = ragged(int(n), int(n), kmin, kmax, seed, 2 * i + 1)

@@ -36,7 +36,7 @@ class Params(ctypes.Structure):
     _fields_ = [("sort_threshold", c_i32), ("force_category", c_i32),
                 ("chunk_len_fine_log2", c_i32), ("chunk_len_coarse_log2", c_i32),
                 ("dense_chunk_threshold", c_i32), ("validate", c_i32),
-                ("max_scratch_bytes", c_i64), ("l2_fetch_bytes", c_i32), ("reserved", c_i32)]
+                ("max_scratch_bytes", c_i64), ("l2_fetch_bytes", c_i32), ("numeric_graph", c_i32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -93,6 +93,13 @@ SIGNATURES = {
     "magnus_enable_timing": (c_i32, [c_p, ctypes.c_int]),
     "magnus_stage_times": (c_i32, [c_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "magnus_launch_count": (c_u64, []),
+    "magnus_plan_batched": (c_i32, [ctypes.POINTER(c_p), c_i32, ctypes.POINTER(CsrDesc),
+                                    ctypes.POINTER(CsrDesc), ctypes.POINTER(Params), c_p]),
+    "magnus_batch_layout": (c_i32, [c_p, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
+    "magnus_symbolic_batched": (c_i32, [c_p, c_p, ctypes.POINTER(c_i64), c_p]),
+    "magnus_numeric_batched": (c_i32, [c_p, c_p, c_p, c_p, c_p]),
+    "magnus_batch_info": (c_i32, [c_p, ctypes.POINTER(PlanInfo)]),
+    "magnus_free_batched": (None, [c_p]),
     "magnus_chunk_model": (c_i32, [c_i64, c_i64, c_i64, c_i32, ctypes.POINTER(ChunkModel)]),
 }
 
@@ -221,7 +228,7 @@ class DeviceCSR:
 
 def make_params(sort_threshold=0, force_category=CAT_AUTO, chunk_len_fine_log2=0,
                 chunk_len_coarse_log2=0, dense_chunk_threshold=0, validate=0,
-                max_scratch_bytes=0, l2_fetch_bytes=0) -> Params:
+                max_scratch_bytes=0, l2_fetch_bytes=0, numeric_graph=0) -> Params:
     p = magnus_params_default()
     p.sort_threshold = sort_threshold
     p.force_category = force_category
@@ -231,6 +238,7 @@ def make_params(sort_threshold=0, force_category=CAT_AUTO, chunk_len_fine_log2=0
     p.validate = validate
     p.max_scratch_bytes = max_scratch_bytes
     p.l2_fetch_bytes = l2_fetch_bytes
+    p.numeric_graph = numeric_graph
     return p
 
 
@@ -279,6 +287,86 @@ class Plan:
     def free(self):
         if self.handle:
             magnus_free(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class BatchPlan:
+    """Owns a batched plan for products C_i = A_i * B_i (one packed C)."""
+
+    def __init__(self, As, Bs, params: Params | None = None, stream=None):
+        import torch
+        if len(As) != len(Bs) or not As:
+            raise ValueError("need equally many A and B operands (at least one)")
+        self.As, self.Bs = list(As), list(Bs)
+        self.count = len(As)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        da = (CsrDesc * self.count)(*[a.desc(True) for a in self.As])
+        db = (CsrDesc * self.count)(*[b.desc(True) for b in self.Bs])
+        h = c_p()
+        _check(_lib().magnus_plan_batched(ctypes.byref(h), self.count, da, db,
+                                          ctypes.byref(params) if params is not None else None,
+                                          c_p(self.stream.cuda_stream)), "magnus_plan_batched")
+        self.handle = h.value
+        ro = (c_i64 * (self.count + 1))()
+        tot = c_i64()
+        _check(_lib().magnus_batch_layout(c_p(self.handle), ro, ctypes.byref(tot)),
+               "magnus_batch_layout")
+        self.row_offsets = list(ro)
+        self.total_rows = tot.value
+        self.c_row_ptr = None
+        self.c_offsets = None
+        self.c_col = None
+        self.c_val = None
+
+    def symbolic(self) -> list:
+        import torch
+        dev = self.As[0].row_ptr.device
+        self.c_row_ptr = torch.empty(self.total_rows + 1, dtype=torch.int64, device=dev)
+        off = (c_i64 * (self.count + 1))()
+        _check(_lib().magnus_symbolic_batched(c_p(self.handle), c_p(self.c_row_ptr.data_ptr()),
+                                              off, c_p(self.stream.cuda_stream)),
+               "magnus_symbolic_batched")
+        self.c_offsets = list(off)
+        return self.c_offsets
+
+    def numeric(self, c_col=None, c_val=None):
+        import torch
+        dev = self.As[0].row_ptr.device
+        nnz = self.c_offsets[-1]
+        if c_col is None:
+            c_col = self.c_col if self.c_col is not None else \
+                torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
+        if c_val is None:
+            c_val = self.c_val if self.c_val is not None else \
+                torch.empty(max(nnz, 1), dtype=torch.float64, device=dev)
+        self.c_col, self.c_val = c_col, c_val
+        _check(_lib().magnus_numeric_batched(c_p(self.handle), c_p(self.c_row_ptr.data_ptr()),
+                                             c_p(c_col.data_ptr()), c_p(c_val.data_ptr()),
+                                             c_p(self.stream.cuda_stream)),
+               "magnus_numeric_batched")
+        return c_col[:nnz], c_val[:nnz]
+
+    def result(self, i: int) -> DeviceCSR:
+        """C_i as a DeviceCSR (views into the packed C; row pointers copied)."""
+        r0, r1 = self.row_offsets[i], self.row_offsets[i + 1]
+        e0, e1 = self.c_offsets[i], self.c_offsets[i + 1]
+        rp = self.c_row_ptr[r0:r1 + 1] - e0
+        return DeviceCSR(r1 - r0, self.Bs[i].n_cols, rp, self.c_col[e0:e1], self.c_val[e0:e1])
+
+    def info(self) -> dict:
+        info = PlanInfo()
+        _check(_lib().magnus_batch_info(c_p(self.handle), ctypes.byref(info)), "magnus_batch_info")
+        return info.as_dict()
+
+    def free(self):
+        if self.handle:
+            _lib().magnus_free_batched(c_p(self.handle))
             self.handle = 0
 
     def __del__(self):

@@ -11,14 +11,10 @@ from paper_2501_07056_gb300 import magnus
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared():
-    names = set()
-    for fn in os.listdir(os.path.join(ROOT, "include")):
-        if fn.endswith(".h"):
-            src = open(os.path.join(ROOT, "include", fn)).read()
-            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names.update(re.findall(r"\b(magnus_\w+)\s*\(", src))
-    return sorted(names)
+def _declared(header):
+    src = open(os.path.join(ROOT, "include", header)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(magnus_\w+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -28,13 +24,38 @@ def lib():
     return magnus._lib()
 
 
+def test_every_header_is_checked():
+    assert sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")) == \
+        ["magnus.h", "magnus_inputs.h"]
+
+
 def test_every_declared_symbol_is_exported(lib):
-    names = _declared()
+    names = _declared("magnus.h")
     assert len(names) >= 10
     raw = ctypes.CDLL(magnus.LIB_PATH)
     for n in names:
         assert hasattr(raw, n), n
         assert n in magnus.SIGNATURES, n
+
+
+def test_input_generator_symbols_are_exported(lib):
+    from paper_2501_07056_gb300 import gen_device
+    names = _declared("magnus_inputs.h")
+    assert len(names) == 3
+    raw = ctypes.CDLL(gen_device.LIB_PATH)
+    for n in names:
+        assert hasattr(raw, n), n
+        assert n in gen_device.SIGNATURES, n
+    # the generator library holds no SpGEMM entry point
+    assert not hasattr(raw, "magnus_plan")
+
+
+def test_generator_rejects_bad_args_without_gpu(lib):
+    from paper_2501_07056_gb300 import gen_device
+    g = gen_device._lib()
+    assert g.magnus_gen_ragged_rowptr(10, 10, 0, 5, 0, 0, None, None, None) == 1
+    assert g.magnus_gen_ragged_rowptr(10, 10, 2, 65, 0, 0, 8, None, None) == 1
+    assert g.magnus_gen_stencil27(0, 8, 8, 8, None) == 1
 
 
 def test_strerror(lib):

@@ -59,3 +59,32 @@ def test_batched_and_served_descriptors():
     reqs = inputs.served_stream(50, seed=0)
     assert all(16 <= r["k"] <= 96 for r in reqs)
     assert inputs.served_stream(50, seed=0) == reqs
+
+
+def test_splitmix64_first_output():
+    # SplitMix64 seeded with 0: its first output is 0xE220A8397B1DCDAF
+    # (Steele, Lea and Flood 2014; the reference sequence of the generator).
+    assert int(inputs.ctr_u64(np.uint64(0), 0)) == 0xE220A8397B1DCDAF
+
+
+def test_ragged_ctr_properties():
+    A = inputs.ragged_ctr(4000, 700, 2, 32, seed=0, matrix_id=9)
+    A.validate()
+    L = np.diff(A.row_ptr)
+    assert L.min() >= 2 and L.max() <= 32 and abs(L.mean() - 17) < 0.6
+    assert A.nnz == inputs.ragged_ctr_nnz(4000, 700, 2, 32, seed=0, matrix_id=9)
+    assert A.val.min() >= -1 and A.val.max() < 1
+    B = inputs.ragged_ctr(4000, 700, 2, 32, seed=0, matrix_id=9)
+    assert np.array_equal(A.col, B.col) and np.array_equal(A.val, B.val)
+    C = inputs.ragged_ctr(4000, 700, 2, 32, seed=0, matrix_id=10)
+    assert not np.array_equal(A.row_ptr, C.row_ptr)
+    # columns are spread over the whole range
+    assert A.col.min() < 10 and A.col.max() > 690
+
+
+def test_ragged_ctr_full_rows():
+    # rows as long as the column range: every column once (the fill-in rule)
+    A = inputs.ragged_ctr(50, 20, 20, 32, seed=3, matrix_id=1)
+    A.validate()
+    assert np.all(np.diff(A.row_ptr) == 20)
+    assert np.array_equal(A.col.reshape(50, 20), np.tile(np.arange(20, dtype=np.int32), (50, 1)))
