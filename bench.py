@@ -464,23 +464,34 @@ def run_batched(args, dist):
     stream = torch.cuda.current_stream()
     nw = max(1, min(args.batch_waves, count))
     bounds = [round(w * count / nw) for w in range(nw + 1)]
-    stats = {"n_inter": 0, "nnz_c": 0}
+    stats = {"n_inter": 0, "nnz_c": 0, "stage_ms": {}, "rows_per_category": [0, 0, 0, 0]}
 
     def step(record=False):
         tot_i = tot_c = 0
+        st = {}
         for w in range(nw):
             lo, hi = bounds[w], bounds[w + 1]
             bp = magnus.BatchPlan(As[lo:hi], Bs[lo:hi], params, stream)
+            if record:
+                bp.enable_timing(True)
             off = bp.symbolic()
             col, val = bp.numeric()
             del col, val
             bp.c_col = bp.c_val = None
             if record:
-                tot_i += bp.info()["n_interprod"]
+                info = bp.info()
+                tot_i += info["n_interprod"]
                 tot_c += off[-1]
+                for k, v in bp.stage_times().items():
+                    st[k] = st.get(k, 0.0) + v
+                for c in range(4):
+                    stats["rows_per_category"][c] += info["rows_per_category"][c]
+                stats["plan"] = {k: info[k] for k in (
+                    "chunk_len_fine_log2", "chunk_len_coarse_log2", "n_chunks_coarse",
+                    "n_batches_coarse", "sort_threshold", "dense_cols", "scratch_bytes")}
             bp.free()
         if record:
-            stats["n_inter"], stats["nnz_c"] = tot_i, tot_c
+            stats["n_inter"], stats["nnz_c"], stats["stage_ms"] = tot_i, tot_c, st
 
     step(record=True)
     for _ in range(args.warmup - 1):
@@ -537,6 +548,9 @@ def run_batched(args, dist):
                                  "gflops": 2.0 * n_inter / (ms_one * 1e-3) / 1e9},
         "clocks": clk,
         "gpu_launches": n_launch,
+        "detail": {"stage_ms_untimed_step": stats["stage_ms"],
+                   "rows_per_category": stats["rows_per_category"],
+                   "last_wave_plan": stats.get("plan")},
     }
 
 

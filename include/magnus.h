@@ -82,8 +82,10 @@ typedef struct {
  * re-derived for shared memory and L2; see magnus_chunk_model).
  *
  * sort_threshold      rows with P_i < sort_threshold use the sort accumulator
- *                     (Section 3.1, category 1).  Range 1..257; 0 = 256
- *                     (the threshold of Section 4.1.1).
+ *                     (Section 3.1, category 1).  Range 1..1025; 0 = 256
+ *                     (the threshold of Section 4.1.1).  Rows of up to 256
+ *                     products sort in one warp, rows of 257..1024 in one
+ *                     thread block.
  * force_category      -1 = automatic; otherwise every non-empty row is put in
  *                     that category (used to exercise each stage).
  * chunk_len_fine_log2 log2 of the fine chunk length (columns) for the numeric
@@ -113,7 +115,14 @@ typedef struct {
  *                     kernel).  Needs a stream other than the legacy default
  *                     stream (NULL), else the launches run uncaptured; stage
  *                     timing (magnus_enable_timing) also runs uncaptured.
- *                     0 = no graph.                                          */
+ *                     0 = no graph.
+ * wide_sort_max       automatic categorisation only: a row whose column range
+ *                     is too wide for the dense accumulator and that has at
+ *                     most this many products uses the sort accumulator
+ *                     instead of the fine/coarse levels (GPU rule; the paper
+ *                     sends such rows to the reorder levels).  Range 1..1024;
+ *                     0 = 1024; -1 = off.
+ * reserved            must be 0.                                             */
 typedef struct {
   int32_t sort_threshold;
   int32_t force_category;
@@ -124,6 +133,8 @@ typedef struct {
   int64_t max_scratch_bytes;
   int32_t l2_fetch_bytes;
   int32_t numeric_graph;
+  int32_t wide_sort_max;
+  int32_t reserved;
 } magnus_params_t;
 
 /* Fill *p with the automatic values.  Returns MAGNUS_INVALID_ARG on NULL. */
@@ -248,6 +259,10 @@ int magnus_symbolic_batched(magnus_batch_t batch, int64_t* c_row_ptr, int64_t* c
 int magnus_numeric_batched(magnus_batch_t batch, const int64_t* c_row_ptr, int32_t* c_col,
                            double* c_val, void* stream);
 void magnus_free_batched(magnus_batch_t batch);
+/* The inner plan of the packed problem (owned by the batch; valid until
+ * magnus_free_batched), for magnus_enable_timing / magnus_stage_times /
+ * magnus_plan_info.  NULL for a NULL batch. */
+magnus_plan_t magnus_batch_inner_plan(magnus_batch_t batch);
 
 /* ---- plan introspection ------------------------------------------------ */
 typedef struct {

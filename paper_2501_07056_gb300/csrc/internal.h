@@ -12,20 +12,24 @@
 namespace magnus {
 
 // Row bins.  Sort rows are split by capacity (32 * E products, E = 1,2,4,8)
-// so each warp kernel sorts in registers with a fixed network size.
+// so each warp kernel sorts in registers with a fixed network size; rows of
+// 257..1024 products sort in one thread block (bins SORT512, SORT1024).
 enum Bin : int {
   BIN_EMPTY = 0,
   BIN_SORT32 = 1,
   BIN_SORT64 = 2,
   BIN_SORT128 = 3,
   BIN_SORT256 = 4,
-  BIN_DENSE = 5,
-  BIN_FINE = 6,
-  BIN_COARSE = 7,
-  NUM_BINS = 8
+  BIN_SORT512 = 5,
+  BIN_SORT1024 = 6,
+  BIN_DENSE = 7,
+  BIN_FINE = 8,
+  BIN_COARSE = 9,
+  NUM_BINS = 10
 };
 
-constexpr int SORT_MAX = 256;        // largest sort-row capacity
+constexpr int SORT_MAX = 256;        // largest warp sort-row capacity
+constexpr int SORT_BLOCK_MAX = 1024; // largest block sort-row capacity
 constexpr int DENSE_NT = 256;        // threads of the dense/fine block kernels
 constexpr int FINE_MAX_CHUNKS = 4096;  // fine chunks one block can bookkeep in smem
 constexpr int GROUP_SORT_CAP = 1024; // block sort capacity for merged fine chunks
@@ -40,6 +44,8 @@ struct CatParams {
   int64_t fine_max_products;  // ... and its products fit one block's staging slab
   int32_t prefer_fine;        // automatic mode: fine level (1) or coarse level (0) for
                               // rows wider than the dense accumulator
+  int32_t wide_sort_max;      // automatic mode: rows wider than the dense accumulator
+                              // with at most this many products use the sort bins
 };
 
 struct Csr {
@@ -99,6 +105,8 @@ struct SortArgs {
   double* c_val;
 };
 cudaError_t launch_sort_rows(int bin, bool numeric, const SortArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_sort_rows_block(int bin, bool numeric, const SortArgs& a, int num_sms,
+                                   cudaStream_t s);
 
 // Dense rows (block per row).
 struct DenseArgs {

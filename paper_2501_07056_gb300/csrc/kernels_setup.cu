@@ -86,12 +86,16 @@ __global__ void k_rowinfo(Csr A, Csr B, CatParams cp, int64_t* __restrict__ P,
     // category
     int b = BIN_EMPTY;
     bool need_range = false;
+    auto sort_bin = [](int64_t q) {
+      return q <= 32 ? BIN_SORT32 : q <= 64 ? BIN_SORT64 : q <= 128 ? BIN_SORT128
+             : q <= 256 ? BIN_SORT256 : q <= 512 ? BIN_SORT512 : BIN_SORT1024;
+    };
     if (p > 0) {
-      const bool sort_ok = p <= SORT_MAX;
+      const bool sort_ok = p <= SORT_BLOCK_MAX;
       const bool want_sort = (cp.force == MAGNUS_CAT_SORT) ? sort_ok
                              : (cp.force < 0 ? (p < cp.sort_threshold) : false);
       if (want_sort) {
-        b = p <= 32 ? BIN_SORT32 : p <= 64 ? BIN_SORT64 : p <= 128 ? BIN_SORT128 : BIN_SORT256;
+        b = sort_bin(p);
       } else {
         need_range = true;
       }
@@ -127,6 +131,7 @@ __global__ void k_rowinfo(Csr A, Csr B, CatParams cp, int64_t* __restrict__ P,
       if (cp.force == MAGNUS_CAT_COARSE) b = BIN_COARSE;
       else if (cp.force == MAGNUS_CAT_FINE) b = fine_ok ? BIN_FINE : BIN_COARSE;
       else if (dense_ok) b = BIN_DENSE;
+      else if (cp.force < 0 && p <= cp.wide_sort_max) b = sort_bin(p);
       else b = (cp.prefer_fine && fine_ok) ? BIN_FINE : BIN_COARSE;
     }
     if (active && sub == 0) {

@@ -1,0 +1,264 @@
+// Sort-category rows of 257..1024 products (Section 3.1, category 1, with the
+// sort accumulator of Algorithm 2 widened to a thread block).
+//
+// A row of bin SORT512 / SORT1024 is handled by one block of CAP/8 threads
+// (64 or 128), eight products per thread.  The products are generated from
+// A and B, their values (numeric pass) parked in shared memory by slot, and
+// the (column, slot) keys sorted by a bitonic network: partners within a
+// thread are swapped in registers, partners within a warp exchanged by
+// shuffles, partners in other warps through shared memory.  Equal columns
+// are then adjacent with their slots ascending, so summing a run of equal
+// columns in sorted order sums the products in the traversal order of
+// Algorithm 1.  The symbolic pass counts the runs; the numeric pass sorts
+// again (no order is recorded for these bins) and writes one entry per run,
+// consecutive threads writing consecutive entries of the row of C.
+//
+// Blocks are persistent: each takes rows idx = blockIdx.x, + gridDim.x, ...
+#include "sort_accum.cuh"
+
+namespace magnus {
+
+namespace {
+
+constexpr int BR = 8;  // keys per thread
+
+template <typename K>
+__device__ __forceinline__ void cmp_swap(K& x, K& y, bool up) {
+  const bool sw = up ? (x > y) : (x < y);
+  const K t = x;
+  x = sw ? y : x;
+  y = sw ? t : y;
+}
+
+// Bitonic sort of NT * BR keys; thread t holds positions t * BR + e.
+template <int NT, typename K>
+__device__ __forceinline__ void block_sort_keys(K (&key)[BR], K* s_key) {
+  constexpr int CAP = NT * BR;
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int k = 2; k <= CAP; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j < BR) {
+#pragma unroll
+        for (int e = 0; e < BR; ++e) {
+          if ((e & j) == 0) {
+            const int q = t * BR + e;
+            cmp_swap(key[e], key[e | j], (q & k) == 0);
+          }
+        }
+      } else if (j < 32 * BR) {
+        const int lm = j / BR;  // partner lane distance
+#pragma unroll
+        for (int e = 0; e < BR; ++e) {
+          const int q = t * BR + e;
+          const K o = __shfl_xor_sync(FULL, key[e], lm);
+          const bool up = (q & k) == 0;
+          const bool lower = (q & j) == 0;
+          // the lower position keeps the smaller key when ascending
+          const bool take_min = (lower == up);
+          key[e] = take_min ? (o < key[e] ? o : key[e]) : (o > key[e] ? o : key[e]);
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < BR; ++e) s_key[t * BR + e] = key[e];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < BR; ++e) {
+          const int q = t * BR + e;
+          const K o = s_key[q ^ j];
+          const bool up = (q & k) == 0;
+          const bool lower = (q & j) == 0;
+          const bool take_min = (lower == up);
+          key[e] = take_min ? (o < key[e] ? o : key[e]) : (o > key[e] ? o : key[e]);
+        }
+        __syncthreads();
+      }
+    }
+  }
+}
+
+template <int CAPLOG, typename K, bool NUMERIC>
+__global__ void __launch_bounds__((1 << CAPLOG) / BR) k_sort_rows_block(SortArgs a) {
+  constexpr int CAP = 1 << CAPLOG;
+  constexpr int NT = CAP / BR;
+  constexpr int NWB = NT / 32;
+  constexpr int SB = CAPLOG;  // slot bits of a key
+  constexpr int HW = CAP / 32;
+  using KT = KeyTraits<K>;
+  __shared__ K s_key[CAP];
+  __shared__ int32_t s_start[CAP + 1];  // first slot of each non-empty segment
+  __shared__ int64_t s_bs[CAP];         // B.rowPtr of the segment's B row
+  __shared__ double s_av[NUMERIC ? CAP : 1];
+  __shared__ double s_val[NUMERIC ? CAP : 1];  // product value by slot
+  __shared__ uint32_t s_head[HW];
+  __shared__ int32_t s_pw[HW];
+  __shared__ int32_t s_ws[NWB + 1];
+  __shared__ int32_t s_ws2[NWB + 1];
+  const int t = threadIdx.x, lane = lane_id(), w = warp_id();
+
+  for (int64_t idx = blockIdx.x; idx < a.n_rows; idx += gridDim.x) {
+    const RowDesc d = a.desc[idx];
+    // 1. segments: the non-empty B rows referenced by the row, in stored
+    //    order, with their first slots (block scan of the lengths)
+    int nseg = 0, P = 0;
+    for (int j0 = 0; j0 < d.na; j0 += NT) {
+      const int j = j0 + t;
+      int L = 0;
+      int64_t bs = 0;
+      double av = 0.0;
+      if (j < d.na) {
+        L = a.seg_len[d.as + j];
+        bs = a.seg_bs[d.as + j];
+        if (NUMERIC) av = a.A.val[d.as + j];
+      }
+      const int nz = L > 0 ? 1 : 0;
+      const int incL = warp_inclusive_scan(L);
+      const int incZ = warp_inclusive_scan(nz);
+      if (lane == 31) {
+        s_ws[w] = incL;
+        s_ws2[w] = incZ;
+      }
+      __syncthreads();
+      int offL = 0, offZ = 0, totL = 0, totZ = 0;
+#pragma unroll
+      for (int i = 0; i < NWB; ++i) {
+        offL += (i < w) ? s_ws[i] : 0;
+        offZ += (i < w) ? s_ws2[i] : 0;
+        totL += s_ws[i];
+        totZ += s_ws2[i];
+      }
+      if (L > 0) {
+        const int g = nseg + offZ + incZ - 1;
+        s_start[g] = P + offL + incL - L;
+        s_bs[g] = bs;
+        if (NUMERIC) s_av[g] = av;
+      }
+      nseg += totZ;
+      P += totL;
+      __syncthreads();
+    }
+    if (t == 0) s_start[nseg] = P;
+    __syncthreads();
+    // 2. expand: slot s = e * NT + t (consecutive threads read consecutive
+    //    entries of a B row); all gathers are issued before any is used
+    int64_t kk[BR];
+    int gg[BR];
+#pragma unroll
+    for (int e = 0; e < BR; ++e) {
+      const int s = e * NT + t;
+      kk[e] = -1;
+      gg[e] = 0;
+      if (s < P) {
+        const int g = upper_bound_i32(s_start, nseg, s) - 1;
+        gg[e] = g;
+        kk[e] = s_bs[g] + (s - s_start[g]);
+      }
+    }
+    int32_t cg[BR];
+    double vg[BR];
+#pragma unroll
+    for (int e = 0; e < BR; ++e) {
+      cg[e] = kk[e] >= 0 ? __ldg(a.B.col + kk[e]) : 0;
+      if (NUMERIC) vg[e] = kk[e] >= 0 ? __ldg(a.B.val + kk[e]) : 0.0;
+    }
+    K key[BR];
+#pragma unroll
+    for (int e = 0; e < BR; ++e) {
+      const int s = e * NT + t;
+      key[e] = (s < P) ? KT::template make<SB>(cg[e], s) : ~K(0);
+      if (NUMERIC && s < P) s_val[s] = s_av[gg[e]] * vg[e];
+    }
+    // 3. sort
+    block_sort_keys<NT>(key, s_key);
+#pragma unroll
+    for (int e = 0; e < BR; ++e) s_key[t * BR + e] = key[e];
+    __syncthreads();
+    // 4. run heads: position q starts a run if its column differs from q-1
+    uint32_t hb = 0;
+#pragma unroll
+    for (int e = 0; e < BR; ++e) {
+      const int q = t * BR + e;
+      const int32_t c = KT::template col<SB>(key[e]);
+      const int32_t pc = q == 0 ? -1 : KT::template col<SB>(s_key[q - 1]);
+      if (q < P && (q == 0 || c != pc)) hb |= 1u << e;
+    }
+    // threads 4m..4m+3 hold the 32 positions of head word m
+    uint32_t word = hb << (8 * (t & 3));
+    word |= __shfl_xor_sync(FULL, word, 1);
+    word |= __shfl_xor_sync(FULL, word, 2);
+    if ((t & 3) == 0) s_head[t >> 2] = word;
+    __syncthreads();
+    if (!NUMERIC) {
+      if (w == 0) {
+        int c = 0;
+        for (int i = lane; i < HW; i += 32) c += __popc(s_head[i]);
+        c = warp_sum(c);
+        if (lane == 0) a.out_cnt[d.row] = c;
+      }
+    } else {
+      if (w == 0) {
+        const int c = lane < HW ? __popc(s_head[lane]) : 0;
+        const int inc = warp_inclusive_scan(c);
+        if (lane < HW) s_pw[lane] = inc - c;
+      }
+      __syncthreads();
+      const int64_t crp = a.c_rp[d.row];
+#pragma unroll 1
+      for (int e = 0; e < BR; ++e) {
+        const int q = e * NT + t;
+        if (q >= P) break;
+        const uint32_t hw = s_head[q >> 5];
+        if (!((hw >> (q & 31)) & 1u)) continue;
+        const int o = s_pw[q >> 5] + __popc(hw & ((1u << (q & 31)) - 1u));
+        const K kq = s_key[q];
+        const int32_t c = KT::template col<SB>(kq);
+        double acc = s_val[KT::template slot<SB>(kq)];
+        for (int q2 = q + 1; q2 < P; ++q2) {
+          const K k2 = s_key[q2];
+          if (KT::template col<SB>(k2) != c) break;
+          acc += s_val[KT::template slot<SB>(k2)];
+        }
+        a.c_col[crp + o] = c;
+        a.c_val[crp + o] = acc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int CAPLOG, typename K, bool NUMERIC>
+cudaError_t launch_block(const SortArgs& a, int num_sms, cudaStream_t s) {
+  constexpr int NT = (1 << CAPLOG) / BR;
+  auto kern = k_sort_rows_block<CAPLOG, K, NUMERIC>;
+  int per_sm = 0;
+  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, 0);
+  if (err != cudaSuccess) return err;
+  if (per_sm < 1) per_sm = 1;
+  int64_t blocks = a.n_rows;
+  const int64_t cap = (int64_t)num_sms * per_sm;
+  if (blocks > cap) blocks = cap;
+  kern<<<(unsigned)blocks, NT, 0, s>>>(a);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_sort_rows_block(int bin, bool numeric, const SortArgs& a, int num_sms,
+                                   cudaStream_t s) {
+  if (a.n_rows == 0) return cudaSuccess;
+  const bool big = bin == BIN_SORT1024;
+  if (a.key32) {
+    if (numeric) return big ? launch_block<10, uint32_t, true>(a, num_sms, s)
+                            : launch_block<9, uint32_t, true>(a, num_sms, s);
+    return big ? launch_block<10, uint32_t, false>(a, num_sms, s)
+               : launch_block<9, uint32_t, false>(a, num_sms, s);
+  }
+  if (numeric) return big ? launch_block<10, uint64_t, true>(a, num_sms, s)
+                          : launch_block<9, uint64_t, true>(a, num_sms, s);
+  return big ? launch_block<10, uint64_t, false>(a, num_sms, s)
+             : launch_block<9, uint64_t, false>(a, num_sms, s);
+}
+
+}  // namespace magnus

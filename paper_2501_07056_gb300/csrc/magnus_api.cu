@@ -353,7 +353,9 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
     if (cur != (size_t)P.l2_fetch_bytes)
       CUDA_TRY(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)P.l2_fetch_bytes));
   }
-  if (P.sort_threshold < 0 || P.sort_threshold > SORT_MAX + 1) return MAGNUS_INVALID_ARG;
+  if (P.sort_threshold < 0 || P.sort_threshold > SORT_BLOCK_MAX + 1) return MAGNUS_INVALID_ARG;
+  if (P.wide_sort_max < -1 || P.wide_sort_max > SORT_BLOCK_MAX) return MAGNUS_INVALID_ARG;
+  if (P.reserved != 0) return MAGNUS_INVALID_ARG;
   pl->sort_T = P.sort_threshold > 0 ? P.sort_threshold : 256;
   const int64_t m_c = B->n_cols > 0 ? B->n_cols : 1;
   pl->col_bits = ceil_log2_i64(m_c);
@@ -382,8 +384,8 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
   pl->n_chunks_coarse = (int)((m_c + ((int64_t)1 << sc) - 1) >> sc);
   pl->dthr = P.dense_chunk_threshold > 0 ? P.dense_chunk_threshold : 256;
   if (pl->dthr > GROUP_SORT_CAP) pl->dthr = GROUP_SORT_CAP;
-  for (int b = BIN_SORT32; b <= BIN_SORT256; ++b) {
-    const int sb = 4 + b;  // log2(32 * E): 5, 6, 7, 8
+  for (int b = BIN_SORT32; b <= BIN_SORT1024; ++b) {
+    const int sb = 4 + b;  // log2 of the bin capacity: 5, 6, 7, 8, 9, 10
     pl->key32[b] = (pl->col_bits + sb <= 32) ? 1 : 0;
   }
   size_t free_b = 0, total_b = 0;
@@ -435,6 +437,10 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
   // rows wider than the dense accumulator use the coarse level unless the
   // fine level is forced.
   cp.prefer_fine = 0;
+  // Rows too wide for the dense accumulator but with at most this many
+  // products sort in registers (one warp) or in one block instead of taking
+  // the coarse level's four passes over their products.
+  cp.wide_sort_max = P.wide_sort_max == 0 ? SORT_BLOCK_MAX : (P.wide_sort_max < 0 ? 0 : P.wide_sort_max);
   CUDA_TRY(launch_rowinfo(pl->A, pl->B, cp, pl->P, pl->bin, pl->lo, pl->hi, pl->seg_bs,
                           pl->seg_len, s));
   int64_t* stats;
@@ -498,7 +504,7 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
   MAG_TRY(copy_bin(BIN_DENSE, drows, dP, nullptr, nullptr));
   MAG_TRY(copy_bin(BIN_FINE, pl->fine_rows, pl->fine_P, &pl->fine_lo, &pl->fine_hi));
   MAG_TRY(copy_bin(BIN_COARSE, pl->coarse_rows, pl->coarse_P, nullptr, nullptr));
-  for (int b = BIN_SORT32; b <= BIN_SORT256; ++b)
+  for (int b = BIN_SORT32; b <= BIN_SORT1024; ++b)
     pl->rows_cat[MAGNUS_CAT_SORT] += pl->bin_off[b + 1] - pl->bin_off[b];
   pl->rows_cat[MAGNUS_CAT_DENSE] = (int64_t)drows.size();
   pl->rows_cat[MAGNUS_CAT_FINE] = (int64_t)pl->fine_rows.size();
@@ -590,7 +596,7 @@ static int run_phase(magnus_plan_t pl, bool numeric, int64_t* out_cnt, const int
   // sort rows
   {
     StageTimer tm(pl, st_base + 0, s);
-    for (int b = BIN_SORT32; b <= BIN_SORT256; ++b) {
+    for (int b = BIN_SORT32; b <= BIN_SORT1024; ++b) {
       SortArgs a{};
       a.A = A;
       a.B = B;
@@ -604,7 +610,8 @@ static int run_phase(magnus_plan_t pl, bool numeric, int64_t* out_cnt, const int
       a.c_rp = c_rp;
       a.c_col = c_col;
       a.c_val = c_val;
-      CUDA_TRY(launch_sort_rows(b, numeric, a, pl->num_sms, s));
+      if (b <= BIN_SORT256) CUDA_TRY(launch_sort_rows(b, numeric, a, pl->num_sms, s));
+      else CUDA_TRY(launch_sort_rows_block(b, numeric, a, pl->num_sms, s));
     }
   }
   // dense rows
@@ -856,7 +863,7 @@ int magnus_numeric_noalloc(magnus_plan_t pl, const double* a_val, const double* 
   Csr A = pl->A, B = pl->B;
   A.val = a_val;
   B.val = b_val;
-  for (int b = BIN_SORT32; b <= BIN_SORT256; ++b) {
+  for (int b = BIN_SORT32; b <= BIN_SORT1024; ++b) {
     SortArgs a{};
     a.A = A;
     a.B = B;
@@ -869,7 +876,8 @@ int magnus_numeric_noalloc(magnus_plan_t pl, const double* a_val, const double* 
     a.c_rp = c_row_ptr;
     a.c_col = c_col;
     a.c_val = c_val;
-    CUDA_TRY(launch_sort_rows(b, true, a, pl->num_sms, s));
+    if (b <= BIN_SORT256) CUDA_TRY(launch_sort_rows(b, true, a, pl->num_sms, s));
+    else CUDA_TRY(launch_sort_rows_block(b, true, a, pl->num_sms, s));
   }
   {
     DenseArgs a{};

@@ -326,6 +326,8 @@ int magnus_numeric_batched(magnus_batch_t b, const int64_t* c_row_ptr, int32_t* 
   return body();
 }
 
+magnus_plan_t magnus_batch_inner_plan(magnus_batch_t b) { return b ? b->inner : nullptr; }
+
 int magnus_batch_info(magnus_batch_t b, magnus_plan_info_t* info) {
   if (!b || !info) return MAGNUS_INVALID_ARG;
   return magnus_plan_info(b->inner, info);

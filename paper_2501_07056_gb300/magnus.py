@@ -36,7 +36,7 @@ class Params(ctypes.Structure):
     _fields_ = [("sort_threshold", c_i32), ("force_category", c_i32),
                 ("chunk_len_fine_log2", c_i32), ("chunk_len_coarse_log2", c_i32),
                 ("dense_chunk_threshold", c_i32), ("validate", c_i32),
-                ("max_scratch_bytes", c_i64), ("l2_fetch_bytes", c_i32), ("numeric_graph", c_i32)]
+                ("max_scratch_bytes", c_i64), ("l2_fetch_bytes", c_i32), ("numeric_graph", c_i32), ("wide_sort_max", c_i32), ("reserved", c_i32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -100,6 +100,7 @@ SIGNATURES = {
     "magnus_numeric_batched": (c_i32, [c_p, c_p, c_p, c_p, c_p]),
     "magnus_batch_info": (c_i32, [c_p, ctypes.POINTER(PlanInfo)]),
     "magnus_free_batched": (None, [c_p]),
+    "magnus_batch_inner_plan": (c_p, [c_p]),
     "magnus_chunk_model": (c_i32, [c_i64, c_i64, c_i64, c_i32, ctypes.POINTER(ChunkModel)]),
 }
 
@@ -228,7 +229,8 @@ class DeviceCSR:
 
 def make_params(sort_threshold=0, force_category=CAT_AUTO, chunk_len_fine_log2=0,
                 chunk_len_coarse_log2=0, dense_chunk_threshold=0, validate=0,
-                max_scratch_bytes=0, l2_fetch_bytes=0, numeric_graph=0) -> Params:
+                max_scratch_bytes=0, l2_fetch_bytes=0, numeric_graph=0,
+                wide_sort_max=0) -> Params:
     p = magnus_params_default()
     p.sort_threshold = sort_threshold
     p.force_category = force_category
@@ -239,6 +241,7 @@ def make_params(sort_threshold=0, force_category=CAT_AUTO, chunk_len_fine_log2=0
     p.max_scratch_bytes = max_scratch_bytes
     p.l2_fetch_bytes = l2_fetch_bytes
     p.numeric_graph = numeric_graph
+    p.wide_sort_max = wide_sort_max
     return p
 
 
@@ -363,6 +366,12 @@ class BatchPlan:
         info = PlanInfo()
         _check(_lib().magnus_batch_info(c_p(self.handle), ctypes.byref(info)), "magnus_batch_info")
         return info.as_dict()
+
+    def enable_timing(self, on=True):
+        magnus_enable_timing(_lib().magnus_batch_inner_plan(c_p(self.handle)), on)
+
+    def stage_times(self) -> dict:
+        return magnus_stage_times(_lib().magnus_batch_inner_plan(c_p(self.handle)))
 
     def free(self):
         if self.handle:

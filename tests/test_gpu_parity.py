@@ -62,6 +62,31 @@ def test_ragged_mixed_categories(seed, T):
     assert_parity(got, A, B)
 
 
+@pytest.mark.parametrize("T,wide", [(512, 0), (1025, 0), (0, 0), (0, -1), (100, 300)])
+def test_block_sort_bins(T, wide):
+    # rows of about 200-1600 products over 200000 columns: the block sort bins
+    # (257..1024 products), the wide-row rule, and coarse rows above 1024
+    A = inputs.ragged(2500, 6000, 8, 40, seed=4, matrix_id=1)
+    B = inputs.ragged(6000, 200000, 8, 40, seed=4, matrix_id=2)
+    got = run_gpu(A, B, P(sort_threshold=T, wide_sort_max=wide, validate=1))
+    assert_parity(got, A, B)
+    lens = np.diff(A.row_ptr)
+    Bl = np.diff(B.row_ptr)
+    Prow = np.add.reduceat(Bl[A.col], A.row_ptr[:-1]) * (lens > 0)
+    cats = got["info"]["rows_per_category"]
+    limit = max(T - 1 if T else 255, {0: 1024, -1: 0}.get(wide, wide))
+    assert cats[SORT] == int(((Prow > 0) & (Prow <= limit)).sum())
+
+
+def test_block_sort_64bit_keys():
+    # 2^27 columns: column + 10 slot bits exceed 32 bits
+    A = inputs.ragged(1500, 3000, 10, 40, seed=6, matrix_id=1)
+    B = inputs.ragged(3000, 1 << 27, 10, 40, seed=6, matrix_id=2)
+    got = run_gpu(A, B, P(sort_threshold=1025))
+    assert_parity(got, A, B)
+    assert got["info"]["key_bits32"] == 0
+
+
 @pytest.mark.parametrize("force", [-1, SORT, DENSE, FINE, COARSE])
 def test_rmat_small(force):
     A = inputs.rmat(13, 16, seed=0)
