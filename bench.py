@@ -54,6 +54,10 @@ WORKLOADS = {
               "duplicates merged, FP64 U(0,1), seed 0",
     "rmat16": "C=A*A, A R-MAT scale 16, edge factor 16, (a,b,c)=(.57,.19,.19), "
               "duplicates merged, FP64 U(0,1), seed 0 (profiling size)",
+    "served": "open-loop stream of SpGEMM requests, Poisson arrivals, each C=A*B with A the "
+              "27-point stencil on a k^3 grid (k uniform in {16..96}) and B n x n (n=k^3) with "
+              "nnz/row uniform in {4..16} (counter-based generator, drawn on the device), FP64, "
+              "seed 0",
     "batched4096": "4096 independent products C_i=A_i*B_i, n_i log-uniform in [256, 65536], "
                    "A_i and B_i n_i x n_i with nnz/row uniform in {2..32} (counter-based "
                    "generator, drawn on the device), FP64 U(-1,1), seed 0",
@@ -82,6 +86,10 @@ def parse_args(argv=None):
                    help="batched workload: number of products")
     p.add_argument("--batch-waves", type=int, default=4,
                    help="batched workload: products are planned in this many waves")
+    p.add_argument("--requests", type=int, default=2000,
+                   help="served workload: number of requests")
+    p.add_argument("--rho", type=float, default=0.8,
+                   help="served workload: offered load as a fraction of the one-call capacity")
     p.add_argument("--numeric-graph", type=int, default=0,
                    help="1 = capture the numeric phase in a CUDA graph")
     p.add_argument("--l2-fetch", type=int, default=0,
@@ -554,6 +562,70 @@ def run_batched(args, dist):
     }
 
 
+def run_served(args, dist):
+    """Served workload: the one-call-per-product capacity is measured on a
+    closed-loop sample, the arrival rate set to rho times it, and the same
+    open-loop arrival sequence replayed through the one-call server and the
+    continuous-batching server."""
+    import torch
+
+    from paper_2501_07056_gb300 import inputs, magnus, serve
+
+    dev = torch.device("cuda", dist.local_rank if dist.world > 1 else 0)
+    torch.cuda.set_device(dev)
+    magnus._lib()
+    descs = inputs.served_stream(args.requests, seed=0)
+    params = magnus.make_params(sort_threshold=args.sort_threshold,
+                                force_category=args.force_category)
+    work = serve.StencilTimesRandom(device=dev)
+
+    def reqs_at(rate, d=descs):
+        return serve.make_requests(d, seed=0, rate=rate, exact=False)
+
+    # capacity of the one-call path: a closed-loop sample (all arrive at 0)
+    nsamp = min(len(descs), 200)
+    serve.Server(work, params, mode="single", device=dev).run(reqs_at(1e12, descs[:16]))
+    srv = serve.Server(work, params, mode="single", device=dev)
+    srv.run(reqs_at(1e12, descs[:nsamp]))
+    cap = srv.executed_products / srv.makespan
+    srvb = serve.Server(work, params, mode="batched", n_streams=3, max_requests=64,
+                        max_products=1 << 30, device=dev)
+    srvb.run(reqs_at(1e12, descs[:nsamp]))
+    cap_batched = srvb.executed_products / srvb.makespan
+    mean_p = np.mean([r.products for r in reqs_at(1.0)])
+    rate = args.rho * cap / mean_p
+    out = {}
+    for mode in ("single", "batched"):
+        reqs = reqs_at(rate)
+        srv = serve.Server(work, params, mode=mode, n_streams=3, max_requests=64,
+                           max_products=1 << 30, device=dev)
+        clocks = ClockSampler(dev.index).start()
+        n0 = magnus.magnus_launch_count()
+        srv.run(reqs)
+        clk = clocks.stop()
+        prods = srv.executed_products
+        out[mode] = dict(serve.latency_stats(reqs), requests_per_s=len(reqs) / srv.makespan,
+                         gflops=2.0 * prods / srv.makespan / 1e9, makespan_s=srv.makespan,
+                         batches=srv.n_batches, gpu_launches=magnus.magnus_launch_count() - n0,
+                         clocks=clk)
+    b, o = out["batched"], out["single"]
+    return {
+        "metric": "served products/s", "value": b["requests_per_s"], "unit": "products/s",
+        "n_gpus": dist.world, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * b["makespan_s"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS["served"], "requests": len(descs), "rho": args.rho,
+                   "arrival_rate_per_s": rate, "one_call_capacity_products_per_s": cap,
+                   "batched_capacity_products_per_s": cap_batched,
+                   "capacity_sample": "first %d requests, all arriving at once" % nsamp,
+                   "mean_products_per_request": float(mean_p),
+                   "parallelism": "replicas" if dist.world > 1 else "single"},
+        "latency_ms": {"p50": b["p50_ms"], "p99": b["p99_ms"]},
+        "served_batched": b, "served_one_call": o,
+        "clocks": b["clocks"], "gpu_launches": b["gpu_launches"],
+    }
+
+
 def run_e2e(args, dist, A, dev, params, n_inter, nnz_c):
     """Same metric through the public API with host buffers: every step
     copies A from pinned host memory to the device, computes C and copies C
@@ -607,6 +679,8 @@ def main(argv=None):
             res = run_reference(args, dist)
         elif args.workload == "batched4096":
             res = run_batched(args, dist)
+        elif args.workload == "served":
+            res = run_served(args, dist)
         else:
             res = run_ours(args, dist)
         if dist.rank == 0 and res is not None:
