@@ -90,6 +90,9 @@ def parse_args(argv=None):
                    help="served workload: number of requests")
     p.add_argument("--rho", type=float, default=0.8,
                    help="served workload: offered load as a fraction of the one-call capacity")
+    p.add_argument("--autotune", type=int, default=0,
+                   help="1 = run magnus_autotune (row sample of about 2^27 products, at most "
+                        "16 runs) before the warm-up and time its choice")
     p.add_argument("--numeric-graph", type=int, default=0,
                    help="1 = capture the numeric phase in a CUDA graph")
     p.add_argument("--l2-fetch", type=int, default=0,
@@ -349,6 +352,14 @@ def run_ours(args, dist):
                                 chunk_len_fine_log2=args.chunk_fine,
                                 l2_fetch_bytes=args.l2_fetch)
     stream = torch.cuda.current_stream()
+    tuned = None
+    if args.autotune:
+        t0 = time.perf_counter()
+        params, rep = magnus.autotune(dA, dA, params, sample_products=1 << 27, max_trials=16,
+                                      stream=stream)
+        tuned = {"report": rep, "seconds": time.perf_counter() - t0,
+                 "params": magnus.params_dict(params)}
+        torch.cuda.empty_cache()
 
     def step(keep):
         plan = magnus.Plan(dA, dA, params, stream)
@@ -432,7 +443,8 @@ def run_ours(args, dist):
                      if peak_kind == "measured" else "fallback 6.8 TB/s"},
         "clocks": clk,
         "gpu_launches": n_launch,
-        "detail": {"nnz_c": nnz_c, "stage_ms": stage_ms, "t_over_t_ideal": (ms_max / args.steps) / t_ideal_ms,
+        "detail": {"nnz_c": nnz_c, "autotune": tuned,
+                   "stage_ms": stage_ms, "t_over_t_ideal": (ms_max / args.steps) / t_ideal_ms,
                    "t_ideal_ms": t_ideal_ms, "rows_per_category": info["rows_per_category"],
                    "sort_threshold": info["sort_threshold"]},
     }

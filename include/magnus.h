@@ -264,6 +264,37 @@ void magnus_free_batched(magnus_batch_t batch);
  * magnus_plan_info.  NULL for a NULL batch. */
 magnus_plan_t magnus_batch_inner_plan(magnus_batch_t batch);
 
+/* ---- autotuner -----------------------------------------------------------
+ * magnus_autotune measures the whole step (magnus_plan + magnus_symbolic +
+ * magnus_numeric, CUDA events on `stream`) for candidate parameter sets and
+ * returns the fastest in *best.  The search starts from *base (NULL = the
+ * automatic parameters) and does coordinate descent over sort_threshold
+ * (64..1025), wide_sort_max, chunk_len_coarse_log2 (11..13, when coarse rows
+ * exist), chunk_len_fine_log2 (7..10) and dense_chunk_threshold (when fine
+ * rows exist); at most max_trials measured runs.  The paper fixes the
+ * threshold and derives the chunk lengths from its cache model (Section 3.5,
+ * Section 4.1.1); on the GPU those values are the starting point.
+ * sample_products > 0 and a product with more intermediate products than
+ * that: the runs use 16 evenly spaced row blocks of A holding about
+ * sample_products products (a device copy of those rows).
+ * A and B need values.  Results are cached per (device, shapes, nnz,
+ * sample_products): a repeated call returns the cached set with
+ * report->from_cache = 1.  The device memory of the trials (one C of the
+ * tuned operand and the plans' scratch) is released before returning.
+ * Synchronises `stream`.  Status codes as for magnus_plan. */
+typedef struct {
+  int32_t trials;          /* measured runs (the base run counts as one) */
+  int32_t from_cache;      /* 1 if *best came from the cache (no runs) */
+  int64_t sampled_rows;    /* rows of A used, 0 = all */
+  int64_t products_full;   /* n_interProd of the full product */
+  float base_ms;           /* step time with *base */
+  float best_ms;           /* step time with *best */
+} magnus_tune_report_t;
+
+int magnus_autotune(const magnus_csr_t* A, const magnus_csr_t* B, const magnus_params_t* base,
+                    int64_t sample_products, int32_t max_trials, magnus_params_t* best,
+                    magnus_tune_report_t* report, void* stream);
+
 /* ---- plan introspection ------------------------------------------------ */
 typedef struct {
   int64_t n_rows;               /* rows of A (= rows of C) */

@@ -60,6 +60,11 @@ class PlanInfo(ctypes.Structure):
         return d
 
 
+class TuneReport(ctypes.Structure):
+    _fields_ = [("trials", c_i32), ("from_cache", c_i32), ("sampled_rows", c_i64),
+                ("products_full", c_i64), ("base_ms", ctypes.c_float), ("best_ms", ctypes.c_float)]
+
+
 class ChunkModel(ctypes.Structure):
     _fields_ = [("m_c_log2", c_i32), ("chunk_len_fine_log2", c_i32),
                 ("chunk_len_fine_sym_log2", c_i32), ("n_chunks_fine_max_log2", c_i32),
@@ -101,6 +106,9 @@ SIGNATURES = {
     "magnus_batch_info": (c_i32, [c_p, ctypes.POINTER(PlanInfo)]),
     "magnus_free_batched": (None, [c_p]),
     "magnus_batch_inner_plan": (c_p, [c_p]),
+    "magnus_autotune": (c_i32, [ctypes.POINTER(CsrDesc), ctypes.POINTER(CsrDesc),
+                                ctypes.POINTER(Params), c_i64, c_i32, ctypes.POINTER(Params),
+                                ctypes.POINTER(TuneReport), c_p]),
     "magnus_chunk_model": (c_i32, [c_i64, c_i64, c_i64, c_i32, ctypes.POINTER(ChunkModel)]),
 }
 
@@ -297,6 +305,25 @@ class Plan:
             self.free()
         except Exception:
             pass
+
+
+def autotune(A: "DeviceCSR", B: "DeviceCSR", base: Params | None = None, sample_products=0,
+             max_trials=16, stream=None):
+    """magnus_autotune: returns (best Params, report dict)."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    best = Params()
+    rep = TuneReport()
+    da, db = A.desc(True), B.desc(True)
+    _check(_lib().magnus_autotune(ctypes.byref(da), ctypes.byref(db),
+                                  ctypes.byref(base) if base is not None else None,
+                                  sample_products, max_trials, ctypes.byref(best),
+                                  ctypes.byref(rep), c_p(s.cuda_stream)), "magnus_autotune")
+    return best, {name: getattr(rep, name) for name, _ in rep._fields_}
+
+
+def params_dict(p: Params) -> dict:
+    return {name: getattr(p, name) for name, _ in p._fields_}
 
 
 class BatchPlan:

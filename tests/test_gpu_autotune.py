@@ -1,0 +1,44 @@
+"""Autotuner: the chosen parameters compute the oracle's C, the search never
+returns something slower than its starting point, repeated calls hit the
+cache, and row sampling runs on a copy of evenly spaced row blocks."""
+import numpy as np
+import pytest
+
+from paper_2501_07056_gb300 import inputs
+from tests._gpu import assert_parity, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def test_autotune_mixed_rows():
+    from paper_2501_07056_gb300 import magnus
+    A = inputs.rmat(12, 16, seed=2, matrix_id=1)
+    dA = magnus.DeviceCSR.from_host(A)
+    best, rep = magnus.autotune(dA, dA, max_trials=12)
+    assert 1 < rep["trials"] <= 12 and rep["from_cache"] == 0
+    assert rep["best_ms"] <= rep["base_ms"]
+    got = run_gpu(A, A, best, same=True)
+    assert_parity(got, A, A)
+    best2, rep2 = magnus.autotune(dA, dA, max_trials=12)
+    assert rep2["from_cache"] == 1 and rep2["trials"] == 0
+    assert magnus.params_dict(best2) == magnus.params_dict(best)
+
+
+def test_autotune_sampled_rows():
+    from paper_2501_07056_gb300 import magnus
+    A = inputs.ragged(20000, 20000, 2, 40, seed=3, matrix_id=1)
+    B = inputs.ragged(20000, 300000, 2, 40, seed=3, matrix_id=2)
+    dA, dB = magnus.DeviceCSR.from_host(A), magnus.DeviceCSR.from_host(B)
+    lens = np.diff(B.row_ptr)
+    full = int(lens[A.col].sum())
+    best, rep = magnus.autotune(dA, dB, sample_products=full // 10, max_trials=6)
+    assert rep["products_full"] == full
+    assert 0 < rep["sampled_rows"] < A.n_rows
+    got = run_gpu(A, B, best)
+    assert_parity(got, A, B)
