@@ -62,8 +62,8 @@ WORKLOADS = {
                    "A_i and B_i n_i x n_i with nnz/row uniform in {2..32} (counter-based "
                    "generator, drawn on the device), FP64 U(-1,1), seed 0",
 }
-CPU_SAMPLE_ROWS = 1 << 21
-REF_STEP_ROWS = 1 << 18
+CPU_SAMPLE_PRODUCTS = 1 << 29   # cpu_baseline: about 2-15 s of oracle time
+REF_STEP_PRODUCTS = 1 << 27     # reference arm: one step
 PROFILE_DIR = os.path.join(ROOT, "profiles")
 
 
@@ -291,11 +291,35 @@ def workload_config(args, A, dist):
 
 # ---------------------------------------------------------------------------
 
+def row_products(A):
+    lens = np.diff(A.row_ptr)
+    per_nz = lens[A.col].astype(np.int64)
+    cs = np.concatenate(([0], np.cumsum(per_nz)))
+    return cs[A.row_ptr[1:]] - cs[A.row_ptr[:-1]]
+
+
+def sample_rows(A, max_products, n_blocks=64):
+    """Rows of n_blocks evenly spaced equal row blocks holding at most
+    max_products intermediate products (all rows if they fit)."""
+    P = row_products(A)
+    if P.sum() <= max_products:
+        return np.arange(A.n_rows, dtype=np.int64), int(P.sum())
+    cs = np.concatenate(([0], np.cumsum(P)))
+    starts = (np.arange(n_blocks) * (A.n_rows // n_blocks)).astype(np.int64)
+    lo, hi = 1, max(1, A.n_rows // n_blocks)
+    while lo < hi:  # largest block length within the budget
+        mid = (lo + hi + 1) // 2
+        if int((cs[starts + mid] - cs[starts]).sum()) <= max_products:
+            lo = mid
+        else:
+            hi = mid - 1
+    rows = (starts[:, None] + np.arange(lo)[None, :]).reshape(-1)
+    return rows, int(P[rows].sum())
+
+
 def cpu_oracle_rate(A, rows, threads):
     import oracle
-    rp = A.row_ptr
-    lens = np.diff(rp)
-    prods = int(lens[A.col[rp[rows[0]]:rp[rows[-1] + 1]]].sum())
+    prods = int(row_products(A)[rows].sum())
     t0 = time.perf_counter()
     oracle.spgemm(A, A, rows=rows, threads=threads)
     dt = time.perf_counter() - t0
@@ -310,8 +334,7 @@ def run_reference(args, dist):
         return None
     A, _ = inputs.workload(args.workload)
     threads = os.cpu_count() or 1
-    n = min(A.n_rows, REF_STEP_ROWS)
-    rows = np.arange(n, dtype=np.int64)
+    rows, _ = sample_rows(A, REF_STEP_PRODUCTS)
     for _ in range(args.warmup):
         cpu_oracle_rate(A, rows, threads)
     rates, total_prods, total_t = [], 0, 0.0
@@ -321,7 +344,8 @@ def run_reference(args, dist):
         total_prods += prods
         total_t += dt
     value = 2.0 * total_prods / total_t / 1e9
-    sample = "rows 0..%d of the workload (%d products per step), C rows via Eq. 1" % (n - 1, total_prods // args.steps)
+    sample = ("%d rows of the workload in 64 evenly spaced row blocks (%d products per step), "
+              "C rows via Eq. 1" % (rows.size, total_prods // args.steps))
     return {
         "impl": "reference", "metric": "SpGEMM GFLOP/s", "value": value, "unit": "GFLOP/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -452,11 +476,12 @@ def run_ours(args, dist):
         result["e2e"] = run_e2e(args, dist, A, dev, params, n_inter, nnz_c)
     if not args.no_cpu and dist.rank == 0:
         threads = os.cpu_count() or 1
-        n = min(A.n_rows, CPU_SAMPLE_ROWS)
-        rate, prods, dt = cpu_oracle_rate(A, np.arange(n, dtype=np.int64), threads)
+        rows, _ = sample_rows(A, CPU_SAMPLE_PRODUCTS)
+        rate, prods, dt = cpu_oracle_rate(A, rows, threads)
         result["cpu_baseline"] = {
             "value": rate, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
-            "sample": "rows 0..%d of the workload (%d products, %.1f s wall)" % (n - 1, prods, dt)}
+            "sample": "%d rows of the workload in 64 evenly spaced row blocks (%d products, "
+                      "%.1f s wall)" % (rows.size, prods, dt)}
     return result
 
 
