@@ -97,6 +97,8 @@ struct SortArgs {
   int key32;            // 1: (col << slot_bits | slot) fits 32 bits
   uint8_t* perm;        // sorted slot order, 32*E bytes per listed row
                         // (written by the symbolic pass, replayed by the numeric pass)
+  uint16_t* perm2;      // block bins: sorted slot order, P_i entries per row at
+  const int64_t* perm2_off;  // perm2 + perm2_off[k] for the bin's k-th row
   // symbolic
   int64_t* out_cnt;     // indexed by row
   // numeric

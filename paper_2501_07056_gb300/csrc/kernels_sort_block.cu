@@ -2,16 +2,20 @@
 // sort accumulator of Algorithm 2 widened to a thread block).
 //
 // A row of bin SORT512 / SORT1024 is handled by one block of CAP/8 threads
-// (64 or 128), eight products per thread.  The products are generated from
-// A and B, their values (numeric pass) parked in shared memory by slot, and
-// the (column, slot) keys sorted by a bitonic network: partners within a
-// thread are swapped in registers, partners within a warp exchanged by
-// shuffles, partners in other warps through shared memory.  Equal columns
-// are then adjacent with their slots ascending, so summing a run of equal
-// columns in sorted order sums the products in the traversal order of
-// Algorithm 1.  The symbolic pass counts the runs; the numeric pass sorts
-// again (no order is recorded for these bins) and writes one entry per run,
-// consecutive threads writing consecutive entries of the row of C.
+// (64 or 128), eight products per thread.
+//
+// Symbolic: the products' (column, slot) keys are generated from A and B and
+// sorted by a bitonic network (partners within a thread are swapped in
+// registers, partners within a warp exchanged by shuffles, partners in other
+// warps through shared memory); the runs of equal columns are counted
+// (precise prediction, Section 2.1) and the sorted slot order is stored, two
+// bytes per product.
+//
+// Numeric: the products are generated again with their values, parked in
+// shared memory by slot, and visited in the recorded order: equal columns
+// are adjacent with their slots ascending, so a run is summed in the
+// traversal order of Algorithm 1.  Consecutive threads take consecutive
+// sorted positions and write consecutive entries of the row of C.
 //
 // Blocks are persistent: each takes rows idx = blockIdx.x, + gridDim.x, ...
 #include "sort_accum.cuh"
@@ -82,11 +86,13 @@ __global__ void __launch_bounds__((1 << CAPLOG) / BR) k_sort_rows_block(SortArgs
   constexpr int SB = CAPLOG;  // slot bits of a key
   constexpr int HW = CAP / 32;
   using KT = KeyTraits<K>;
-  __shared__ K s_key[CAP];
+  __shared__ K s_key[NUMERIC ? 1 : CAP];
   __shared__ int32_t s_start[CAP + 1];  // first slot of each non-empty segment
   __shared__ int64_t s_bs[CAP];         // B.rowPtr of the segment's B row
   __shared__ double s_av[NUMERIC ? CAP : 1];
-  __shared__ double s_val[NUMERIC ? CAP : 1];  // product value by slot
+  __shared__ double s_val[NUMERIC ? CAP : 1];    // product value by slot
+  __shared__ int32_t s_col[NUMERIC ? CAP : 1];   // product column by slot
+  __shared__ uint16_t s_perm[NUMERIC ? CAP : 1]; // slot at each sorted position
   __shared__ uint32_t s_head[HW];
   __shared__ int32_t s_pw[HW];
   __shared__ int32_t s_ws[NWB + 1];
@@ -95,6 +101,7 @@ __global__ void __launch_bounds__((1 << CAPLOG) / BR) k_sort_rows_block(SortArgs
 
   for (int64_t idx = blockIdx.x; idx < a.n_rows; idx += gridDim.x) {
     const RowDesc d = a.desc[idx];
+    const int64_t poff = a.perm2_off[idx];
     // 1. segments: the non-empty B rows referenced by the row, in stored
     //    order, with their first slots (block scan of the lengths)
     int nseg = 0, P = 0;
@@ -134,8 +141,6 @@ __global__ void __launch_bounds__((1 << CAPLOG) / BR) k_sort_rows_block(SortArgs
       P += totL;
       __syncthreads();
     }
-    if (t == 0) s_start[nseg] = P;
-    __syncthreads();
     // 2. expand: slot s = e * NT + t (consecutive threads read consecutive
     //    entries of a B row); all gathers are issued before any is used
     int64_t kk[BR];
@@ -153,46 +158,73 @@ __global__ void __launch_bounds__((1 << CAPLOG) / BR) k_sort_rows_block(SortArgs
     }
     int32_t cg[BR];
     double vg[BR];
+    uint16_t pg[BR];
 #pragma unroll
     for (int e = 0; e < BR; ++e) {
       cg[e] = kk[e] >= 0 ? __ldg(a.B.col + kk[e]) : 0;
-      if (NUMERIC) vg[e] = kk[e] >= 0 ? __ldg(a.B.val + kk[e]) : 0.0;
+      if (NUMERIC) {
+        vg[e] = kk[e] >= 0 ? __ldg(a.B.val + kk[e]) : 0.0;
+        const int q = e * NT + t;
+        pg[e] = q < P ? a.perm2[poff + q] : (uint16_t)0;
+      }
     }
-    K key[BR];
-#pragma unroll
-    for (int e = 0; e < BR; ++e) {
-      const int s = e * NT + t;
-      key[e] = (s < P) ? KT::template make<SB>(cg[e], s) : ~K(0);
-      if (NUMERIC && s < P) s_val[s] = s_av[gg[e]] * vg[e];
-    }
-    // 3. sort
-    block_sort_keys<NT>(key, s_key);
-#pragma unroll
-    for (int e = 0; e < BR; ++e) s_key[t * BR + e] = key[e];
-    __syncthreads();
-    // 4. run heads: position q starts a run if its column differs from q-1
-    uint32_t hb = 0;
-#pragma unroll
-    for (int e = 0; e < BR; ++e) {
-      const int q = t * BR + e;
-      const int32_t c = KT::template col<SB>(key[e]);
-      const int32_t pc = q == 0 ? -1 : KT::template col<SB>(s_key[q - 1]);
-      if (q < P && (q == 0 || c != pc)) hb |= 1u << e;
-    }
-    // threads 4m..4m+3 hold the 32 positions of head word m
-    uint32_t word = hb << (8 * (t & 3));
-    word |= __shfl_xor_sync(FULL, word, 1);
-    word |= __shfl_xor_sync(FULL, word, 2);
-    if ((t & 3) == 0) s_head[t >> 2] = word;
-    __syncthreads();
     if (!NUMERIC) {
-      if (w == 0) {
-        int c = 0;
-        for (int i = lane; i < HW; i += 32) c += __popc(s_head[i]);
-        c = warp_sum(c);
-        if (lane == 0) a.out_cnt[d.row] = c;
+      K key[BR];
+#pragma unroll
+      for (int e = 0; e < BR; ++e) {
+        const int s = e * NT + t;
+        key[e] = (s < P) ? KT::template make<SB>(cg[e], s) : ~K(0);
+      }
+      // 3s. sort, store the order, count the runs of equal columns
+      block_sort_keys<NT>(key, s_key);
+#pragma unroll
+      for (int e = 0; e < BR; ++e) {
+        const int q = t * BR + e;
+        s_key[q] = key[e];
+        if (q < P) a.perm2[poff + q] = (uint16_t)KT::template slot<SB>(key[e]);
+      }
+      __syncthreads();
+      uint32_t hb = 0;
+#pragma unroll
+      for (int e = 0; e < BR; ++e) {
+        const int q = t * BR + e;
+        const int32_t c = KT::template col<SB>(key[e]);
+        const int32_t pc = q == 0 ? -1 : KT::template col<SB>(s_key[q - 1]);
+        if (q < P && (q == 0 || c != pc)) hb |= 1u << e;
+      }
+      int c = __popc(hb);
+      c = warp_sum(c);
+      if (lane == 0) s_ws[w] = c;
+      __syncthreads();
+      if (t == 0) {
+        int tot = 0;
+        for (int i = 0; i < NWB; ++i) tot += s_ws[i];
+        a.out_cnt[d.row] = tot;
       }
     } else {
+      // 3n. replay the recorded order
+#pragma unroll
+      for (int e = 0; e < BR; ++e) {
+        const int s = e * NT + t;
+        if (s < P) {
+          s_col[s] = cg[e];
+          s_val[s] = s_av[gg[e]] * vg[e];
+          s_perm[s] = pg[e];  // position s of the sorted order holds slot pg[e]
+        }
+      }
+      __syncthreads();
+      // run heads in position-major order: word m of the head bitmap covers
+      // positions 32m..32m+31, one warp's lanes for one e
+      int32_t cq[BR];
+#pragma unroll
+      for (int e = 0; e < BR; ++e) {
+        const int q = e * NT + t;
+        cq[e] = q < P ? s_col[pg[e]] : 0;
+        const int32_t pc = (q == 0 || q >= P) ? -1 : s_col[s_perm[q - 1]];
+        const unsigned hb = __ballot_sync(FULL, q < P && cq[e] != pc);
+        if (lane == 0) s_head[(e * NT + w * 32) >> 5] = hb;
+      }
+      __syncthreads();
       if (w == 0) {
         const int c = lane < HW ? __popc(s_head[lane]) : 0;
         const int inc = warp_inclusive_scan(c);
@@ -200,23 +232,22 @@ __global__ void __launch_bounds__((1 << CAPLOG) / BR) k_sort_rows_block(SortArgs
       }
       __syncthreads();
       const int64_t crp = a.c_rp[d.row];
-#pragma unroll 1
+#pragma unroll
       for (int e = 0; e < BR; ++e) {
         const int q = e * NT + t;
-        if (q >= P) break;
-        const uint32_t hw = s_head[q >> 5];
-        if (!((hw >> (q & 31)) & 1u)) continue;
-        const int o = s_pw[q >> 5] + __popc(hw & ((1u << (q & 31)) - 1u));
-        const K kq = s_key[q];
-        const int32_t c = KT::template col<SB>(kq);
-        double acc = s_val[KT::template slot<SB>(kq)];
-        for (int q2 = q + 1; q2 < P; ++q2) {
-          const K k2 = s_key[q2];
-          if (KT::template col<SB>(k2) != c) break;
-          acc += s_val[KT::template slot<SB>(k2)];
+        const uint32_t hw = q < P ? s_head[q >> 5] : 0u;
+        if ((hw >> (q & 31)) & 1u) {
+          const int o = s_pw[q >> 5] + __popc(hw & ((1u << (q & 31)) - 1u));
+          const int32_t c = cq[e];
+          double acc = s_val[pg[e]];
+          for (int q2 = q + 1; q2 < P; ++q2) {
+            const int s2 = s_perm[q2];
+            if (s_col[s2] != c) break;
+            acc += s_val[s2];
+          }
+          a.c_col[crp + o] = c;
+          a.c_val[crp + o] = acc;
         }
-        a.c_col[crp + o] = c;
-        a.c_val[crp + o] = acc;
       }
     }
     __syncthreads();
@@ -245,14 +276,13 @@ cudaError_t launch_sort_rows_block(int bin, bool numeric, const SortArgs& a, int
                                    cudaStream_t s) {
   if (a.n_rows == 0) return cudaSuccess;
   const bool big = bin == BIN_SORT1024;
+  if (numeric)  // the replay holds no keys
+    return big ? launch_block<10, uint32_t, true>(a, num_sms, s)
+               : launch_block<9, uint32_t, true>(a, num_sms, s);
   if (a.key32) {
-    if (numeric) return big ? launch_block<10, uint32_t, true>(a, num_sms, s)
-                            : launch_block<9, uint32_t, true>(a, num_sms, s);
     return big ? launch_block<10, uint32_t, false>(a, num_sms, s)
                : launch_block<9, uint32_t, false>(a, num_sms, s);
   }
-  if (numeric) return big ? launch_block<10, uint64_t, true>(a, num_sms, s)
-                          : launch_block<9, uint64_t, true>(a, num_sms, s);
   return big ? launch_block<10, uint64_t, false>(a, num_sms, s)
              : launch_block<9, uint64_t, false>(a, num_sms, s);
 }

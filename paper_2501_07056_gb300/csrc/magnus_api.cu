@@ -165,6 +165,8 @@ struct magnus_plan_s {
   // sorted slot order of the sort rows (symbolic -> numeric)
   uint8_t* perm = nullptr;
   int64_t perm_off[NUM_BINS + 1] = {0};
+  uint16_t* perm2 = nullptr;         // block sort bins: sorted slot order
+  int64_t* perm2_off = nullptr;      // per block-bin row (both bins), + total
   // state and statistics
   bool symbolic_done = false;
   int64_t nnz_c = -1;
@@ -497,6 +499,20 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
         o += (pl->bin_off[b + 1] - pl->bin_off[b]) * ((int64_t)32 << (b - BIN_SORT32));
     }
     MAG_TRY(plan_alloc(pl, &pl->perm, (size_t)o + 16, s));
+    // block sort bins: P_i two-byte slots per row, at the prefix sum of P
+    const int64_t nblk = pl->bin_off[BIN_SORT1024 + 1] - pl->bin_off[BIN_SORT512];
+    int64_t tot = 0;
+    if (nblk > 0) {
+      MAG_TRY(plan_alloc(pl, &pl->perm2_off, (size_t)nblk + 1, s));
+      CUDA_TRY(launch_gather_i64(pl->P, pl->rows_sorted + pl->bin_off[BIN_SORT512], nblk,
+                                 pl->perm2_off, s));
+      int64_t* stmp;
+      MAG_TRY(tmp.get(&stmp, (size_t)scan_tmp_elems(nblk) + 2));
+      CUDA_TRY(launch_exclusive_scan_i64(pl->perm2_off, nblk, stmp, s));
+      CUDA_TRY(cudaMemcpyAsync(&tot, pl->perm2_off + nblk, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    MAG_TRY(plan_alloc(pl, &pl->perm2, (size_t)tot + 8, s));
   }
   // per-category statistics and the dense row count
   std::vector<int32_t> drows;
@@ -606,6 +622,8 @@ static int run_phase(magnus_plan_t pl, bool numeric, int64_t* out_cnt, const int
       a.n_rows = pl->bin_off[b + 1] - pl->bin_off[b];
       a.key32 = pl->key32[b];
       a.perm = pl->perm + pl->perm_off[b];
+      a.perm2 = pl->perm2;
+      a.perm2_off = (pl->perm2_off && b >= BIN_SORT512) ? pl->perm2_off + (pl->bin_off[b] - pl->bin_off[BIN_SORT512]) : nullptr;
       a.out_cnt = out_cnt;
       a.c_rp = c_rp;
       a.c_col = c_col;
@@ -873,6 +891,8 @@ int magnus_numeric_noalloc(magnus_plan_t pl, const double* a_val, const double* 
     a.n_rows = pl->bin_off[b + 1] - pl->bin_off[b];
     a.key32 = pl->key32[b];
     a.perm = pl->perm + pl->perm_off[b];
+    a.perm2 = pl->perm2;
+    a.perm2_off = (pl->perm2_off && b >= BIN_SORT512) ? pl->perm2_off + (pl->bin_off[b] - pl->bin_off[BIN_SORT512]) : nullptr;
     a.c_rp = c_row_ptr;
     a.c_col = c_col;
     a.c_val = c_val;
