@@ -58,6 +58,14 @@ WORKLOADS = {
               "27-point stencil on a k^3 grid (k uniform in {16..96}) and B n x n (n=k^3) with "
               "nnz/row uniform in {4..16} (counter-based generator, drawn on the device), FP64, "
               "seed 0",
+    "massive20": "C=A*B, A 4096 x 2^21 and B 2^21 x 2^20, 512 stratified-uniform cols/row in "
+                 "both (counter-based generator, drawn on the device), FP64 U(-1,1), seed 0",
+    "massive24": "C=A*B, A 4096 x 2^21 and B 2^21 x 2^24, 512 stratified-uniform cols/row in "
+                 "both (counter-based generator, drawn on the device), FP64 U(-1,1), seed 0",
+    "massive28": "C=A*B, A 4096 x 2^21 and B 2^21 x 2^28, 512 stratified-uniform cols/row in "
+                 "both (counter-based generator, drawn on the device), FP64 U(-1,1), seed 0",
+    "massive30": "C=A*B, A 4096 x 2^21 and B 2^21 x 2^30, 512 stratified-uniform cols/row in "
+                 "both (counter-based generator, drawn on the device), FP64 U(-1,1), seed 0",
     "batched4096": "4096 independent products C_i=A_i*B_i, n_i log-uniform in [256, 65536], "
                    "A_i and B_i n_i x n_i with nnz/row uniform in {2..32} (counter-based "
                    "generator, drawn on the device), FP64 U(-1,1), seed 0",
@@ -280,19 +288,46 @@ def ideal_bytes(n_rows, nnz_a, n_inter, nnz_c):
     return read + write
 
 
-def workload_config(args, A, dist):
-    lens = np.diff(A.row_ptr)
-    return {"workload": WORKLOADS[args.workload], "n": A.n_rows, "nnz_a": A.nnz,
-            "n_interprod": int(lens[A.col].sum()),
+def workload_config(args, n_rows, nnz_a, n_inter, dist):
+    return {"workload": WORKLOADS[args.workload], "n": n_rows, "nnz_a": nnz_a,
+            "n_interprod": int(n_inter),
             "parallelism": "replicas" if dist.world > 1 else "single",
             "l2": "inputs larger than L2 (A and B exceed the 126 MB L2), no flush",
             "step": "plan+symbolic+alloc C+numeric"}
 
 
+# The paper's massive nonsquare uniform workload (Section 4.3): C has 4096
+# rows and m_C columns; A is 4096 x K, B is K x m_C, 512 nonzeros per row in
+# both (the paper uses 2048 with float values; 512 with FP64 keeps B and C
+# within one GPU).
+MASSIVE_ROWS, MASSIVE_K, MASSIVE_NNZ = 4096, 1 << 21, 512
+
+
+def massive_operands(name, dev):
+    from paper_2501_07056_gb300 import gen_device
+    m_c = 1 << int(name[len("massive"):])
+    dA = gen_device.stratified(MASSIVE_ROWS, MASSIVE_K, MASSIVE_NNZ, 0, 1, device=dev)
+    dB = gen_device.stratified(MASSIVE_K, m_c, MASSIVE_NNZ, 0, 2, device=dev)
+    return dA, dB
+
+
+def massive_host(name, max_products):
+    """Host A and the rows of B referenced by a sample of A's rows."""
+    from paper_2501_07056_gb300 import inputs
+    m_c = 1 << int(name[len("massive"):])
+    A = inputs.stratified(MASSIVE_ROWS, MASSIVE_K, MASSIVE_NNZ, 0, 1)
+    n = max(1, min(MASSIVE_ROWS, max_products // (MASSIVE_NNZ * MASSIVE_NNZ)))
+    rows = (np.arange(n, dtype=np.int64) * (MASSIVE_ROWS // n)).astype(np.int64)
+    need = np.unique(np.concatenate([A.col[A.row_ptr[r]:A.row_ptr[r + 1]] for r in rows]))
+    B = inputs.stratified(MASSIVE_K, m_c, MASSIVE_NNZ, 0, 2, rows=need)
+    return A, B, rows
+
+
 # ---------------------------------------------------------------------------
 
-def row_products(A):
-    lens = np.diff(A.row_ptr)
+def row_products(A, B=None):
+    B = A if B is None else B
+    lens = np.diff(B.row_ptr)
     per_nz = lens[A.col].astype(np.int64)
     cs = np.concatenate(([0], np.cumsum(per_nz)))
     return cs[A.row_ptr[1:]] - cs[A.row_ptr[:-1]]
@@ -317,11 +352,12 @@ def sample_rows(A, max_products, n_blocks=64):
     return rows, int(P[rows].sum())
 
 
-def cpu_oracle_rate(A, rows, threads):
+def cpu_oracle_rate(A, rows, threads, B=None):
     import oracle
-    prods = int(row_products(A)[rows].sum())
+    B = A if B is None else B
+    prods = int(row_products(A, B)[rows].sum())
     t0 = time.perf_counter()
-    oracle.spgemm(A, A, rows=rows, threads=threads)
+    oracle.spgemm(A, B, rows=rows, threads=threads)
     dt = time.perf_counter() - t0
     return 2.0 * prods / dt / 1e9, prods, dt
 
@@ -332,14 +368,17 @@ def run_reference(args, dist):
     from paper_2501_07056_gb300 import inputs
     if dist.rank != 0:
         return None
-    A, _ = inputs.workload(args.workload)
     threads = os.cpu_count() or 1
-    rows, _ = sample_rows(A, REF_STEP_PRODUCTS)
+    if args.workload.startswith("massive"):
+        A, B, rows = massive_host(args.workload, REF_STEP_PRODUCTS)
+    else:
+        A, B = inputs.workload(args.workload)
+        rows, _ = sample_rows(A, REF_STEP_PRODUCTS)
     for _ in range(args.warmup):
-        cpu_oracle_rate(A, rows, threads)
+        cpu_oracle_rate(A, rows, threads, B)
     rates, total_prods, total_t = [], 0, 0.0
     for _ in range(args.steps):
-        r, prods, dt = cpu_oracle_rate(A, rows, threads)
+        r, prods, dt = cpu_oracle_rate(A, rows, threads, B)
         rates.append(r)
         total_prods += prods
         total_t += dt
@@ -351,7 +390,8 @@ def run_reference(args, dist):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args, A, dist),
+        "config": workload_config(args, A.n_rows, A.nnz, int(row_products(A, B).sum())
+                                  if not args.workload.startswith("massive") else -1, dist),
         "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
@@ -367,8 +407,14 @@ def run_ours(args, dist):
     dev = torch.device("cuda", dist.local_rank if dist.world > 1 else 0)
     torch.cuda.set_device(dev)
     magnus._lib()  # fail loudly if the library is missing
-    A, _ = inputs.workload(args.workload)
-    dA = magnus.DeviceCSR.from_host(A, dev)
+    massive = args.workload.startswith("massive")
+    if massive:
+        A = None
+        dA, dB = massive_operands(args.workload, dev)
+    else:
+        A, _ = inputs.workload(args.workload)
+        dA = magnus.DeviceCSR.from_host(A, dev)
+        dB = dA
     torch.cuda.synchronize()
     params = magnus.make_params(force_category=args.force_category,
                                 sort_threshold=args.sort_threshold,
@@ -379,14 +425,14 @@ def run_ours(args, dist):
     tuned = None
     if args.autotune:
         t0 = time.perf_counter()
-        params, rep = magnus.autotune(dA, dA, params, sample_products=1 << 27, max_trials=16,
+        params, rep = magnus.autotune(dA, dB, params, sample_products=1 << 27, max_trials=16,
                                       stream=stream)
         tuned = {"report": rep, "seconds": time.perf_counter() - t0,
                  "params": magnus.params_dict(params)}
         torch.cuda.empty_cache()
 
     def step(keep):
-        plan = magnus.Plan(dA, dA, params, stream)
+        plan = magnus.Plan(dA, dB, params, stream)
         plan.enable_timing(True)
         plan.symbolic()
         c_col, c_val = plan.numeric()
@@ -448,18 +494,18 @@ def run_ours(args, dist):
         traffic = profiled_traffic("bucket_dense_numeric", args.workload, COARSE_KERNEL_SOURCES)
     else:
         kern_ms = stage_ms["num_sort"]
-        alg = numeric_sort_alg_bytes(A.n_rows, A.nnz, n_inter, nnz_c)
+        alg = numeric_sort_alg_bytes(dA.n_rows, dA.nnz, n_inter, nnz_c)
         kernel = "k_sort_rows numeric"
         traffic = profiled_traffic("sort_rows_numeric", args.workload)
     achieved = alg / (kern_ms * 1e-3) / 1e9 if kern_ms > 0 else 0.0
-    t_ideal_ms = ideal_bytes(A.n_rows, A.nnz, n_inter, nnz_c) / (peak * 1e9) * 1e3
+    t_ideal_ms = ideal_bytes(dA.n_rows, dA.nnz, n_inter, nnz_c) / (peak * 1e9) * 1e3
 
     result = {
         "metric": "SpGEMM GFLOP/s", "value": value, "unit": "GFLOP/s", "n_gpus": dist.world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": workload_config(args, A, dist),
+        "config": workload_config(args, dA.n_rows, dA.nnz, n_inter, dist),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
                      "alg_bytes_per_launch": alg, "kernel_ms": kern_ms,
@@ -472,12 +518,16 @@ def run_ours(args, dist):
                    "t_ideal_ms": t_ideal_ms, "rows_per_category": info["rows_per_category"],
                    "sort_threshold": info["sort_threshold"]},
     }
-    if not args.no_e2e:
+    if not args.no_e2e and not massive:
         result["e2e"] = run_e2e(args, dist, A, dev, params, n_inter, nnz_c)
     if not args.no_cpu and dist.rank == 0:
         threads = os.cpu_count() or 1
-        rows, _ = sample_rows(A, CPU_SAMPLE_PRODUCTS)
-        rate, prods, dt = cpu_oracle_rate(A, rows, threads)
+        if massive:
+            A, Bh, rows = massive_host(args.workload, 1 << 26)
+        else:
+            Bh = A
+            rows, _ = sample_rows(A, CPU_SAMPLE_PRODUCTS)
+        rate, prods, dt = cpu_oracle_rate(A, rows, threads, Bh)
         result["cpu_baseline"] = {
             "value": rate, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
             "sample": "%d rows of the workload in 64 evenly spaced row blocks (%d products, "

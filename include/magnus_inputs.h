@@ -28,6 +28,14 @@
  * rounded as one product and one sum (no fused multiply-add).
  * Requires 1 <= kmin <= kmax <= 64.
  *
+ * Stratified matrix (the massive nonsquare uniform workload, rows of hundreds
+ * or thousands of entries): every row has exactly k entries; entry j lies in
+ * the stratum [floor(j*n_cols/k), floor((j+1)*n_cols/k)) at offset
+ * floor(hi32(ctr(key(s,id,4), r*k + j)) * width / 2^32), so the columns are
+ * distinct, ascending and spread uniformly; its value is
+ * lo + (hi - lo) * (ctr(key(s,id,5), r*k + j) >> 11) * 2^-53 (one product,
+ * one sum).  Requires 1 <= k <= n_cols.
+ *
  * 27-point stencil on a k x k x k grid, lexicographic numbering, truncated at
  * the boundary: 26 on the diagonal and -1 at every in-range neighbour;
  * nnz = (3k - 2)^3.
@@ -58,6 +66,12 @@ int magnus_gen_ragged_rowptr(int64_t n_rows, int64_t n_cols, int32_t kmin, int32
 int magnus_gen_ragged_fill(int64_t n_rows, int64_t n_cols, int32_t kmin, int32_t kmax,
                            uint64_t seed, uint64_t matrix_id, double lo, double hi,
                            const int64_t* row_ptr, int32_t* col, double* val, void* stream);
+
+/* The stratified matrix: row_ptr (n_rows + 1, = r * k), col and val
+ * (n_rows * k entries each). */
+int magnus_gen_stratified(int64_t n_rows, int64_t n_cols, int32_t k, uint64_t seed,
+                          uint64_t matrix_id, double lo, double hi, int64_t* row_ptr,
+                          int32_t* col, double* val, void* stream);
 
 /* The 27-point stencil on a k^3 grid: row_ptr (k^3 + 1), col and val
  * ((3k-2)^3 each).  1 <= k <= 1290. */

@@ -555,6 +555,35 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
     CUDA_TRY(cudaMemcpyAsync(pl->fine_rows_d, pl->fine_rows.data(), nf * 4, cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(pl->fine_P_d, pl->fine_P.data(), nf * 8, cudaMemcpyHostToDevice, s));
   }
+  // Sparse wide coarse rows.  d = products per column of the row that a
+  // typical product belongs to (rows weighted by their products, so a few
+  // heavy rows of a power-law matrix dominate).  Dense rows (R-MAT: a 2^13
+  // chunk receives >= 1024 products) keep the chunks of the block dense
+  // accumulator.  Sparser rows widen the chunks: to about 2048 products per
+  // (row, chunk) bucket when the fine level inside still sees >= 8 products
+  // per 2^10-column chunk, else to about 128 (a warp sort per bucket), so the
+  // per-bucket bookkeeping does not outgrow the products.
+  if (!pl->coarse_rows.empty() && P.chunk_len_coarse_log2 <= 0) {
+    double sp = 0.0, sp2 = 0.0;
+    for (int64_t p : pl->coarse_P) {
+      sp += (double)p;
+      sp2 += (double)p * (double)p;
+    }
+    const double m_cd = (double)(B->n_cols > 0 ? B->n_cols : 1);
+    const double d = sp > 0.0 ? sp2 / sp / m_cd : 0.0;
+    int sc = pl->shift_coarse;
+    if (d * 8192.0 < 1024.0) {
+      const double target = d * 1024.0 >= 8.0 ? 2048.0 : 128.0;
+      while (sc < pl->col_bits && sc < 31 && sc - pl->shift_fine < 12 &&
+             d * std::ldexp(1.0, sc) < target)
+        ++sc;
+    }
+    if (sc != pl->shift_coarse) {
+      pl->shift_coarse = sc;
+      pl->n_chunks_coarse = (int)((B->n_cols + ((int64_t)1 << sc) - 1) >> sc);
+      if (pl->n_chunks_coarse < 1) pl->n_chunks_coarse = 1;
+    }
+  }
   // coarse rows: batched by staging capacity (two 12 B/product buffers) and
   // by the size of the (row, chunk) bookkeeping
   if (!pl->coarse_rows.empty()) {

@@ -80,6 +80,23 @@ __global__ void k_ragged_fill(int64_t n, int64_t n_cols, uint64_t kc, uint64_t k
   }
 }
 
+__global__ void k_stratified(int64_t n, int64_t n_cols, int k, uint64_t kc, uint64_t kv,
+                             double lo, double hi, int64_t* __restrict__ rp,
+                             int32_t* __restrict__ col, double* __restrict__ val) {
+  const int64_t total = n * k;
+  const double w = hi - lo;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / k, j = e - r * k;
+    const int64_t s0 = j * n_cols / k, s1 = (j + 1) * n_cols / k;
+    col[e] = (int32_t)(s0 + scale32(ctr(kc, (uint64_t)e), s1 - s0));
+    const double u = (double)(ctr(kv, (uint64_t)e) >> 11) * 0x1.0p-53;
+    val[e] = __dadd_rn(lo, __dmul_rn(w, u));
+    if (j == 0) rp[r] = e;
+    if (e == total - 1) rp[n] = total;
+  }
+}
+
 __global__ void k_stencil_len(int k, int64_t* __restrict__ len) {
   const int64_t n = (int64_t)k * k * k;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
@@ -204,6 +221,22 @@ int magnus_gen_ragged_fill(int64_t n_rows, int64_t n_cols, int32_t kmin, int32_t
   k_ragged_fill<<<grid_for(n_rows), 256, 0, s>>>(n_rows, n_cols, gen_key(seed, matrix_id, 2),
                                                  gen_key(seed, matrix_id, 3), lo, hi, row_ptr,
                                                  col, val);
+  return cudaGetLastError() == cudaSuccess ? 0 : 5;
+}
+
+int magnus_gen_stratified(int64_t n_rows, int64_t n_cols, int32_t k, uint64_t seed,
+                          uint64_t matrix_id, double lo, double hi, int64_t* row_ptr,
+                          int32_t* col, double* val, void* stream) {
+  if (n_rows < 0 || n_cols < 1 || n_cols >= ((int64_t)1 << 31) || k < 1 || k > n_cols ||
+      !row_ptr || (n_rows > 0 && (!col || !val)))
+    return 1;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_rows == 0) return cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), s) == cudaSuccess ? 0 : 5;
+  int64_t blocks = (n_rows * k + 255) / 256;
+  if (blocks > 65535 * 8) blocks = 65535 * 8;
+  k_stratified<<<(unsigned)blocks, 256, 0, s>>>(n_rows, n_cols, k, gen_key(seed, matrix_id, 4),
+                                               gen_key(seed, matrix_id, 5), lo, hi, row_ptr, col,
+                                               val);
   return cudaGetLastError() == cudaSuccess ? 0 : 5;
 }
 

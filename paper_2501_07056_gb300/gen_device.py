@@ -23,6 +23,8 @@ SIGNATURES = {
     "magnus_gen_ragged_fill": (c_i32, [c_i64, c_i64, c_i32, c_i32, c_u64, c_u64, c_f64, c_f64,
                                        c_p, c_p, c_p, c_p]),
     "magnus_gen_stencil27": (c_i32, [c_i32, c_p, c_p, c_p, c_p]),
+    "magnus_gen_stratified": (c_i32, [c_i64, c_i64, c_i32, c_u64, c_u64, c_f64, c_f64, c_p, c_p,
+                                      c_p, c_p]),
 }
 _LIB = None
 
@@ -76,3 +78,18 @@ def stencil27(k: int, device="cuda", stream=None) -> DeviceCSR:
     _check(_lib().magnus_gen_stencil27(k, rp.data_ptr(), col.data_ptr(), val.data_ptr(),
                                        s.cuda_stream), "magnus_gen_stencil27")
     return DeviceCSR(n, n, rp, col, val)
+
+
+def stratified(n_rows: int, n_cols: int, k: int, seed: int = 0, matrix_id: int = 0,
+               lo: float = -1.0, hi: float = 1.0, device="cuda", stream=None) -> DeviceCSR:
+    """The stratified matrix of ``inputs.stratified``, drawn on the device."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    nnz = n_rows * k
+    rp = torch.empty(n_rows + 1, dtype=torch.int64, device=device)
+    col = torch.empty(max(nnz, 1), dtype=torch.int32, device=device)
+    val = torch.empty(max(nnz, 1), dtype=torch.float64, device=device)
+    _check(_lib().magnus_gen_stratified(n_rows, n_cols, k, seed, matrix_id, lo, hi, rp.data_ptr(),
+                                        col.data_ptr(), val.data_ptr(), s.cuda_stream),
+           "magnus_gen_stratified")
+    return DeviceCSR(n_rows, n_cols, rp, col[:nnz], val[:nnz])

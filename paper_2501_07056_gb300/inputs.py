@@ -33,7 +33,7 @@ import numpy as np
 __all__ = [
     "CSR", "rng_for", "uniform", "ragged", "rmat", "stencil27", "identity",
     "permutation", "from_dense", "batched_sizes", "batched_problems", "served_stream",
-    "workload", "ctr_key", "ctr_u64", "ragged_ctr", "ragged_ctr_nnz",
+    "workload", "ctr_key", "ctr_u64", "ragged_ctr", "ragged_ctr_nnz", "stratified",
 ]
 
 
@@ -249,6 +249,32 @@ def ragged_ctr(n_rows: int, n_cols: int, kmin: int, kmax: int, seed: int = 0,
     u = (ctr_u64(kv, r * np.uint64(64) + k) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
     vals = lo + (hi - lo) * u
     return _csr_from_lengths(n_rows, n_cols, L, cols, vals)
+
+
+def stratified(n_rows: int, n_cols: int, k: int, seed: int = 0, matrix_id: int = 0,
+               lo: float = -1.0, hi: float = 1.0, rows=None) -> CSR:
+    """Exactly k distinct ascending columns per row, one uniform draw in each
+    of k equal strata of [0, n_cols): the host twin of magnus_gen_stratified
+    (definition in include/magnus_inputs.h).  ``rows`` (optional) lists the
+    rows to fill; the others are left empty (for the oracle, which needs only
+    the rows of B that sampled rows of A reference)."""
+    if not (1 <= k <= n_cols):
+        raise ValueError("need 1 <= k <= n_cols")
+    rows = np.arange(n_rows, dtype=np.int64) if rows is None else np.unique(np.asarray(rows, np.int64))
+    lengths = np.zeros(n_rows, dtype=np.int64)
+    lengths[rows] = k
+    j = np.arange(k, dtype=np.int64)
+    e = (rows[:, None] * k + j[None, :]).astype(np.uint64).reshape(-1)
+    s0 = (j * n_cols) // k
+    width = ((j + 1) * n_cols) // k - s0
+    kc = ctr_key(seed, matrix_id, 4)
+    kv = ctr_key(seed, matrix_id, 5)
+    x = ctr_u64(kc, e).reshape(len(rows), k) >> np.uint64(32)
+    off = (x * width.astype(np.uint64)[None, :]) >> np.uint64(32)
+    cols = (s0[None, :] + off.astype(np.int64)).reshape(-1).astype(np.int32)
+    u = (ctr_u64(kv, e) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    vals = lo + (hi - lo) * u
+    return _csr_from_lengths(n_rows, n_cols, lengths, cols, vals)
 
 
 def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19,

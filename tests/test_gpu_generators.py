@@ -44,3 +44,15 @@ def test_stencil_matches_host(k):
     assert np.array_equal(c, H.col)
     assert np.array_equal(v, H.val)
     assert H.nnz == (3 * k - 2) ** 3
+
+
+@pytest.mark.parametrize("n,m,k,mid", [(300, 1 << 20, 512, 1), (64, 1000, 1000, 2), (7, 5, 3, 3),
+                                        (1000, 1 << 30, 37, 4)])
+def test_stratified_matches_host(n, m, k, mid):
+    from paper_2501_07056_gb300 import gen_device
+    D = gen_device.stratified(n, m, k, 0, mid)
+    H = inputs.stratified(n, m, k, 0, mid)
+    rp, c, v = _host(D)
+    assert np.array_equal(rp, H.row_ptr)
+    assert np.array_equal(c, H.col)
+    assert np.array_equal(v.view(np.uint64), H.val.view(np.uint64))

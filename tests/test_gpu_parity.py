@@ -87,6 +87,31 @@ def test_block_sort_64bit_keys():
     assert got["info"]["key_bits32"] == 0
 
 
+@pytest.mark.parametrize("m_log2,k", [(26, 128), (20, 200), (30, 64)])
+def test_massive_nonsquare_sampled(m_log2, k):
+    # the massive nonsquare uniform workload at reduced size: rows of k*k
+    # products spread over 2^m_log2 columns go to the coarse level, whose
+    # chunks widen with the sparsity of the rows
+    import torch
+    from paper_2501_07056_gb300 import gen_device, magnus
+    rows_a, kdim = 64, 1 << 14
+    dA = gen_device.stratified(rows_a, kdim, k, 0, 11)
+    dB = gen_device.stratified(kdim, 1 << m_log2, k, 0, 12)
+    plan = magnus.Plan(dA, dB)
+    plan.symbolic()
+    col, val = plan.numeric()
+    torch.cuda.synchronize()
+    info = plan.info()
+    assert info["rows_per_category"][COARSE] == rows_a
+    if m_log2 >= 26:
+        assert info["chunk_len_coarse_log2"] > 13
+    A = inputs.stratified(rows_a, kdim, k, 0, 11)
+    B = inputs.stratified(kdim, 1 << m_log2, k, 0, 12, rows=np.unique(A.col))
+    got = dict(row_ptr=plan.c_row_ptr.cpu().numpy(), col=col.cpu().numpy(), val=val.cpu().numpy())
+    assert_parity(got, A, B)
+    plan.free()
+
+
 @pytest.mark.parametrize("force", [-1, SORT, DENSE, FINE, COARSE])
 def test_rmat_small(force):
     A = inputs.rmat(13, 16, seed=0)

@@ -88,3 +88,18 @@ def test_ragged_ctr_full_rows():
     A.validate()
     assert np.all(np.diff(A.row_ptr) == 20)
     assert np.array_equal(A.col.reshape(50, 20), np.tile(np.arange(20, dtype=np.int32), (50, 1)))
+
+
+def test_stratified_rows():
+    A = inputs.stratified(200, 10000, 64, seed=0, matrix_id=3)
+    A.validate()
+    assert np.all(np.diff(A.row_ptr) == 64)
+    # one column in each of the 64 strata [floor(j n/k), floor((j+1) n/k))
+    j = np.arange(64, dtype=np.int64)
+    c = A.col.reshape(200, 64).astype(np.int64)
+    assert np.all(c >= (j * 10000) // 64) and np.all(c < ((j + 1) * 10000) // 64)
+    # partial generation fills exactly the listed rows, with the same entries
+    P = inputs.stratified(200, 10000, 64, seed=0, matrix_id=3, rows=[3, 150])
+    assert P.nnz == 128
+    assert np.array_equal(P.col[:64], A.col[3 * 64:4 * 64])
+    assert np.array_equal(P.val[64:], A.val[150 * 64:151 * 64])
