@@ -66,6 +66,10 @@ WORKLOADS = {
                  "both (counter-based generator, drawn on the device), FP64 U(-1,1), seed 0",
     "massive30": "C=A*B, A 4096 x 2^21 and B 2^21 x 2^30, 512 stratified-uniform cols/row in "
                  "both (counter-based generator, drawn on the device), FP64 U(-1,1), seed 0",
+    "ablation": "building blocks of one reorder level (histogram, scan, reorder, per-chunk "
+                "dense accumulation) on a uniform stream of 2^28 (int32 index, FP64 value) "
+                "pairs with indices in [0, 2^16), [0, 2^20) and [0, 2^24), against a stream "
+                "copy and a global dense accumulator; chunk count swept 2^0..2^14",
     "batched4096": "4096 independent products C_i=A_i*B_i, n_i log-uniform in [256, 65536], "
                    "A_i and B_i n_i x n_i with nnz/row uniform in {2..32} (counter-based "
                    "generator, drawn on the device), FP64 U(-1,1), seed 0",
@@ -713,6 +717,56 @@ def run_served(args, dist):
     }
 
 
+def run_ablation(args, dist):
+    """Figures 5-6 analogue: per-step device times of one reorder level versus
+    the number of chunks, and their sum relative to a stream copy."""
+    import torch
+
+    from paper_2501_07056_gb300 import gen_device, magnus
+
+    dev = torch.device("cuda", dist.local_rank if dist.world > 1 else 0)
+    torch.cuda.set_device(dev)
+    n = 1 << 28
+    sweep = []
+    clocks = ClockSampler(dev.index).start()
+    for m_log2 in (16, 20, 24):
+        m = 1 << m_log2
+        col, val = gen_device.uniform_stream(n, m, 0, m_log2, device=dev)
+        for lg in range(0, 15):
+            best = None
+            for _ in range(max(1, args.warmup)):  # keep the fastest of the repeats
+                r, _, _, _ = magnus.microbench_chunks(col, val, m, lg)
+                if best is None or r["copy_ms"] < best["copy_ms"]:
+                    best = r
+            reorder = best["reorder_ms"]
+            if best["reorder_staged_ms"] >= 0:
+                reorder = min(reorder, best["reorder_staged_ms"])
+            steps = best["histogram_ms"] + best["scan_ms"] + reorder
+            best["reorder_level_over_copy"] = steps / best["copy_ms"]
+            if best["accumulate_ms"] >= 0:
+                best["with_accumulate_over_copy"] = (steps + best["accumulate_ms"]) / best["copy_ms"]
+                best["global_accumulate_over_copy"] = best["global_accumulate_ms"] / best["copy_ms"]
+            best["chunks_log2"] = lg
+            best["index_range_log2"] = m_log2
+            sweep.append(best)
+        del col, val
+    clk = clocks.stop()
+    full = [r["with_accumulate_over_copy"] for r in sweep if "with_accumulate_over_copy" in r]
+    copy_gbs = n * 24 / (min(r["copy_ms"] for r in sweep) * 1e-3) / 1e9
+    return {
+        "metric": "reorder level + dense accumulation time over stream copy", "value": min(full),
+        "unit": "x", "n_gpus": dist.world, "steps": len(sweep), "warmup": args.warmup,
+        "ms_per_step": sum(r["copy_ms"] for r in sweep) / len(sweep),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS["ablation"], "stream": n, "index_range": "2^16, 2^20, 2^24",
+                   "copy_GBps": copy_gbs,
+                   "paper": "Section 4.1: about 2.2x streaming time at the optimal chunk "
+                            "count, reorder breaking point at 2^13 chunks (1 core, SPR)"},
+        "sweep": sweep, "clocks": clk, "gpu_launches": 5 * len(sweep),
+    }
+
+
 def run_e2e(args, dist, A, dev, params, n_inter, nnz_c):
     """Same metric through the public API with host buffers: every step
     copies A from pinned host memory to the device, computes C and copies C
@@ -768,6 +822,8 @@ def main(argv=None):
             res = run_batched(args, dist)
         elif args.workload == "served":
             res = run_served(args, dist)
+        elif args.workload == "ablation":
+            res = run_ablation(args, dist)
         else:
             res = run_ours(args, dist)
         if dist.rank == 0 and res is not None:

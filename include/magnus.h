@@ -295,6 +295,40 @@ int magnus_autotune(const magnus_csr_t* A, const magnus_csr_t* B, const magnus_p
                     int64_t sample_products, int32_t max_trials, magnus_params_t* best,
                     magnus_tune_report_t* report, void* stream);
 
+/* ---- building-block microbenchmark ---------------------------------------
+ * The steps of one reorder level (Section 4.1, Figures 5-6) on a stream of
+ * `length` (index, value) pairs with indices in [0, m): histogram per chunk
+ * (index >> shift, 2^n_chunks_log2 chunks), prefix sum, reorder into chunk
+ * order (element by element, and staged through shared memory), and
+ * per-chunk dense accumulation (one block's shared-memory
+ * accumulator; only when the chunk length 2^shift is at most 2^13), each
+ * timed with CUDA events on `stream`; beside them a copy of the stream and a
+ * dense accumulator over all of [0, m) in global memory (FP64 atomics, no
+ * locality generation).  col/val: device input (caller-owned).
+ * out_col/out_val: device, `length` entries: chunk c's unique indices
+ * (ascending, global numbering) with their sums start at the chunk's first
+ * element in chunk order; chunk_nnz (device, n_chunks entries, may be NULL
+ * when no accumulation runs) gets their counts.  m <= 2^31, n_chunks_log2 in
+ * 0..14.  Allocates and frees its scratch; synchronises `stream`.  The paper
+ * has no counterpart as an API: it is its microbenchmark. */
+typedef struct {
+  float copy_ms;
+  float histogram_ms;
+  float scan_ms;
+  float reorder_ms;
+  float accumulate_ms;          /* -1 when the chunks exceed 2^13 indices */
+  float global_accumulate_ms;
+  int32_t n_chunks;
+  int32_t chunk_len_log2;
+  float reorder_staged_ms;      /* tile sorted by chunk in shared memory, then
+                                   written as runs; -1 above 4096 chunks */
+  int32_t reserved;
+} magnus_microbench_t;
+
+int magnus_microbench_chunks(const int32_t* col, const double* val, int64_t length, int64_t m,
+                             int32_t n_chunks_log2, int32_t* out_col, double* out_val,
+                             int64_t* chunk_nnz, magnus_microbench_t* result, void* stream);
+
 /* ---- plan introspection ------------------------------------------------ */
 typedef struct {
   int64_t n_rows;               /* rows of A (= rows of C) */

@@ -36,6 +36,10 @@
  * lo + (hi - lo) * (ctr(key(s,id,5), r*k + j) >> 11) * 2^-53 (one product,
  * one sum).  Requires 1 <= k <= n_cols.
  *
+ * Uniform stream (the building-block microbenchmark): element i has index
+ * floor(hi32(ctr(key(s,id,6), i)) * m / 2^32) and value
+ * lo + (hi - lo) * (ctr(key(s,id,7), i) >> 11) * 2^-53.
+ *
  * 27-point stencil on a k x k x k grid, lexicographic numbering, truncated at
  * the boundary: 26 on the diagonal and -1 at every in-range neighbour;
  * nnz = (3k - 2)^3.
@@ -72,6 +76,10 @@ int magnus_gen_ragged_fill(int64_t n_rows, int64_t n_cols, int32_t kmin, int32_t
 int magnus_gen_stratified(int64_t n_rows, int64_t n_cols, int32_t k, uint64_t seed,
                           uint64_t matrix_id, double lo, double hi, int64_t* row_ptr,
                           int32_t* col, double* val, void* stream);
+
+/* The uniform stream: col and val (n entries each), 1 <= m <= 2^31. */
+int magnus_gen_uniform_stream(int64_t n, int64_t m, uint64_t seed, uint64_t stream_id, double lo,
+                              double hi, int32_t* col, double* val, void* stream);
 
 /* The 27-point stencil on a k^3 grid: row_ptr (k^3 + 1), col and val
  * ((3k-2)^3 each).  1 <= k <= 1290. */

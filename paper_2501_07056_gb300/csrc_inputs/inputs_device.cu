@@ -1,5 +1,5 @@
-// On-device generators of the synthetic benchmark inputs (ragged random
-// matrices and 27-point stencils).  Input generation only: no SpGEMM
+// On-device generators of the synthetic benchmark inputs (ragged, stratified
+// and stencil matrices, uniform index streams).  Input generation only: no SpGEMM
 // arithmetic here, and nothing here is shared with the SpGEMM library.  The
 // definitions are stated in magnus_inputs.h; inputs.py holds the host twin.
 #include <cuda_runtime.h>
@@ -94,6 +94,17 @@ __global__ void k_stratified(int64_t n, int64_t n_cols, int k, uint64_t kc, uint
     val[e] = __dadd_rn(lo, __dmul_rn(w, u));
     if (j == 0) rp[r] = e;
     if (e == total - 1) rp[n] = total;
+  }
+}
+
+__global__ void k_uniform_stream(int64_t n, int64_t m, uint64_t kc, uint64_t kv, double lo,
+                                 double hi, int32_t* __restrict__ col, double* __restrict__ val) {
+  const double w = hi - lo;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    col[i] = (int32_t)scale32(ctr(kc, (uint64_t)i), m);
+    const double u = (double)(ctr(kv, (uint64_t)i) >> 11) * 0x1.0p-53;
+    val[i] = __dadd_rn(lo, __dmul_rn(w, u));
   }
 }
 
@@ -237,6 +248,18 @@ int magnus_gen_stratified(int64_t n_rows, int64_t n_cols, int32_t k, uint64_t se
   k_stratified<<<(unsigned)blocks, 256, 0, s>>>(n_rows, n_cols, k, gen_key(seed, matrix_id, 4),
                                                gen_key(seed, matrix_id, 5), lo, hi, row_ptr, col,
                                                val);
+  return cudaGetLastError() == cudaSuccess ? 0 : 5;
+}
+
+int magnus_gen_uniform_stream(int64_t n, int64_t m, uint64_t seed, uint64_t stream_id, double lo,
+                              double hi, int32_t* col, double* val, void* stream) {
+  if (n < 0 || m < 1 || m > ((int64_t)1 << 31) || (n > 0 && (!col || !val))) return 1;
+  if (n == 0) return 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 65535 * 8) blocks = 65535 * 8;
+  k_uniform_stream<<<(unsigned)blocks, 256, 0, s>>>(n, m, gen_key(seed, stream_id, 6),
+                                                   gen_key(seed, stream_id, 7), lo, hi, col, val);
   return cudaGetLastError() == cudaSuccess ? 0 : 5;
 }
 

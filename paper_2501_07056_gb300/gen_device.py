@@ -25,6 +25,7 @@ SIGNATURES = {
     "magnus_gen_stencil27": (c_i32, [c_i32, c_p, c_p, c_p, c_p]),
     "magnus_gen_stratified": (c_i32, [c_i64, c_i64, c_i32, c_u64, c_u64, c_f64, c_f64, c_p, c_p,
                                       c_p, c_p]),
+    "magnus_gen_uniform_stream": (c_i32, [c_i64, c_i64, c_u64, c_u64, c_f64, c_f64, c_p, c_p, c_p]),
 }
 _LIB = None
 
@@ -93,3 +94,16 @@ def stratified(n_rows: int, n_cols: int, k: int, seed: int = 0, matrix_id: int =
                                         col.data_ptr(), val.data_ptr(), s.cuda_stream),
            "magnus_gen_stratified")
     return DeviceCSR(n_rows, n_cols, rp, col[:nnz], val[:nnz])
+
+
+def uniform_stream(n: int, m: int, seed: int = 0, stream_id: int = 0, lo: float = -1.0,
+                   hi: float = 1.0, device="cuda", stream=None):
+    """(col, val) tensors of ``inputs.uniform_stream``, drawn on the device."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    col = torch.empty(max(n, 1), dtype=torch.int32, device=device)
+    val = torch.empty(max(n, 1), dtype=torch.float64, device=device)
+    _check(_lib().magnus_gen_uniform_stream(n, m, seed, stream_id, lo, hi, col.data_ptr(),
+                                            val.data_ptr(), s.cuda_stream),
+           "magnus_gen_uniform_stream")
+    return col[:n], val[:n]

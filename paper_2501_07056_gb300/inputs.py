@@ -34,6 +34,7 @@ __all__ = [
     "CSR", "rng_for", "uniform", "ragged", "rmat", "stencil27", "identity",
     "permutation", "from_dense", "batched_sizes", "batched_problems", "served_stream",
     "workload", "ctr_key", "ctr_u64", "ragged_ctr", "ragged_ctr_nnz", "stratified",
+    "uniform_stream",
 ]
 
 
@@ -275,6 +276,16 @@ def stratified(n_rows: int, n_cols: int, k: int, seed: int = 0, matrix_id: int =
     u = (ctr_u64(kv, e) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
     vals = lo + (hi - lo) * u
     return _csr_from_lengths(n_rows, n_cols, lengths, cols, vals)
+
+
+def uniform_stream(n: int, m: int, seed: int = 0, stream_id: int = 0, lo: float = -1.0,
+                   hi: float = 1.0):
+    """(col, val) of a stream of n uniform indices in [0, m): the host twin
+    of magnus_gen_uniform_stream (building-block microbenchmark)."""
+    i = np.arange(n, dtype=np.uint64)
+    col = _scale32(ctr_u64(ctr_key(seed, stream_id, 6), i), m).astype(np.int32)
+    u = (ctr_u64(ctr_key(seed, stream_id, 7), i) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    return col, lo + (hi - lo) * u
 
 
 def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19,

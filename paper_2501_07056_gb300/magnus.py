@@ -65,6 +65,14 @@ class TuneReport(ctypes.Structure):
                 ("products_full", c_i64), ("base_ms", ctypes.c_float), ("best_ms", ctypes.c_float)]
 
 
+class MicrobenchResult(ctypes.Structure):
+    _fields_ = [("copy_ms", ctypes.c_float), ("histogram_ms", ctypes.c_float),
+                ("scan_ms", ctypes.c_float), ("reorder_ms", ctypes.c_float),
+                ("accumulate_ms", ctypes.c_float), ("global_accumulate_ms", ctypes.c_float),
+                ("n_chunks", c_i32), ("chunk_len_log2", c_i32),
+                ("reorder_staged_ms", ctypes.c_float), ("reserved", c_i32)]
+
+
 class ChunkModel(ctypes.Structure):
     _fields_ = [("m_c_log2", c_i32), ("chunk_len_fine_log2", c_i32),
                 ("chunk_len_fine_sym_log2", c_i32), ("n_chunks_fine_max_log2", c_i32),
@@ -106,6 +114,8 @@ SIGNATURES = {
     "magnus_batch_info": (c_i32, [c_p, ctypes.POINTER(PlanInfo)]),
     "magnus_free_batched": (None, [c_p]),
     "magnus_batch_inner_plan": (c_p, [c_p]),
+    "magnus_microbench_chunks": (c_i32, [c_p, c_p, c_i64, c_i64, c_i32, c_p, c_p, c_p,
+                                         ctypes.POINTER(MicrobenchResult), c_p]),
     "magnus_autotune": (c_i32, [ctypes.POINTER(CsrDesc), ctypes.POINTER(CsrDesc),
                                 ctypes.POINTER(Params), c_i64, c_i32, ctypes.POINTER(Params),
                                 ctypes.POINTER(TuneReport), c_p]),
@@ -320,6 +330,25 @@ def autotune(A: "DeviceCSR", B: "DeviceCSR", base: Params | None = None, sample_
                                   sample_products, max_trials, ctypes.byref(best),
                                   ctypes.byref(rep), c_p(s.cuda_stream)), "magnus_autotune")
     return best, {name: getattr(rep, name) for name, _ in rep._fields_}
+
+
+def microbench_chunks(col, val, m: int, n_chunks_log2: int, stream=None):
+    """magnus_microbench_chunks on device tensors; returns (result dict,
+    out_col, out_val, chunk_nnz)."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    n = col.numel()
+    out_col = torch.empty(n, dtype=torch.int32, device=col.device)
+    out_val = torch.empty(n, dtype=torch.float64, device=col.device)
+    nch = 1 << n_chunks_log2
+    chunk_nnz = torch.zeros(nch + 1, dtype=torch.int64, device=col.device)
+    res = MicrobenchResult()
+    _check(_lib().magnus_microbench_chunks(c_p(col.data_ptr()), c_p(val.data_ptr()), n, m,
+                                           n_chunks_log2, c_p(out_col.data_ptr()),
+                                           c_p(out_val.data_ptr()), c_p(chunk_nnz.data_ptr()),
+                                           ctypes.byref(res), c_p(s.cuda_stream)),
+           "magnus_microbench_chunks")
+    return ({name: getattr(res, name) for name, _ in res._fields_}, out_col, out_val, chunk_nnz)
 
 
 def params_dict(p: Params) -> dict:

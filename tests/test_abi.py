@@ -41,7 +41,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_input_generator_symbols_are_exported(lib):
     from paper_2501_07056_gb300 import gen_device
     names = _declared("magnus_inputs.h")
-    assert len(names) == 4
+    assert len(names) == 5
     raw = ctypes.CDLL(gen_device.LIB_PATH)
     for n in names:
         assert hasattr(raw, n), n
