@@ -169,7 +169,7 @@ struct CoarseArgs {
   int32_t* rows_b;           // coarseRowsB list
   int32_t* n_rows_b;         // device counter
   int64_t* counts;           // n_rows * n_chunks + 1 (becomes offsetsCoarse)
-  int32_t* cursor;           // n_rows * n_chunks
+  unsigned long long* cursor; // n_rows * n_chunks: reorder position per bucket
   int32_t* chunk_col;        // staged products
   double* chunk_val;
   int32_t* fine_col;         // second staging buffer for the fine level

@@ -89,7 +89,8 @@ __global__ void k_coarse_outer(Csr B, const int64_t* __restrict__ item_off, int6
                                const int64_t* __restrict__ col_ptr,
                                const int32_t* __restrict__ csc_row,
                                const double* __restrict__ csc_val, int sc, int nc,
-                               int64_t* __restrict__ counts, int32_t* __restrict__ cursor,
+                               int64_t* __restrict__ counts,
+                               unsigned long long* __restrict__ cursor,
                                int32_t* __restrict__ chunk_col, double* __restrict__ chunk_val) {
   const int lane = lane_id();
   const int64_t total = item_off[nB];
@@ -120,13 +121,21 @@ __global__ void k_coarse_outer(Csr B, const int64_t* __restrict__ item_off, int6
     const int chunk = col >> sc;
     const int64_t e0 = cs + et * ET;
     const int64_t e1 = (e0 + ET < cs + C) ? e0 + ET : cs + C;
+    // the A^CSC entry of the next step is loaded one step ahead
+    int32_t t_nx = (valid && e0 + sub < e1) ? csc_row[e0 + sub] : 0;
+    double av_nx = (NUMERIC && valid && e0 + sub < e1) ? csc_val[e0 + sub] : 0.0;
     for (int64_t eg = e0; eg < e1; eg += G) {
       const int64_t e = eg + sub;
       const bool on = valid && e < e1;
+      const int32_t t = t_nx;
+      const double av = av_nx;
+      const int64_t en = e + G;
+      if (valid && en < e1) {
+        t_nx = csc_row[en];
+        if (NUMERIC) av_nx = csc_val[en];
+      }
       const unsigned active = __ballot_sync(FULL, on);
       if (on) {
-        const int32_t t = csc_row[e];
-        const double av = NUMERIC ? csc_val[e] : 0.0;
         const int64_t slot = (int64_t)t * nc + chunk;
         const unsigned m = __match_any_sync(active, (unsigned long long)slot);
         const int leader = __ffs(m) - 1;
@@ -135,10 +144,12 @@ __global__ void k_coarse_outer(Csr B, const int64_t* __restrict__ item_off, int6
             atomicAdd(reinterpret_cast<unsigned long long*>(&counts[slot]),
                       (unsigned long long)__popc(m));
         } else {
-          int base = 0;
-          if (lane == leader) base = atomicAdd(&cursor[slot], __popc(m));
+          // the cursor starts at the bucket's offset: one atomic gives the
+          // group's absolute position
+          unsigned long long base = 0;
+          if (lane == leader) base = atomicAdd(&cursor[slot], (unsigned long long)__popc(m));
           base = __shfl_sync(m, base, leader);
-          const int64_t pos = counts[slot] + base + __popc(m & ((1u << lane) - 1));
+          const int64_t pos = (int64_t)base + __popc(m & ((1u << lane) - 1));
           st_stream(&chunk_col[pos], col - (chunk << sc));
           if (NUMERIC) st_stream(&chunk_val[pos], av * bv);
         }
@@ -472,7 +483,7 @@ static cudaError_t coarse_impl(CoarseArgs& a, cudaStream_t s) {
   // 3. row-chained prefix sum
   CK(launch_exclusive_scan_i64(a.counts, nbk, a.scan_tmp, s));
   // 4. reorder
-  CK(cudaMemsetAsync(a.cursor, 0, (size_t)nbk * sizeof(int32_t), s));
+  CK(cudaMemcpyAsync(a.cursor, a.counts, (size_t)nbk * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
   k_coarse_outer<true, NUMERIC><<<go, nt, 0, s>>>(a.B, a.item_off, nB, a.col_ptr, a.csc_row,
                                                   a.csc_val, a.shift_coarse, a.n_chunks, a.counts,
                                                   a.cursor, a.chunk_col, a.chunk_val);
