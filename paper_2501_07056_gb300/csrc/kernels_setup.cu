@@ -74,12 +74,21 @@ __global__ void k_rowinfo(Csr A, Csr B, CatParams cp, int64_t* __restrict__ P,
     int64_t s = 0, e = 0;
     if (active) { s = A.rp[i]; e = A.rp[i + 1]; }
     int64_t p = 0;
-    for (int64_t j = s + sub; j < e; j += V) {
+    // two entries per lane and step, their loads issued together
+    for (int64_t j = s + sub; j < e; j += 2 * V) {
+      const int64_t j2 = j + V;
+      const bool two = j2 < e;
       const int32_t c = A.col[j];
+      const int32_t c2 = two ? A.col[j2] : 0;
       const int64_t b0 = B.rp[c], b1 = B.rp[c + 1];
-      p += b1 - b0;
+      const int64_t b2 = two ? B.rp[c2] : 0, b3 = two ? B.rp[c2 + 1] : 0;
+      p += (b1 - b0) + (b3 - b2);
       seg_bs[j] = b0;
       seg_len[j] = (int32_t)(b1 - b0);
+      if (two) {
+        seg_bs[j2] = b2;
+        seg_len[j2] = (int32_t)(b3 - b2);
+      }
     }
 #pragma unroll
     for (int d = V / 2; d > 0; d >>= 1) p += __shfl_xor_sync(gmask, p, d, V);
@@ -149,8 +158,8 @@ cudaError_t launch_rowinfo(const Csr& A, const Csr& B, CatParams cp, int64_t* P,
   if (A.n_rows == 0) return cudaSuccess;
   const double avg = A.n_rows ? (double)A.nnz / (double)A.n_rows : 0.0;
   const int nt = 256;
-  int v = 1;
-  while (v < 32 && v < avg) v <<= 1;
+  int v = 1;  // lanes per row: about half the row's nonzeros (two per lane)
+  while (v < 32 && 2 * v < avg) v <<= 1;
   unsigned g = grid_cap(cdiv(A.n_rows * v, nt), 1 << 20);
   switch (v) {
     case 1: k_rowinfo<1><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg_bs, seg_len); break;
