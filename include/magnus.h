@@ -95,7 +95,11 @@ typedef struct {
  *                     the fine one is raised to it.
  * dense_chunk_threshold per-chunk hybrid threshold (Section 3.4): a fine chunk
  *                     with at least this many products uses the dense
- *                     accumulator, otherwise the sort accumulator; 0 = auto.
+ *                     accumulator, otherwise the sort accumulator (a warp
+ *                     bitonic sort; values above 257 act as 257); 0 = 1
+ *                     (dense only: on GB300 a warp's dense accumulator
+ *                     beats the warp sort down to about 16 products per
+ *                     chunk; the autotuner tries the hybrid).
  * validate            1 = check the input CSR structure on the device in
  *                     magnus_plan (returns MAGNUS_UNSORTED_OR_DUP on failure).
  * max_scratch_bytes   upper bound on the reorder staging buffer of one batch

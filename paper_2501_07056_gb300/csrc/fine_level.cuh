@@ -1,18 +1,24 @@
 // Fine-level chunk accumulation shared by fine rows and large coarse chunks
-// (Algorithm 3 accumulation step with the Section 3.4 dense accumulator).
+// (Algorithm 3 accumulation step with the hybrid accumulator of Section 3.4).
 //
-// The staged products of a row (or coarse chunk) are grouped by fine chunk;
-// each warp of the block owns a private dense accumulator of one chunk's
-// columns in shared memory (FP64 values and a bitmap in the numeric phase,
-// the bitmap alone in the symbolic phase).  Warps take consecutive chunks, a
-// round of FNW chunks at a time, so a round needs two block barriers for the
-// prefix of its chunk counts instead of barriers per chunk.  Emission walks
-// the bitmap in column order and resets exactly the entries it touched, as
-// Algorithm 1's output loop resets its bitmap, so the accumulators are clean
-// for the next chunk without clearing the whole array.
+// The staged products of a row (or coarse chunk) are grouped by fine chunk.
+// Each chunk is accumulated by one warp, chosen chunk by chunk:
+//   * fewer than `dthr` products (at most 256): sort accumulator - the
+//     chunk's (column, position) keys are sorted by the warp's bitonic
+//     network and runs of equal columns are merged (Algorithm 2);
+//   * otherwise: dense accumulator - each warp owns a private accumulator of
+//     one chunk's columns in shared memory (FP64 values and a bitmap in the
+//     numeric phase, the bitmap alone in the symbolic phase).
+// Warps take consecutive chunks, a round of FNW chunks at a time, so a round
+// needs two block barriers for the prefix of its chunk counts instead of
+// barriers per chunk.  Dense emission walks the bitmap in column order and
+// resets exactly the entries it touched, as Algorithm 1's output loop resets
+// its bitmap, so the accumulators are clean for the next chunk without
+// clearing the whole array.
 #pragma once
 
 #include "block_accum.cuh"
+#include "sort_accum.cuh"
 
 namespace magnus {
 
@@ -21,6 +27,7 @@ constexpr int FNW = FNT / 32;      // warps per block
 constexpr int WARP_ACC_LOG2 = 10;  // numeric: 1024 FP64 columns per warp accumulator
 constexpr int WARP_BITS_LOG2 = 13; // symbolic: 8192 columns per warp bitmap
 constexpr int DIRECT_BITS_LOG2 = 19;  // symbolic: block bitmap for a whole row's range
+constexpr int FINE_SORT_MAX = 256;    // largest chunk the warp sort accumulator takes
 
 struct FineSmem {
   int32_t* cnt;     // [FINE_MAX_CHUNKS]     chunk histogram, then reorder cursor
@@ -30,13 +37,17 @@ struct FineSmem {
   int words;        // bitmap words per warp
   uint32_t* direct; // symbolic: block bitmap of a whole row (aliases the above)
   int64_t* wcnt;    // [FNW + 1]             chunk counts of the current round
+  double* svals;    // [FNW][FINE_SORT_MAX]  sort accumulator: values by position (numeric)
+  uint32_t* skeys;  // [FNW][FINE_SORT_MAX]  sort accumulator: sorted keys (numeric)
 };
 
 __host__ __device__ inline int fine_words(int shift) { return shift >= 5 ? (1 << (shift - 5)) : 1; }
 
 // Shared memory of the fine kernels for a chunk shift (numeric: shift <=
-// WARP_ACC_LOG2; symbolic: shift <= WARP_BITS_LOG2).
-__host__ __device__ inline size_t fine_smem_bytes(bool numeric, int shift) {
+// WARP_ACC_LOG2; symbolic: shift <= WARP_BITS_LOG2).  `hybrid`: a hybrid
+// threshold above 1 is in use, so the numeric sort accumulator's per-warp
+// staging is reserved as well (dense-only launches do without it).
+__host__ __device__ inline size_t fine_smem_bytes(bool numeric, int shift, bool hybrid) {
   size_t b = (size_t)FINE_MAX_CHUNKS * 4 + (size_t)(FINE_MAX_CHUNKS + 1) * 4;
   b = (b + 15) & ~(size_t)15;
   if (numeric) b += (size_t)FNW * ((size_t)1 << shift) * 8;
@@ -48,10 +59,11 @@ __host__ __device__ inline size_t fine_smem_bytes(bool numeric, int shift) {
   }
   b = (b + 15) & ~(size_t)15;
   b += (FNW + 1) * 8;
+  if (numeric && hybrid) b += (size_t)FNW * FINE_SORT_MAX * (8 + 4);
   return b;
 }
 
-__device__ inline FineSmem fine_carve(unsigned char* base, bool numeric, int shift) {
+__device__ inline FineSmem fine_carve(unsigned char* base, bool numeric, int shift, bool hybrid) {
   FineSmem f;
   size_t o = 0;
   f.cnt = reinterpret_cast<int32_t*>(base + o);
@@ -72,6 +84,10 @@ __device__ inline FineSmem fine_carve(unsigned char* base, bool numeric, int shi
   }
   o = (o + 15) & ~(size_t)15;
   f.wcnt = reinterpret_cast<int64_t*>(base + o);
+  o += (FNW + 1) * 8;
+  f.svals = (numeric && hybrid) ? reinterpret_cast<double*>(base + o) : nullptr;
+  if (numeric && hybrid) o += (size_t)FNW * FINE_SORT_MAX * 8;
+  f.skeys = (numeric && hybrid) ? reinterpret_cast<uint32_t*>(base + o) : nullptr;
   return f;
 }
 
@@ -86,43 +102,89 @@ __device__ inline void fine_clear(const FineSmem& f, int shift) {
   __syncthreads();
 }
 
+// Sort accumulator of one chunk of n <= 32*E products: keys (column in the
+// chunk, position in the staging) sorted by the warp; returns the distinct
+// count and leaves the sorted keys in k[0..E).
+template <int E>
+__device__ __forceinline__ int fine_sort_count(uint32_t (&k)[8], const int32_t* __restrict__ cols,
+                                               int n, int cmask) {
+  constexpr int SB = Log2Cap<E>::v;
+  uint32_t kk[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int s = e * 32 + lane_id();
+    kk[e] = s < n ? KeyTraits<uint32_t>::template make<SB>(cols[s] & cmask, s) : ~0u;
+  }
+  warp_bitonic_sort<E>(kk);
+#pragma unroll
+  for (int e = 0; e < E; ++e) k[e] = kk[e];
+  return warp_merge_emit<E, uint32_t, false>(kk, n, nullptr, nullptr, 0, nullptr, nullptr);
+}
+
+template <int E>
+__device__ __forceinline__ void fine_sort_emit(const uint32_t (&k)[8], int n, const double* vals,
+                                               uint32_t* skeys, int32_t col_add,
+                                               int32_t* __restrict__ out_col,
+                                               double* __restrict__ out_val) {
+  uint32_t kk[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) kk[e] = k[e];
+  warp_merge_emit<E, uint32_t, true>(kk, n, vals, skeys, col_add, out_col, out_val);
+}
+
 // Accumulates the staged chunks [0, nch): chunk ch holds
 // stage_col/stage_val[off[ch] .. off[ch + 1]), columns relative to col_base
 // (chunk index << shift | column inside the chunk).  Writes the sorted unique
-// entries to out_col/out_val[0..) (numeric) and returns their number.  All
-// threads must call; the warp accumulators must be clean on entry and are
-// clean on exit.
+// entries to out_col/out_val[0..) (numeric) and returns their number.  A
+// chunk with fewer than dthr products (dthr <= FINE_SORT_MAX + 1) takes the
+// sort accumulator, the others the dense one.  All threads must call; the
+// warp accumulators must be clean on entry and are clean on exit.
 template <bool NUMERIC>
 __device__ int64_t warp_chunks_accumulate(const FineSmem& f, int nch, int shift,
                                           const int32_t* __restrict__ stage_col,
                                           const double* __restrict__ stage_val,
                                           int64_t col_base, int32_t* __restrict__ out_col,
-                                          double* __restrict__ out_val) {
+                                          double* __restrict__ out_val, int dthr) {
   const int lane = lane_id(), w = warp_id();
   const int cl = 1 << shift;
   const int words = f.words;
   double* acc = f.acc + (size_t)w * cl;
   uint32_t* bits = f.bits + (size_t)w * words;
+  double* svals = NUMERIC ? f.svals + (size_t)w * FINE_SORT_MAX : nullptr;
+  uint32_t* skeys = NUMERIC ? f.skeys + (size_t)w * FINE_SORT_MAX : nullptr;
   const int wpl = (words + 31) / 32;  // bitmap words per lane, in column order
   int64_t outp = 0;
   for (int r0 = 0; r0 < nch; r0 += FNW) {
     const int ch = r0 + w;
-    int cnt = 0;
+    int cnt = 0, lane_cnt = 0, n = 0, sort_e = 0;
+    uint32_t key[8];
     if (ch < nch) {
       const int p0 = f.off[ch], p1 = f.off[ch + 1];
-      for (int p = p0 + lane; p < p1; p += 32) {
-        const int idx = stage_col[p] & (cl - 1);
-        atomicOr(&bits[idx >> 5], 1u << (idx & 31));
-        if (NUMERIC) atomicAdd(&acc[idx], stage_val[p]);
-      }
-      __syncwarp();
-      for (int k = 0; k < wpl; ++k) {
-        const int wd = lane * wpl + k;
-        if (wd < words) cnt += __popc(bits[wd]);
+      n = p1 - p0;
+      if (n > 0 && n < dthr && n <= FINE_SORT_MAX && (!NUMERIC || f.svals != nullptr)) {
+        // sort accumulator (warp-uniform branch: n is the same in all lanes)
+        if (NUMERIC)
+          for (int s = lane; s < n; s += 32) svals[s] = stage_val[p0 + s];
+        sort_e = n <= 32 ? 1 : n <= 64 ? 2 : n <= 128 ? 4 : 8;
+        const int32_t* cc = stage_col + p0;
+        if (sort_e == 1) cnt = fine_sort_count<1>(key, cc, n, cl - 1);
+        else if (sort_e == 2) cnt = fine_sort_count<2>(key, cc, n, cl - 1);
+        else if (sort_e == 4) cnt = fine_sort_count<4>(key, cc, n, cl - 1);
+        else cnt = fine_sort_count<8>(key, cc, n, cl - 1);
+      } else {
+        for (int p = p0 + lane; p < p1; p += 32) {
+          const int idx = stage_col[p] & (cl - 1);
+          atomicOr(&bits[idx >> 5], 1u << (idx & 31));
+          if (NUMERIC) atomicAdd(&acc[idx], stage_val[p]);
+        }
+        __syncwarp();
+        for (int k = 0; k < wpl; ++k) {
+          const int wd = lane * wpl + k;
+          if (wd < words) lane_cnt += __popc(bits[wd]);
+        }
+        cnt = warp_sum(lane_cnt);
       }
     }
-    const int lane_cnt = cnt;
-    cnt = warp_sum(cnt);
     if (lane == 0) f.wcnt[w] = cnt;
     __syncthreads();
     int64_t before = 0, total = 0;
@@ -133,10 +195,20 @@ __device__ int64_t warp_chunks_accumulate(const FineSmem& f, int nch, int shift,
       total += c;
     }
     if (ch < nch && cnt > 0) {
-      if (NUMERIC) {
+      const int64_t cb = col_base + ((int64_t)ch << shift);
+      if (sort_e > 0) {
+        if (NUMERIC) {
+          int32_t* oc = out_col + outp + before;
+          double* ov = out_val + outp + before;
+          const int32_t add = (int32_t)cb;
+          if (sort_e == 1) fine_sort_emit<1>(key, n, svals, skeys, add, oc, ov);
+          else if (sort_e == 2) fine_sort_emit<2>(key, n, svals, skeys, add, oc, ov);
+          else if (sort_e == 4) fine_sort_emit<4>(key, n, svals, skeys, add, oc, ov);
+          else fine_sort_emit<8>(key, n, svals, skeys, add, oc, ov);
+        }
+      } else if (NUMERIC) {
         const int inc = warp_inclusive_scan(lane_cnt);
         int64_t o = outp + before + inc - lane_cnt;
-        const int64_t cb = col_base + ((int64_t)ch << shift);
         for (int k = 0; k < wpl; ++k) {
           const int wd = lane * wpl + k;
           if (wd >= words) break;

@@ -32,7 +32,6 @@ constexpr int SORT_MAX = 256;        // largest warp sort-row capacity
 constexpr int SORT_BLOCK_MAX = 1024; // largest block sort-row capacity
 constexpr int DENSE_NT = 256;        // threads of the dense/fine block kernels
 constexpr int FINE_MAX_CHUNKS = 4096;  // fine chunks one block can bookkeep in smem
-constexpr int GROUP_SORT_CAP = 1024; // block sort capacity for merged fine chunks
 
 // Parameters a kernel needs to categorise a row (Section 3.1).
 struct CatParams {
@@ -148,7 +147,7 @@ struct FineArgs {
 };
 cudaError_t launch_fine_rows(bool numeric, const FineArgs& a, int grid, cudaStream_t s);
 // Resident blocks per SM of the fine-row kernel for a phase and chunk shift.
-int fine_rows_blocks_per_sm(bool numeric, int shift);
+int fine_rows_blocks_per_sm(bool numeric, int shift, bool hybrid);
 
 // Coarse level (Algorithm 4) for one batch of coarse rows.
 struct CoarseArgs {

@@ -68,8 +68,10 @@ cudaError_t launch_dense_rows(bool numeric, const DenseArgs& a, int num_sms, cud
 //   reorder:     products written to the block's staging slab at
 //                offset[chunk] + running count; columns are kept relative to
 //                the row's first chunk (chunk << shift | column in chunk)
-//   accumulate:  warp-private dense accumulators, one chunk per warp
-//                (warp_chunks_accumulate), chunks emitted in column order.
+//   accumulate:  one chunk per warp, by the hybrid of Section 3.4: a warp
+//                sort for chunks below the threshold, a warp-private dense
+//                accumulator otherwise (warp_chunks_accumulate); chunks are
+//                emitted in column order.
 // Symbolic phase: a row dense enough for one block bitmap over its whole
 // column range (range <= 2^19, range / 32 <= 4 * P) is counted directly from
 // A and B without a reorder; other rows take the chunked path with bitmaps
@@ -77,7 +79,7 @@ cudaError_t launch_dense_rows(bool numeric, const DenseArgs& a, int num_sms, cud
 template <bool NUMERIC>
 __global__ void __launch_bounds__(NT) k_fine_rows(FineArgs a) {
   extern __shared__ __align__(16) unsigned char fsm[];
-  const FineSmem f = fine_carve(fsm, NUMERIC, a.shift);
+  const FineSmem f = fine_carve(fsm, NUMERIC, a.shift, a.dense_chunk_threshold > 1);
   __shared__ TileSmem<NT> ts;
   __shared__ int64_t s_next;
   int32_t* const slab_col = a.stage_col ? a.stage_col + (int64_t)blockIdx.x * a.slab_elems : nullptr;
@@ -148,14 +150,14 @@ __global__ void __launch_bounds__(NT) k_fine_rows(FineArgs a) {
     int32_t* oc = NUMERIC ? a.c_col + a.c_rp[row] : nullptr;
     double* ov = NUMERIC ? a.c_val + a.c_rp[row] : nullptr;
     const int64_t count = warp_chunks_accumulate<NUMERIC>(f, nch, a.shift, slab_col, slab_val,
-                                                          col_base, oc, ov);
+                                                          col_base, oc, ov, a.dense_chunk_threshold);
     if (!NUMERIC && threadIdx.x == 0) a.out_cnt[row] = count;
     __syncthreads();
   }
 }
 
-int fine_rows_blocks_per_sm(bool numeric, int shift) {
-  const size_t smem = fine_smem_bytes(numeric, shift);
+int fine_rows_blocks_per_sm(bool numeric, int shift, bool hybrid) {
+  const size_t smem = fine_smem_bytes(numeric, shift, hybrid);
   int n = 0;
   cudaError_t e;
   if (numeric) {
@@ -174,7 +176,7 @@ int fine_rows_blocks_per_sm(bool numeric, int shift) {
 
 cudaError_t launch_fine_rows(bool numeric, const FineArgs& a, int grid, cudaStream_t s) {
   if (a.n_rows == 0) return cudaSuccess;
-  const size_t smem = fine_smem_bytes(numeric, a.shift);
+  const size_t smem = fine_smem_bytes(numeric, a.shift, a.dense_chunk_threshold > 1);
   int64_t blocks = grid;
   if (blocks > a.n_rows) blocks = a.n_rows;
   if (blocks < 1) blocks = 1;
@@ -192,6 +194,8 @@ cudaError_t launch_fine_rows(bool numeric, const FineArgs& a, int grid, cudaStre
   return cudaGetLastError();
 }
 
-size_t fine_smem_for(bool numeric, int shift) { return fine_smem_bytes(numeric, shift); }
+size_t fine_smem_for(bool numeric, int shift, bool hybrid) {
+  return fine_smem_bytes(numeric, shift, hybrid);
+}
 
 }  // namespace magnus

@@ -16,7 +16,7 @@ using namespace magnus;
 
 namespace magnus {
 uint64_t launches_total();
-size_t fine_smem_for(bool numeric, int shift);
+size_t fine_smem_for(bool numeric, int shift, bool hybrid);
 }
 
 static thread_local std::string g_cuda_err;
@@ -384,8 +384,13 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
   if (sc > 31) sc = 31;
   pl->shift_coarse = sc;
   pl->n_chunks_coarse = (int)((m_c + ((int64_t)1 << sc) - 1) >> sc);
-  pl->dthr = P.dense_chunk_threshold > 0 ? P.dense_chunk_threshold : 256;
-  if (pl->dthr > GROUP_SORT_CAP) pl->dthr = GROUP_SORT_CAP;
+  // fine-level hybrid (Section 3.4): chunks below dthr products sort in a
+  // warp (at most 256), the others use a warp's dense accumulator.  The
+  // paper's CPU threshold is 256; on the GPU a warp's dense accumulator
+  // (1,024 FP64 columns in shared memory) beats the warp sort down to about
+  // 16 products per chunk, and the sort's staging costs occupancy, so the
+  // automatic value is 1 (dense only; the autotuner tries the hybrid).
+  pl->dthr = P.dense_chunk_threshold > 0 ? std::min(P.dense_chunk_threshold, 257) : 1;
   for (int b = BIN_SORT32; b <= BIN_SORT1024; ++b) {
     const int sb = 4 + b;  // log2 of the bin capacity: 5, 6, 7, 8, 9, 10
     pl->key32[b] = (pl->col_bits + sb <= 32) ? 1 : 0;
@@ -428,8 +433,8 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
   // A fine row is staged whole in its block's slab; the slabs of all resident
   // blocks share the staging budget.  Rows with more products than a slab
   // are split across blocks by the coarse level instead.
-  pl->fine_grid_num = fine_rows_blocks_per_sm(true, pl->shift_fine) * pl->num_sms;
-  pl->fine_grid_sym = fine_rows_blocks_per_sm(false, pl->shift_fine_sym) * pl->num_sms;
+  pl->fine_grid_num = fine_rows_blocks_per_sm(true, pl->shift_fine, pl->dthr > 1) * pl->num_sms;
+  pl->fine_grid_sym = fine_rows_blocks_per_sm(false, pl->shift_fine_sym, pl->dthr > 1) * pl->num_sms;
   pl->fine_slab = std::min<int64_t>((int64_t)1 << 20,
                                     pl->scratch_cap / (12 * (int64_t)pl->fine_grid_num));
   if (pl->fine_slab < 256) pl->fine_slab = 256;

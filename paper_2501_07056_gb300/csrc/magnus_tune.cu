@@ -205,7 +205,7 @@ int magnus_autotune(const magnus_csr_t* A, const magnus_csr_t* B, const magnus_p
       {&magnus_params_t::wide_sort_max, {-1, 256, 512, 1024}, p0.force_category < 0},
       {&magnus_params_t::chunk_len_coarse_log2, {11, 12, 13}, has_coarse},
       {&magnus_params_t::chunk_len_fine_log2, {7, 8, 9, 10}, has_fine || has_coarse},
-      {&magnus_params_t::dense_chunk_threshold, {32, 128, 512}, has_fine},
+      {&magnus_params_t::dense_chunk_threshold, {1, 32, 128, 257}, has_fine || has_coarse},
   };
   for (const Dim& d : dims) {
     if (st != MAGNUS_OK || !d.active) continue;

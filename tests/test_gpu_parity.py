@@ -120,7 +120,7 @@ def test_rmat_small(force):
     assert_parity(got, A, A)
 
 
-@pytest.mark.parametrize("dthr", [1, 8, 1024])
+@pytest.mark.parametrize("dthr", [1, 8, 65, 200, 1024])
 @pytest.mark.parametrize("force", [FINE, COARSE])
 def test_hybrid_threshold_extremes(dthr, force):
     A = inputs.rmat(12, 16, seed=1)
