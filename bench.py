@@ -75,6 +75,7 @@ WORKLOADS = {
                    "generator, drawn on the device), FP64 U(-1,1), seed 0",
 }
 CPU_SAMPLE_PRODUCTS = 1 << 29   # cpu_baseline: about 2-15 s of oracle time
+E2E_BLOCKS = 4                  # e2e: row blocks whose results are copied back while the next compute
 REF_STEP_PRODUCTS = 1 << 27     # reference arm: one step
 PROFILE_DIR = os.path.join(ROOT, "profiles")
 
@@ -87,6 +88,8 @@ def parse_args(argv=None):
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="uniform2^24", choices=sorted(WORKLOADS))
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--e2e-blocks", type=int, default=E2E_BLOCKS,
+                   help="e2e: row blocks whose results are copied back while the next compute")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--force-category", type=int, default=-1)
     p.add_argument("--sort-threshold", type=int, default=0)
@@ -772,8 +775,9 @@ def run_ablation(args, dist):
 
 def run_e2e(args, dist, A, dev, params, n_inter, nnz_c):
     """Same metric through the public API with host buffers: every step
-    copies A from pinned host memory to the device, computes C and copies C
-    (row_ptr, col, val) back to pinned host memory."""
+    copies A and B from pinned host memory to the device, computes C in row
+    blocks (magnus.spgemm_host) and copies each block of C (row_ptr, col,
+    val) back to pinned host memory while the next blocks compute."""
     import torch
 
     from paper_2501_07056_gb300 import magnus
@@ -787,13 +791,12 @@ def run_e2e(args, dist, A, dev, params, n_inter, nnz_c):
     h2d = h_rp.numel() * 8 + h_col.numel() * 4 + h_val.numel() * 8
     d2h = o_rp.numel() * 8 + o_col.numel() * 4 + o_val.numel() * 8
 
+    pinned = ((h_rp, h_col, h_val), (h_rp, h_col, h_val))
+
     def step():
-        d = magnus.DeviceCSR(A.n_rows, A.n_cols, h_rp.to(dev, non_blocking=True),
-                             h_col.to(dev, non_blocking=True), h_val.to(dev, non_blocking=True))
-        C = magnus.spgemm(d, d, params, stream)
-        o_rp.copy_(C.row_ptr, non_blocking=True)
-        o_col.copy_(C.col, non_blocking=True)
-        o_val.copy_(C.val, non_blocking=True)
+        # C = A * A: A is copied once and serves as both operands
+        magnus.spgemm_host(A, A, params, blocks=args.e2e_blocks, device=dev, out=(o_rp, o_col, o_val),
+                           pinned=pinned)
         torch.cuda.synchronize()
 
     for _ in range(max(1, args.warmup)):
@@ -810,6 +813,7 @@ def run_e2e(args, dist, A, dev, params, n_inter, nnz_c):
     dt_max = dist.max(dt)
     units = dist.sum(2.0 * n_inter * steps)
     return {"value": units / dt_max / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
+            "row_blocks": args.e2e_blocks,
             "d2h_bytes_per_step": d2h, "steps": steps, "ms_per_step": 1e3 * dt_max / steps}
 
 

@@ -441,6 +441,79 @@ class BatchPlan:
             pass
 
 
+def spgemm_host(A, B, params: Params | None = None, blocks: int = 4, device="cuda",
+                out=None, pinned=None):
+    """C = A * B for host CSR operands with a host result, pipelined: A and B
+    are copied to the device, A's rows are cut into ``blocks`` row blocks
+    (balanced by nonzeros), each planned and computed on its own stream, and
+    each block's rows of C are copied back while the next blocks compute.
+    ``pinned``: optional (A, B) pinned host copies (torch tensors
+    (row_ptr, col, val)) to copy from; ``out``: optional pinned host tensors
+    (row_ptr, col, val) large enough for C (else allocated).  Returns
+    (row_ptr, col, val) host tensors (views of ``out`` when given)."""
+    import numpy as np
+    import torch
+    dev = torch.device(device)
+    if pinned is None:
+        pa = tuple(torch.from_numpy(x).pin_memory() for x in (A.row_ptr, A.col, A.val))
+        pinned = (pa, pa if B is A else
+                  tuple(torch.from_numpy(x).pin_memory() for x in (B.row_ptr, B.col, B.val)))
+    main = torch.cuda.current_stream(dev)
+    (arp, acol, aval), (brp, bcol, bval) = pinned
+    dA = DeviceCSR(A.n_rows, A.n_cols, arp.to(dev, non_blocking=True),
+                   acol.to(dev, non_blocking=True), aval.to(dev, non_blocking=True))
+    if B is A:  # C = A * A: one copy serves both operands
+        dB = dA
+    else:
+        dB = DeviceCSR(B.n_rows, B.n_cols, brp.to(dev, non_blocking=True),
+                       bcol.to(dev, non_blocking=True), bval.to(dev, non_blocking=True))
+    up = torch.cuda.Event()
+    up.record(main)
+    nb = max(1, min(blocks, A.n_rows))
+    targets = np.linspace(0, A.nnz, nb + 1)
+    cuts = np.unique(np.concatenate(([0], np.searchsorted(A.row_ptr, targets[1:-1]), [A.n_rows])))
+    streams = [torch.cuda.Stream(dev) for _ in range(len(cuts) - 1)]
+    parts = []
+    base = 0
+
+    def copy_back(part, o_rp, o_col, o_val):
+        r0, r1, nnz, plan, col, val, s, off = part
+        with torch.cuda.stream(s):
+            # the block's row pointers, shifted by the entries before it
+            o_rp[r0:r1].copy_(plan.c_row_ptr[:r1 - r0] + off, non_blocking=True)
+            o_col[off:off + nnz].copy_(col, non_blocking=True)
+            o_val[off:off + nnz].copy_(val, non_blocking=True)
+
+    for k, s in enumerate(streams):
+        r0, r1 = int(cuts[k]), int(cuts[k + 1])
+        z0, z1 = int(A.row_ptr[r0]), int(A.row_ptr[r1])
+        s.wait_event(up)
+        with torch.cuda.stream(s):
+            Ak = DeviceCSR(r1 - r0, A.n_cols, dA.row_ptr[r0:r1 + 1] - z0, dA.col[z0:z1],
+                           dA.val[z0:z1])
+            plan = Plan(Ak, dB, params, s)
+            nnz = plan.symbolic()
+            col, val = plan.numeric()
+        part = (r0, r1, nnz, plan, col, val, s, base)
+        base += nnz
+        parts.append(part)
+        if out is not None:  # copy this block back while the next ones compute
+            copy_back(part, *out)
+    total = base
+    if out is None:
+        out = (torch.empty(A.n_rows + 1, dtype=torch.int64).pin_memory(),
+               torch.empty(max(total, 1), dtype=torch.int32).pin_memory(),
+               torch.empty(max(total, 1), dtype=torch.float64).pin_memory())
+        for part in parts:
+            copy_back(part, *out)
+    o_rp, o_col, o_val = out
+    for part in parts:
+        part[6].synchronize()
+        part[3].free()
+    o_rp[A.n_rows] = total
+    return o_rp, o_col[:total], o_val[:total]
+
+
 def spgemm(A: DeviceCSR, B: DeviceCSR, params: Params | None = None, stream=None) -> DeviceCSR:
     """C = A * B on the GPU (plan, symbolic, allocate, numeric)."""
     plan = Plan(A, B, params, stream)

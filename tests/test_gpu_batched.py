@@ -173,3 +173,30 @@ def test_batched_device_drawn_workload_sampled():
         B = inputs.ragged_ctr(n, n, 2, 32, 0, 2 * i + 2)
         _check_product(bp, i, A, B)
     bp.free()
+
+
+@pytest.mark.parametrize("blocks", [1, 3, 8])
+def test_spgemm_host_pipelined(blocks):
+    """Host operands and host result, computed in row blocks on several
+    streams with the copies back overlapping the next blocks."""
+    import torch
+    from paper_2501_07056_gb300 import magnus
+    A = inputs.ragged(5000, 3000, 0, 30, seed=8, matrix_id=1)
+    B = inputs.ragged(3000, 9000, 0, 30, seed=8, matrix_id=2)
+    ref = oracle.spgemm(A, B)
+    for out in (None, "pre"):
+        o = None
+        if out == "pre":
+            n = int(ref.row_ptr[-1])
+            o = (torch.empty(A.n_rows + 1, dtype=torch.int64).pin_memory(),
+                 torch.empty(n + 5, dtype=torch.int32).pin_memory(),
+                 torch.empty(n + 5, dtype=torch.float64).pin_memory())
+        rp, col, val = magnus.spgemm_host(A, B, blocks=blocks, out=o)
+        assert np.array_equal(rp.numpy(), ref.row_ptr)
+        assert np.array_equal(col.numpy(), ref.col)
+        assert values_close(val.numpy(), ref.val, ref.abs).all()
+    # C = A * A with one copy of A
+    S = inputs.uniform(4096, 4096, 8, seed=0)
+    rp, col, val = magnus.spgemm_host(S, S, blocks=blocks)
+    refs = oracle.spgemm(S, S)
+    assert np.array_equal(rp.numpy(), refs.row_ptr) and np.array_equal(col.numpy(), refs.col)
