@@ -159,27 +159,6 @@ __device__ __forceinline__ T group_sum(T x) {
   return x;
 }
 
-// Block bitonic sort of n_pow2 keys in shared memory (n_pow2 a power of two,
-// NT threads).  Ascending.  Contains __syncthreads.
-template <int NT, typename K>
-__device__ __forceinline__ void block_bitonic_sort(K* s, int n_pow2) {
-  for (int size = 2; size <= n_pow2; size <<= 1) {
-    for (int j = size >> 1; j > 0; j >>= 1) {
-      for (int t = threadIdx.x; t < (n_pow2 >> 1); t += NT) {
-        const int lo = ((t & ~(j - 1)) << 1) | (t & (j - 1));
-        const int hi = lo + j;
-        const bool asc = (lo & size) == 0;
-        K a = s[lo], b = s[hi];
-        if (asc ? (b < a) : (a < b)) {
-          s[lo] = b;
-          s[hi] = a;
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
-
 __device__ __forceinline__ int upper_bound_i64(const int64_t* a, int n, int64_t x) {
   int lo = 0, hi = n;
   while (lo < hi) {

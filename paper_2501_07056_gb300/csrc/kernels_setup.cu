@@ -295,7 +295,6 @@ cudaError_t launch_gather_i64(const int64_t* src, const int32_t* idx, int64_t n,
 }
 
 __global__ void k_reduce_stats(const int64_t* P, int64_t n, unsigned long long* out) {
-  __shared__ int64_t ws[33];
   int64_t sum = 0, mx = 0;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -309,7 +308,6 @@ __global__ void k_reduce_stats(const int64_t* P, int64_t n, unsigned long long* 
     atomicAdd(&out[0], (unsigned long long)sum);
     atomicMax(&out[1], (unsigned long long)mx);
   }
-  (void)ws;
 }
 
 cudaError_t launch_reduce_stats(const int64_t* P, int64_t n, int64_t* out2, cudaStream_t s) {
