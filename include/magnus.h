@@ -153,8 +153,9 @@ typedef struct magnus_plan_s* magnus_plan_t;
  * A->n_cols must equal B->n_rows.  The plan keeps copies of the two
  * descriptors (not of the data): A and B must stay unchanged and alive until
  * magnus_free.  `params` may be NULL (all automatic).  Synchronises `stream`
- * once (category counts are read back).  On success *plan owns device memory
- * released by magnus_free.  On failure *plan is set to NULL. */
+ * (category counts and per-category row lists are read back).  On success
+ * *plan owns device memory released by magnus_free.  On failure *plan is set
+ * to NULL. */
 int magnus_plan(magnus_plan_t* plan, const magnus_csr_t* A, const magnus_csr_t* B,
                 const magnus_params_t* params, void* stream);
 
