@@ -186,6 +186,8 @@ struct CoarseArgs {
   int num_sms;
   int64_t nnz_batch;         // nnz of A over the batch rows
   unsigned long long* big_stats;  // optional [3]: products, C entries, count of large buckets
+  int64_t* saved_offs;       // optional [n_rows * n_chunks + 1]: the batch's bucket offsets,
+                             // written by the symbolic pass, reused by the numeric pass
   cudaEvent_t big_ev0, big_ev1;   // optional: recorded around the large-bucket kernel
 };
 cudaError_t run_coarse_batch(bool numeric, CoarseArgs& a, cudaStream_t s);

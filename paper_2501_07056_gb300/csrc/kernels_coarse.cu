@@ -473,15 +473,24 @@ static cudaError_t coarse_impl(CoarseArgs& a, cudaStream_t s) {
   count_launch();
   CK(cudaGetLastError());
   CK(launch_exclusive_scan_i64(a.item_off, nB, a.scan_tmp, s));
-  CK(cudaMemsetAsync(a.counts, 0, (size_t)(nbk + 1) * sizeof(int64_t), s));
   const unsigned go = (unsigned)a.num_sms * 16;
-  k_coarse_outer<false, false><<<go, nt, 0, s>>>(a.B, a.item_off, nB, a.col_ptr, a.csc_row,
-                                                 a.csc_val, a.shift_coarse, a.n_chunks, a.counts,
-                                                 a.cursor, a.chunk_col, a.chunk_val);
-  count_launch();
-  CK(cudaGetLastError());
-  // 3. row-chained prefix sum
-  CK(launch_exclusive_scan_i64(a.counts, nbk, a.scan_tmp, s));
+  if (NUMERIC && a.saved_offs) {
+    // the symbolic pass over the same batch kept the bucket offsets
+    CK(cudaMemcpyAsync(a.counts, a.saved_offs, (size_t)(nbk + 1) * sizeof(int64_t),
+                       cudaMemcpyDeviceToDevice, s));
+  } else {
+    CK(cudaMemsetAsync(a.counts, 0, (size_t)(nbk + 1) * sizeof(int64_t), s));
+    k_coarse_outer<false, false><<<go, nt, 0, s>>>(a.B, a.item_off, nB, a.col_ptr, a.csc_row,
+                                                   a.csc_val, a.shift_coarse, a.n_chunks,
+                                                   a.counts, a.cursor, a.chunk_col, a.chunk_val);
+    count_launch();
+    CK(cudaGetLastError());
+    // 3. row-chained prefix sum
+    CK(launch_exclusive_scan_i64(a.counts, nbk, a.scan_tmp, s));
+    if (a.saved_offs)
+      CK(cudaMemcpyAsync(a.saved_offs, a.counts, (size_t)(nbk + 1) * sizeof(int64_t),
+                         cudaMemcpyDeviceToDevice, s));
+  }
   // 4. reorder
   CK(cudaMemcpyAsync(a.cursor, a.counts, (size_t)nbk * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
   k_coarse_outer<true, NUMERIC><<<go, nt, 0, s>>>(a.B, a.item_off, nB, a.col_ptr, a.csc_row,

@@ -162,6 +162,8 @@ struct magnus_plan_s {
   int32_t* coarse_rows_d = nullptr;
   int32_t* bucket_cnt = nullptr;
   unsigned long long* big_stats = nullptr;  // [3] of the last numeric call (coarse large buckets)
+  int64_t* coarse_offs = nullptr;  // bucket offsets of every coarse batch (symbolic -> numeric)
+  std::vector<int64_t> coarse_offs_at;  // start of each batch's offsets in coarse_offs
   // sorted slot order of the sort rows (symbolic -> numeric)
   uint8_t* perm = nullptr;
   int64_t perm_off[NUM_BINS + 1] = {0};
@@ -610,6 +612,14 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
     for (size_t i = 0; i < nc; ++i) pl->coarse_nnz[i] = rp[pl->coarse_rows[i] + 1] - rp[pl->coarse_rows[i]];
     MAG_TRY(plan_alloc(pl, &pl->bucket_cnt, nc * (size_t)pl->n_chunks_coarse, s));
     MAG_TRY(plan_alloc(pl, &pl->big_stats, 3, s));
+    // the bucket offsets of each batch, kept from the symbolic pass for the
+    // numeric pass (the outer-product histogram is the same in both)
+    pl->coarse_offs_at.assign(1, 0);
+    for (size_t bi = 0; bi + 1 < pl->coarse_batches.size(); ++bi) {
+      const int64_t rows = pl->coarse_batches[bi + 1] - pl->coarse_batches[bi];
+      pl->coarse_offs_at.push_back(pl->coarse_offs_at.back() + rows * pl->n_chunks_coarse + 1);
+    }
+    MAG_TRY(plan_alloc(pl, &pl->coarse_offs, (size_t)pl->coarse_offs_at.back() + 1, s));
     CUDA_TRY(cudaMemsetAsync(pl->big_stats, 0, 3 * sizeof(unsigned long long), s));
   }
   CUDA_TRY(cudaStreamSynchronize(s));
@@ -810,6 +820,7 @@ static int run_phase(magnus_plan_t pl, bool numeric, int64_t* out_cnt, const int
           staged += pl->coarse_P[i];
         }
         a.nnz_batch = z;
+        a.saved_offs = pl->coarse_offs ? pl->coarse_offs + pl->coarse_offs_at[bi] : nullptr;
         if (pl->timing) {
           a.big_ev0 = pl->big_ev[ph][2 * bi];
           a.big_ev1 = pl->big_ev[ph][2 * bi + 1];
