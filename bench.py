@@ -371,12 +371,65 @@ def cpu_oracle_rate(A, rows, threads, B=None):
     return 2.0 * prods / dt / 1e9, prods, dt
 
 
+def run_reference_products(args, dist):
+    """Reference arm of the batched and served workloads: the CPU oracle on
+    all host cores over a bounded sample of products (regenerated on the host
+    from the counter-based generator), one product after another, in the
+    metric of our arm (GFLOP/s for batched, products/s for served)."""
+    import oracle
+    from paper_2501_07056_gb300 import inputs, serve
+    threads = os.cpu_count() or 1
+    if args.workload == "batched4096":
+        ns = inputs.batched_sizes(args.batch_count, seed=0)
+        probs = [(int(n), 2 * i + 1, 2 * i + 2) for i, n in enumerate(ns)][:16]
+
+        def make(p):
+            n, ia, ib = p
+            return (inputs.ragged_ctr(n, n, 2, 32, 0, ia), inputs.ragged_ctr(n, n, 2, 32, 0, ib))
+        metric, unit = "SpGEMM GFLOP/s", "GFLOP/s"
+    else:
+        descs = inputs.served_stream(args.requests, seed=0)[:4]
+        probs = [(d["k"], d["b_id"]) for d in descs]
+
+        def make(p):
+            k, b_id = p
+            return inputs.stencil27(k), inputs.ragged_ctr(k ** 3, k ** 3, 4, 16, 0, b_id)
+        metric, unit = "served products/s", "products/s"
+    mats = [make(p) for p in probs]
+    flops = sum(2 * int(row_products(A, B).sum()) for A, B in mats)
+    total_t = 0.0
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for A, B in mats:
+            oracle.spgemm(A, B, threads=threads)
+        if step >= args.warmup:
+            total_t += time.perf_counter() - t0
+    per_step = total_t / args.steps
+    value = (flops / per_step / 1e9) if unit == "GFLOP/s" else len(mats) / per_step
+    sample = "the first %d products of the workload, one after another" % len(mats)
+    return {
+        "impl": "reference", "metric": metric, "value": value, "unit": unit,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "products": len(mats)},
+        "cpu_baseline": {"value": value, "unit": unit, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
 def run_reference(args, dist):
     """Reference arm: the CPU oracle as it stands on all host cores, each step
     a bounded row sample of the workload."""
     from paper_2501_07056_gb300 import inputs
     if dist.rank != 0:
         return None
+    if args.workload in ("batched4096", "served"):
+        return run_reference_products(args, dist)
+    if args.workload == "ablation":
+        return {"impl": "reference",
+                "unavailable": "the building-block microbenchmark has no CPU program to compare"}
     threads = os.cpu_count() or 1
     if args.workload.startswith("massive"):
         A, B, rows = massive_host(args.workload, REF_STEP_PRODUCTS)
