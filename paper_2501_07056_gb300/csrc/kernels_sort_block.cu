@@ -254,6 +254,112 @@ __global__ void __launch_bounds__((1 << CAPLOG) / BR) k_sort_rows_block(SortArgs
   }
 }
 
+// Symbolic pass of the SORT512 bin with one warp per row: sixteen keys per
+// lane, sorted by the warp's register network (group_bitonic_sort over 32
+// lanes: swaps in registers below distance 16, shuffles above), so neither
+// shared-memory exchanges nor block barriers are needed.  Segments are found
+// as in the lane-group kernel (head bits at segment starts, prefix popcounts);
+// the distinct columns are counted and the sorted slot order is stored, two
+// bytes per product, for the block numeric replay.
+constexpr int S5_NW = 4;
+
+template <typename K>
+__global__ void __launch_bounds__(S5_NW * 32) k_sort512_symbolic(SortArgs a) {
+  constexpr int CAP = 512, R = 16, SB = 9, HW = CAP / 32;
+  using KT = KeyTraits<K>;
+  __shared__ uint16_t s_off[S5_NW][CAP];  // first slot of each non-empty segment
+  __shared__ int64_t s_bs[S5_NW][CAP];    // B.rowPtr of the segment's B row
+  __shared__ uint32_t s_head[S5_NW][HW];  // bit s: a segment other than the first starts at s
+  const int lane = lane_id(), w = warp_id();
+  const int64_t nwarps = (int64_t)gridDim.x * S5_NW;
+  for (int64_t idx = (int64_t)blockIdx.x * S5_NW + w; idx < a.n_rows; idx += nwarps) {
+    const RowDesc d = a.desc[idx];
+    const int64_t poff = a.perm2_off[idx];
+    if (lane < HW) s_head[w][lane] = 0u;
+    int nseg = 0, P = 0;
+    for (int j0 = 0; j0 < d.na; j0 += 32) {
+      const int j = j0 + lane;
+      int L = 0;
+      int64_t bs = 0;
+      if (j < d.na) {
+        L = a.seg_len[d.as + j];
+        bs = a.seg_bs[d.as + j];
+      }
+      const unsigned nz = __ballot_sync(FULL, L > 0);
+      const int inc = warp_inclusive_scan(L);
+      if (L > 0) {
+        const int g = nseg + __popc(nz & ((1u << lane) - 1u));
+        s_off[w][g] = (uint16_t)(P + inc - L);
+        s_bs[w][g] = bs;
+      }
+      nseg += __popc(nz);
+      P += __shfl_sync(FULL, inc, 31);
+    }
+    __syncwarp();
+    for (int g = 1 + lane; g < nseg; g += 32) {
+      const int off = s_off[w][g];
+      atomicOr(&s_head[w][off >> 5], 1u << (off & 31));
+    }
+    __syncwarp();
+    uint32_t hw[HW];
+    int pw[HW];
+    {
+      int cum = 0;
+#pragma unroll
+      for (int i = 0; i < HW; ++i) {
+        hw[i] = s_head[w][i];
+        pw[i] = cum;
+        cum += __popc(hw[i]);
+      }
+    }
+    // slot s = e*32 + lane; all gathers issued before any is used
+    int32_t cg[R];
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+      const int s = e * 32 + lane;
+      const int g = pw[e] + __popc(hw[e] & ((2u << lane) - 1u));
+      cg[e] = s < P ? __ldg(a.B.col + s_bs[w][g] + (s - s_off[w][g])) : 0;
+    }
+    K key[R];
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+      const int s = e * 32 + lane;
+      key[e] = s < P ? KT::template make<SB>(cg[e], s) : ~K(0);
+    }
+    group_bitonic_sort<R, 32>(key);
+    // sorted position q = lane*R + e
+    const K prev_last = __shfl_up_sync(FULL, key[R - 1], 1);
+    int h = 0;
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+      const int q = lane * R + e;
+      const int32_t c = KT::template col<SB>(key[e]);
+      const int32_t pc = (e == 0) ? ((lane == 0) ? -1 : KT::template col<SB>(prev_last))
+                                  : KT::template col<SB>(key[e - 1]);
+      h += ((q < P) && (q == 0 || c != pc)) ? 1 : 0;
+      if (q < P) a.perm2[poff + q] = (uint16_t)KT::template slot<SB>(key[e]);
+    }
+    const int cnt = warp_sum(h);
+    if (lane == 0) a.out_cnt[d.row] = cnt;
+    __syncwarp();
+  }
+}
+
+template <typename K>
+cudaError_t launch_sort512_symbolic(const SortArgs& a, int num_sms, cudaStream_t s) {
+  int per_sm = 0;
+  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort512_symbolic<K>,
+                                                                  S5_NW * 32, 0);
+  if (err != cudaSuccess) return err;
+  if (per_sm < 1) per_sm = 1;
+  int64_t blocks = (a.n_rows + S5_NW - 1) / S5_NW;
+  const int64_t cap = (int64_t)num_sms * per_sm;
+  if (blocks > cap) blocks = cap;
+  k_sort512_symbolic<K><<<(unsigned)blocks, S5_NW * 32, 0, s>>>(a);
+  count_launch();
+  return cudaGetLastError();
+}
+
 template <int CAPLOG, typename K, bool NUMERIC>
 cudaError_t launch_block(const SortArgs& a, int num_sms, cudaStream_t s) {
   constexpr int NT = (1 << CAPLOG) / BR;
@@ -279,6 +385,9 @@ cudaError_t launch_sort_rows_block(int bin, bool numeric, const SortArgs& a, int
   if (numeric)  // the replay holds no keys
     return big ? launch_block<10, uint32_t, true>(a, num_sms, s)
                : launch_block<9, uint32_t, true>(a, num_sms, s);
+  if (!big)  // rows of at most 512 products: one warp per row
+    return a.key32 ? launch_sort512_symbolic<uint32_t>(a, num_sms, s)
+                   : launch_sort512_symbolic<uint64_t>(a, num_sms, s);
   if (a.key32) {
     return big ? launch_block<10, uint32_t, false>(a, num_sms, s)
                : launch_block<9, uint32_t, false>(a, num_sms, s);
