@@ -344,7 +344,8 @@ def row_products(A, B=None):
 
 def sample_rows(A, max_products, n_blocks=64):
     """Rows of n_blocks evenly spaced equal row blocks holding at most
-    max_products intermediate products (all rows if they fit)."""
+    max_products intermediate products (all rows if they fit; one row per
+    block if even that exceeds the budget)."""
     P = row_products(A)
     if P.sum() <= max_products:
         return np.arange(A.n_rows, dtype=np.int64), int(P.sum())
