@@ -12,9 +12,17 @@ steps.
 Output: one JSON line (rank 0).  ``value`` is whole-job GFLOP/s
 (2 x intermediate products / s, Section 5 definition of n_interProd), ``e2e``
 the same metric through the public API with host buffers (H2D of A and D2H of
-C inside the timed region), ``roofline`` the dominant kernel's algorithmic
-bytes per launch over its measured duration against the measured HBM copy
-bandwidth, ``cpu_baseline`` the CPU oracle on a bounded row sample.
+C inside the timed region, row blocks pipelined by magnus.spgemm_host),
+``roofline`` the dominant kernel's algorithmic bytes per launch over its
+measured duration against the measured HBM copy bandwidth, ``cpu_baseline``
+the CPU oracle on a bounded row sample.
+
+Other workloads (``--workload``): uniform4096 and uniform2^22 (smaller
+uniform), rmat20 / rmat18 / rmat16 (R-MAT, edge factor 16), massive20..30
+(the nonsquare uniform workload of Section 4.3), batched4096 (many
+independent products, batched plans against one call per product), served
+(open-loop request stream, continuous batching against one call per
+product, p50/p99 latency) and ablation (the building-block microbenchmark).
 
 ``--impl reference`` times the CPU oracle instead (the reference arm): each
 step is the oracle on a bounded sample of the same workload on all host cores.
