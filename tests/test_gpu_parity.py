@@ -261,3 +261,22 @@ def test_wide_coarse_chunks_use_fine_level():
     got = run_gpu(A, B, P(force_category=COARSE, chunk_len_coarse_log2=16, chunk_len_fine_log2=8))
     assert_parity(got, A, B)
     assert got["info"]["chunk_len_coarse_log2"] == 16
+
+
+@pytest.mark.parametrize("zero_frac", [0.0, 0.02, 0.3, 1.0])
+def test_coarse_negative_zero_products(zero_frac):
+    # Products equal to -0.0 (A entries -0.0, B positive): a column reached
+    # only by them is still part of C's structure, whichever accumulator the
+    # coarse buckets use (warp sort, dense bitmap, fine level inside), and
+    # its value is a zero.  Planted at several rates, up to every product.
+    A = inputs.rmat(12, 16, seed=2)
+    rng = np.random.default_rng(11)
+    A.val = np.abs(A.val) + 0.25
+    A.val[rng.random(A.nnz) < zero_frac] = -0.0
+    B = inputs.rmat(12, 16, seed=3)
+    B.val = np.abs(B.val) + 0.5
+    for cl in (9, 10, 13):
+        got = run_gpu(A, B, P(force_category=COARSE, chunk_len_coarse_log2=cl))
+        assert_parity(got, A, B)
+        if zero_frac == 1.0:
+            assert np.all(got["val"] == 0.0)
