@@ -5,7 +5,9 @@
 // Each chunk is accumulated by one warp, chosen chunk by chunk:
 //   * fewer than `dthr` products (at most 256): sort accumulator - the
 //     chunk's (column, position) keys are sorted by the warp's bitonic
-//     network and runs of equal columns are merged (Algorithm 2);
+//     network and runs of equal columns are merged (Algorithm 2); runs of
+//     consecutive small chunks are first merged into groups of up to 32
+//     products, one warp sort each;
 //   * otherwise: dense accumulator - each warp owns a private accumulator of
 //     one chunk's columns in shared memory (FP64 values and a bitmap in the
 //     numeric phase, the bitmap alone in the symbolic phase).
@@ -102,18 +104,18 @@ __device__ inline void fine_clear(const FineSmem& f, int shift) {
   __syncthreads();
 }
 
-// Sort accumulator of one chunk of n <= 32*E products: keys (column in the
-// chunk, position in the staging) sorted by the warp; returns the distinct
-// count and leaves the sorted keys in k[0..E).
+// Sort accumulator of one group of n <= 32*E products: keys (column from the
+// group's first chunk on, position in the staging) sorted by the warp;
+// returns the distinct count and leaves the sorted keys in k[0..E).
 template <int E>
 __device__ __forceinline__ int fine_sort_count(uint32_t (&k)[8], const int32_t* __restrict__ cols,
-                                               int n, int cmask) {
+                                               int n, int32_t sub) {
   constexpr int SB = Log2Cap<E>::v;
   uint32_t kk[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int s = e * 32 + lane_id();
-    kk[e] = s < n ? KeyTraits<uint32_t>::template make<SB>(cols[s] & cmask, s) : ~0u;
+    kk[e] = s < n ? KeyTraits<uint32_t>::template make<SB>(cols[s] - sub, s) : ~0u;
   }
   warp_bitonic_sort<E>(kk);
 #pragma unroll
@@ -132,14 +134,64 @@ __device__ __forceinline__ void fine_sort_emit(const uint32_t (&k)[8], int n, co
   warp_merge_emit<E, uint32_t, true>(kk, n, vals, skeys, col_add, out_col, out_val);
 }
 
+// Chunk merging (Section 4.1.1: sort sizes near 32 are the sort
+// accumulator's best): with the hybrid on, consecutive chunks of at most 32
+// products (and below dthr) are combined greedily in column order into
+// groups of at most 32 products, one key per lane of a warp sort.  Empty
+// chunks join the open group.  Writes the first chunk of group g to f.cnt[g]
+// (the reorder cursors are dead once the leading barrier has passed) and
+// returns the number of groups.  Warp 0 walks the chunks 32 at a time with
+// the group state kept identical in all its lanes.  All threads must call.
+__device__ inline int fine_merge_groups(const FineSmem& f, int nch, int dthr) {
+  __syncthreads();
+  if (warp_id() == 0) {
+    const int lane = lane_id();
+    int ng = 0, cur = 0;
+    bool open = false;  // the last group takes more small chunks
+    for (int c0 = 0; c0 < nch; c0 += 32) {
+      const int ch = c0 + lane;
+      const int n = ch < nch ? f.off[ch + 1] - f.off[ch] : 0;
+      const unsigned small = __ballot_sync(FULL, ch < nch && n <= 32 && n < dthr);
+      const unsigned valid = (nch - c0 >= 32) ? FULL : ((1u << (nch - c0)) - 1u);
+      unsigned starts = 0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int nj = __shfl_sync(FULL, n, j);
+        if ((small >> j) & 1u) {
+          if (open && cur + nj <= 32) {
+            cur += nj;
+          } else {
+            starts |= 1u << j;
+            cur = nj;
+            open = true;
+          }
+        } else {
+          starts |= 1u << j;
+          open = false;
+        }
+      }
+      starts &= valid;
+      if ((starts >> lane) & 1u) f.cnt[ng + __popc(starts & ((1u << lane) - 1u))] = ch;
+      ng += __popc(starts);
+    }
+    if (lane == 0) f.wcnt[FNW] = ng;
+  }
+  __syncthreads();
+  return (int)f.wcnt[FNW];
+}
+
 // Accumulates the staged chunks [0, nch): chunk ch holds
 // stage_col/stage_val[off[ch] .. off[ch + 1]), columns relative to col_base
 // (chunk index << shift | column inside the chunk).  Writes the sorted unique
 // entries to out_col/out_val[0..) (numeric) and returns their number.  A
 // chunk with fewer than dthr products (dthr <= FINE_SORT_MAX + 1) takes the
-// sort accumulator, the others the dense one.  All threads must call; the
-// warp accumulators must be clean on entry and are clean on exit.
-template <bool NUMERIC>
+// sort accumulator, the others the dense one; with dthr > 1 the small chunks
+// are first merged into groups (fine_merge_groups) and each warp takes a
+// group.  HYBRID = false compiles the dense accumulator alone (dthr <= 1),
+// which keeps the sort path's registers out of the dense-only kernels.  All
+// threads must call; the warp accumulators must be clean on entry and are
+// clean on exit.
+template <bool NUMERIC, bool HYBRID>
 __device__ int64_t warp_chunks_accumulate(const FineSmem& f, int nch, int shift,
                                           const int32_t* __restrict__ stage_col,
                                           const double* __restrict__ stage_val,
@@ -153,25 +205,34 @@ __device__ int64_t warp_chunks_accumulate(const FineSmem& f, int nch, int shift,
   double* svals = NUMERIC ? f.svals + (size_t)w * FINE_SORT_MAX : nullptr;
   uint32_t* skeys = NUMERIC ? f.skeys + (size_t)w * FINE_SORT_MAX : nullptr;
   const int wpl = (words + 31) / 32;  // bitmap words per lane, in column order
+  const bool sorting = HYBRID && dthr > 1 && (!NUMERIC || f.svals != nullptr);
+  const int ngr = sorting ? fine_merge_groups(f, nch, dthr) : nch;
   int64_t outp = 0;
-  for (int r0 = 0; r0 < nch; r0 += FNW) {
-    const int ch = r0 + w;
+  for (int r0 = 0; r0 < ngr; r0 += FNW) {
+    const int g = r0 + w;
+    int g0 = g, g1 = g + 1;
+    if (sorting && g < ngr) {
+      g0 = f.cnt[g];
+      g1 = g + 1 < ngr ? f.cnt[g + 1] : nch;
+    }
     int cnt = 0, lane_cnt = 0, n = 0, sort_e = 0;
     uint32_t key[8];
-    if (ch < nch) {
-      const int p0 = f.off[ch], p1 = f.off[ch + 1];
+    if (g < ngr) {
+      const int p0 = f.off[g0], p1 = f.off[g1];
       n = p1 - p0;
-      if (n > 0 && n < dthr && n <= FINE_SORT_MAX && (!NUMERIC || f.svals != nullptr)) {
-        // sort accumulator (warp-uniform branch: n is the same in all lanes)
+      if (n > 0 && sorting && (g1 - g0 > 1 || (n < dthr && n <= FINE_SORT_MAX))) {
+        // sort accumulator (warp-uniform branch: n is the same in all lanes);
+        // a merged group holds at most 32 products
         if (NUMERIC)
           for (int s = lane; s < n; s += 32) svals[s] = stage_val[p0 + s];
         sort_e = n <= 32 ? 1 : n <= 64 ? 2 : n <= 128 ? 4 : 8;
         const int32_t* cc = stage_col + p0;
-        if (sort_e == 1) cnt = fine_sort_count<1>(key, cc, n, cl - 1);
-        else if (sort_e == 2) cnt = fine_sort_count<2>(key, cc, n, cl - 1);
-        else if (sort_e == 4) cnt = fine_sort_count<4>(key, cc, n, cl - 1);
-        else cnt = fine_sort_count<8>(key, cc, n, cl - 1);
-      } else {
+        const int32_t sub = g0 << shift;
+        if (sort_e == 1) cnt = fine_sort_count<1>(key, cc, n, sub);
+        else if (sort_e == 2) cnt = fine_sort_count<2>(key, cc, n, sub);
+        else if (sort_e == 4) cnt = fine_sort_count<4>(key, cc, n, sub);
+        else cnt = fine_sort_count<8>(key, cc, n, sub);
+      } else if (n > 0) {
         for (int p = p0 + lane; p < p1; p += 32) {
           const int idx = stage_col[p] & (cl - 1);
           atomicOr(&bits[idx >> 5], 1u << (idx & 31));
@@ -194,8 +255,8 @@ __device__ int64_t warp_chunks_accumulate(const FineSmem& f, int nch, int shift,
       before += (i < w) ? c : 0;
       total += c;
     }
-    if (ch < nch && cnt > 0) {
-      const int64_t cb = col_base + ((int64_t)ch << shift);
+    if (g < ngr && cnt > 0) {
+      const int64_t cb = col_base + ((int64_t)g0 << shift);
       if (sort_e > 0) {
         if (NUMERIC) {
           int32_t* oc = out_col + outp + before;

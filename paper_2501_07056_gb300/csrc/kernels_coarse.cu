@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(BK_NW * 32)
 // chunk's staged products: histogram and reorder into the second staging
 // buffer by fine chunk, then warp-private dense accumulation.  The fine
 // shift is min(sc, sf) (the launch sizes shared memory with it).
-template <bool NUMERIC>
+template <bool NUMERIC, bool HYBRID>
 __global__ void __launch_bounds__(FNT)
     k_bucket_big(const int64_t* __restrict__ offs, const int32_t* __restrict__ big_list,
                  const int32_t* __restrict__ n_big, const int32_t* __restrict__ chunk_col,
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(FNT)
                  double* __restrict__ c_val, int dthr) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const int shift = sf < sc ? sf : sc;
-  const FineSmem f = fine_carve(fsm, NUMERIC, shift, dthr > 1);
+  const FineSmem f = fine_carve(fsm, NUMERIC, shift, HYBRID);
   __shared__ int64_t ws[FNT / 32 + 1];
   const int nbig = *n_big;
   const int nch = 1 << (sc - shift);
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(FNT)
         f.off[1] = n;
       }
       __syncthreads();
-      cnt = warp_chunks_accumulate<NUMERIC>(f, 1, shift, cc, cv, col_base, oc, ov, dthr);
+      cnt = warp_chunks_accumulate<NUMERIC, HYBRID>(f, 1, shift, cc, cv, col_base, oc, ov, dthr);
     } else {
       // histogram over the fine chunks of the coarse chunk
       for (int i = threadIdx.x; i < nch; i += FNT) f.cnt[i] = 0;
@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(FNT)
         if (NUMERIC) st_stream(&fv[pos], cv[p]);
       }
       __syncthreads();
-      cnt = warp_chunks_accumulate<NUMERIC>(f, nch, shift, fc, fv, col_base, oc, ov, dthr);
+      cnt = warp_chunks_accumulate<NUMERIC, HYBRID>(f, nch, shift, fc, fv, col_base, oc, ov, dthr);
     }
     if (!NUMERIC && threadIdx.x == 0) bucket_cnt[(list_base + t) * nc + c] = (int32_t)cnt;
     __syncthreads();
@@ -533,8 +533,10 @@ static cudaError_t coarse_impl(CoarseArgs& a, cudaStream_t s) {
   } else {
     const size_t smem = fine_smem_bytes(NUMERIC, a.shift_fine < a.shift_coarse ? a.shift_fine : a.shift_coarse,
                                         a.dense_chunk_threshold > 1);
-    CK(cudaFuncSetAttribute(k_bucket_big<NUMERIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_bucket_big<NUMERIC><<<(unsigned)a.num_sms * 2, FNT, smem, s>>>(
+    const bool hybrid = a.dense_chunk_threshold > 1;
+    auto kern = hybrid ? k_bucket_big<NUMERIC, true> : k_bucket_big<NUMERIC, false>;
+    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)a.num_sms * 2, FNT, smem, s>>>(
         a.counts, a.big_list, a.n_big, a.chunk_col, a.chunk_val, a.fine_col, a.fine_val,
         a.shift_coarse, a.shift_fine, a.n_chunks, a.list_base, a.rows,
         a.bucket_cnt, a.bucket_out, a.c_rp, a.c_col, a.c_val, a.dense_chunk_threshold);

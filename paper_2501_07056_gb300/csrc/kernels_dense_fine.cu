@@ -76,10 +76,10 @@ cudaError_t launch_dense_rows(bool numeric, const DenseArgs& a, int num_sms, cud
 // column range (range <= 2^19, range / 32 <= 4 * P) is counted directly from
 // A and B without a reorder; other rows take the chunked path with bitmaps
 // only.
-template <bool NUMERIC>
+template <bool NUMERIC, bool HYBRID>
 __global__ void __launch_bounds__(NT) k_fine_rows(FineArgs a) {
   extern __shared__ __align__(16) unsigned char fsm[];
-  const FineSmem f = fine_carve(fsm, NUMERIC, a.shift, a.dense_chunk_threshold > 1);
+  const FineSmem f = fine_carve(fsm, NUMERIC, a.shift, HYBRID);
   __shared__ TileSmem<NT> ts;
   __shared__ int64_t s_next;
   int32_t* const slab_col = a.stage_col ? a.stage_col + (int64_t)blockIdx.x * a.slab_elems : nullptr;
@@ -149,24 +149,20 @@ __global__ void __launch_bounds__(NT) k_fine_rows(FineArgs a) {
     });
     int32_t* oc = NUMERIC ? a.c_col + a.c_rp[row] : nullptr;
     double* ov = NUMERIC ? a.c_val + a.c_rp[row] : nullptr;
-    const int64_t count = warp_chunks_accumulate<NUMERIC>(f, nch, a.shift, slab_col, slab_val,
+    const int64_t count = warp_chunks_accumulate<NUMERIC, HYBRID>(f, nch, a.shift, slab_col, slab_val,
                                                           col_base, oc, ov, a.dense_chunk_threshold);
     if (!NUMERIC && threadIdx.x == 0) a.out_cnt[row] = count;
     __syncthreads();
   }
 }
 
-int fine_rows_blocks_per_sm(bool numeric, int shift, bool hybrid) {
-  const size_t smem = fine_smem_bytes(numeric, shift, hybrid);
+template <bool NUMERIC, bool HYBRID>
+static int fine_rows_occupancy(size_t smem) {
   int n = 0;
-  cudaError_t e;
-  if (numeric) {
-    e = cudaFuncSetAttribute(k_fine_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fine_rows<true>, NT, smem);
-  } else {
-    e = cudaFuncSetAttribute(k_fine_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fine_rows<false>, NT, smem);
-  }
+  cudaError_t e = cudaFuncSetAttribute(k_fine_rows<NUMERIC, HYBRID>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fine_rows<NUMERIC, HYBRID>, NT, smem);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 1;
@@ -174,22 +170,36 @@ int fine_rows_blocks_per_sm(bool numeric, int shift, bool hybrid) {
   return n < 1 ? 1 : n;
 }
 
+int fine_rows_blocks_per_sm(bool numeric, int shift, bool hybrid) {
+  const size_t smem = fine_smem_bytes(numeric, shift, hybrid);
+  if (numeric) return hybrid ? fine_rows_occupancy<true, true>(smem) : fine_rows_occupancy<true, false>(smem);
+  return hybrid ? fine_rows_occupancy<false, true>(smem) : fine_rows_occupancy<false, false>(smem);
+}
+
+template <bool NUMERIC, bool HYBRID>
+static cudaError_t launch_fine_rows_t(const FineArgs& a, unsigned blocks, size_t smem,
+                                      cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_fine_rows<NUMERIC, HYBRID>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_fine_rows<NUMERIC, HYBRID><<<blocks, NT, smem, s>>>(a);
+  return cudaSuccess;
+}
+
 cudaError_t launch_fine_rows(bool numeric, const FineArgs& a, int grid, cudaStream_t s) {
   if (a.n_rows == 0) return cudaSuccess;
-  const size_t smem = fine_smem_bytes(numeric, a.shift, a.dense_chunk_threshold > 1);
+  const bool hybrid = a.dense_chunk_threshold > 1;
+  const size_t smem = fine_smem_bytes(numeric, a.shift, hybrid);
   int64_t blocks = grid;
   if (blocks > a.n_rows) blocks = a.n_rows;
   if (blocks < 1) blocks = 1;
+  const unsigned b = (unsigned)blocks;
   cudaError_t e;
-  if (numeric) {
-    e = cudaFuncSetAttribute(k_fine_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_fine_rows<true><<<(unsigned)blocks, NT, smem, s>>>(a);
-  } else {
-    e = cudaFuncSetAttribute(k_fine_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_fine_rows<false><<<(unsigned)blocks, NT, smem, s>>>(a);
-  }
+  if (numeric)
+    e = hybrid ? launch_fine_rows_t<true, true>(a, b, smem, s) : launch_fine_rows_t<true, false>(a, b, smem, s);
+  else
+    e = hybrid ? launch_fine_rows_t<false, true>(a, b, smem, s) : launch_fine_rows_t<false, false>(a, b, smem, s);
+  if (e != cudaSuccess) return e;
   count_launch();
   return cudaGetLastError();
 }

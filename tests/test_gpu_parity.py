@@ -280,3 +280,19 @@ def test_coarse_negative_zero_products(zero_frac):
         assert_parity(got, A, B)
         if zero_frac == 1.0:
             assert np.all(got["val"] == 0.0)
+
+
+@pytest.mark.parametrize("dthr", [2, 9, 33, 257])
+@pytest.mark.parametrize("fine_log2", [5, 7])
+@pytest.mark.parametrize("force", [FINE, COARSE])
+def test_chunk_merging_sparse_chunks(dthr, fine_log2, force):
+    # Sparse rows over a wide column range: most fine chunks hold 0-3
+    # products, so long runs of small chunks merge into groups of up to 32
+    # products (one warp sort each), cut by the chunks at or above dthr.
+    # Coarse chunks of 2^15 columns hold several hundred products each and
+    # run the fine level inside.
+    A = inputs.ragged(600, 2000, 10, 40, seed=12, matrix_id=1)
+    B = inputs.ragged(2000, 1 << 16, 5, 40, seed=12, matrix_id=2)
+    got = run_gpu(A, B, P(force_category=force, dense_chunk_threshold=dthr,
+                          chunk_len_fine_log2=fine_log2, chunk_len_coarse_log2=15))
+    assert_parity(got, A, B)
