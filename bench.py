@@ -107,6 +107,8 @@ def parse_args(argv=None):
                    help="log2 of the fine chunk length (0 = planner's choice)")
     p.add_argument("--dthr", type=int, default=0,
                    help="fine-level hybrid threshold (0 = planner's choice; 1 = dense only)")
+    p.add_argument("--chunk-accumulator", type=int, default=0, choices=[0, 1],
+                   help="fine-level chunk accumulator: 0 dense array, 1 hash map")
     p.add_argument("--batch-count", type=int, default=4096,
                    help="batched workload: number of products")
     p.add_argument("--batch-waves", type=int, default=4,
@@ -492,6 +494,7 @@ def run_ours(args, dist):
                                 chunk_len_coarse_log2=args.chunk_coarse,
                                 chunk_len_fine_log2=args.chunk_fine,
                                 dense_chunk_threshold=args.dthr,
+                                chunk_accumulator=args.chunk_accumulator,
                                 l2_fetch_bytes=args.l2_fetch)
     stream = torch.cuda.current_stream()
     tuned = None

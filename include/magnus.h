@@ -126,7 +126,16 @@ typedef struct {
  *                     instead of the fine/coarse levels (GPU rule; the paper
  *                     sends such rows to the reorder levels).  Range 1..1024;
  *                     0 = 1024; -1 = off.
- * reserved            must be 0.                                             */
+ * chunk_accumulator   accumulator of the fine level's non-sort chunks:
+ *                     0 = dense array and bitmap (Algorithm 1); 1 = hash map
+ *                     (the extension of Algorithm 1 named in Section 2.1,
+ *                     storage per Section 3.5's closing remark): a numeric
+ *                     chunk of at most 128 products accumulates in its warp's
+ *                     open-addressing table of 256 columns (linear probing),
+ *                     then the distinct columns are sorted by the warp;
+ *                     larger chunks keep the dense accumulator.  The
+ *                     symbolic phase counts with the bitmap either way (the
+ *                     counts do not depend on the accumulator).  0 or 1.  */
 typedef struct {
   int32_t sort_threshold;
   int32_t force_category;
@@ -138,7 +147,7 @@ typedef struct {
   int32_t l2_fetch_bytes;
   int32_t numeric_graph;
   int32_t wide_sort_max;
-  int32_t reserved;
+  int32_t chunk_accumulator;
 } magnus_params_t;
 
 /* Fill *p with the automatic values.  Returns MAGNUS_INVALID_ARG on NULL. */

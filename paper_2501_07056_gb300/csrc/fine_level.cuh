@@ -30,6 +30,8 @@ constexpr int WARP_ACC_LOG2 = 10;  // numeric: 1024 FP64 columns per warp accumu
 constexpr int WARP_BITS_LOG2 = 13; // symbolic: 8192 columns per warp bitmap
 constexpr int DIRECT_BITS_LOG2 = 19;  // symbolic: block bitmap for a whole row's range
 constexpr int FINE_SORT_MAX = 256;    // largest chunk the warp sort accumulator takes
+constexpr int FINE_HASH_LOG2 = 8;     // slots of a warp's hash table (in the sort staging)
+constexpr int FINE_HASH_MAX = 128;    // largest chunk the hash accumulator takes (load <= 1/2)
 
 struct FineSmem {
   int32_t* cnt;     // [FINE_MAX_CHUNKS]     chunk histogram, then reorder cursor
@@ -123,6 +125,70 @@ __device__ __forceinline__ int fine_sort_count(uint32_t (&k)[8], const int32_t* 
   return warp_merge_emit<E, uint32_t, false>(kk, n, nullptr, nullptr, 0, nullptr, nullptr);
 }
 
+// Hash-map accumulator of one chunk of n <= FINE_HASH_MAX products
+// (Section 2.1's extension of Algorithm 1: the dense array and bitmap become
+// a hash map).  The warp's table has 2^FINE_HASH_LOG2 slots: keys (column in
+// the chunk, EMPTY when free) in hk, FP64 sums in hv; a product claims its
+// column's slot by compare-and-swap (multiplicative hash, linear probing)
+// and adds its value there.  The occupied slots are then compacted to the
+// front of the table (hk[0..d) columns, hv[0..d) sums), so the caller sorts
+// the d distinct columns with the sort accumulator's warp network and emits
+// them with the sums read by position.  The table is cleared on entry; at
+// most half of it fills, so every probe sequence ends within the table.
+// Returns d.
+constexpr uint32_t HASH_EMPTY = 0xffffffffu;
+
+__device__ __forceinline__ int fine_hash_compact(const int32_t* __restrict__ cols,
+                                                 const double* __restrict__ vals, int n,
+                                                 int cmask, uint32_t* hk, double* hv) {
+  constexpr int HT = 1 << FINE_HASH_LOG2;
+  constexpr int PER = HT / 32;  // slots per lane
+  static_assert(HT <= FINE_SORT_MAX && HT % 32 == 0, "the table lives in the sort staging");
+  const int lane = lane_id();
+  for (int i = lane; i < HT; i += 32) {
+    hk[i] = HASH_EMPTY;
+    hv[i] = 0.0;
+  }
+  __syncwarp();
+  for (int s = lane; s < n; s += 32) {
+    const uint32_t c = (uint32_t)(cols[s] & cmask);
+    const double v = vals[s];
+    uint32_t h = (c * 0x9E3779B1u) >> (32 - FINE_HASH_LOG2);
+    for (int probe = 0; probe < HT; ++probe) {
+      const uint32_t prev = atomicCAS(&hk[h], HASH_EMPTY, c);
+      if (prev == HASH_EMPTY || prev == c) {
+        atomicAdd(&hv[h], v);
+        break;
+      }
+      h = (h + 1) & (HT - 1);
+    }
+  }
+  __syncwarp();
+  uint32_t kc[PER];
+  double vc[PER];
+  int occ = 0;
+#pragma unroll
+  for (int e = 0; e < PER; ++e) {
+    kc[e] = hk[lane * PER + e];
+    vc[e] = hv[lane * PER + e];
+    occ += kc[e] != HASH_EMPTY ? 1 : 0;
+  }
+  const int inc = warp_inclusive_scan(occ);
+  const int d = __shfl_sync(FULL, inc, 31);
+  __syncwarp();
+  int idx = inc - occ;
+#pragma unroll
+  for (int e = 0; e < PER; ++e) {
+    if (kc[e] != HASH_EMPTY) {
+      hk[idx] = kc[e];
+      hv[idx] = vc[e];
+      ++idx;
+    }
+  }
+  __syncwarp();
+  return d;
+}
+
 template <int E>
 __device__ __forceinline__ void fine_sort_emit(const uint32_t (&k)[8], int n, const double* vals,
                                                uint32_t* skeys, int32_t col_add,
@@ -187,16 +253,18 @@ __device__ inline int fine_merge_groups(const FineSmem& f, int nch, int dthr) {
 // chunk with fewer than dthr products (dthr <= FINE_SORT_MAX + 1) takes the
 // sort accumulator, the others the dense one; with dthr > 1 the small chunks
 // are first merged into groups (fine_merge_groups) and each warp takes a
-// group.  HYBRID = false compiles the dense accumulator alone (dthr <= 1),
-// which keeps the sort path's registers out of the dense-only kernels.  All
-// threads must call; the warp accumulators must be clean on entry and are
-// clean on exit.
+// group.  With `hash` (numeric), the other chunks of at most FINE_HASH_MAX
+// products take the hash-map accumulator (fine_hash_compact) and larger
+// ones the dense one.  HYBRID = false compiles the dense accumulator alone
+// (dthr <= 1, no hash), which keeps the sort and hash paths' registers out
+// of the dense-only kernels.  All threads must call; the warp accumulators
+// must be clean on entry and are clean on exit.
 template <bool NUMERIC, bool HYBRID>
 __device__ int64_t warp_chunks_accumulate(const FineSmem& f, int nch, int shift,
                                           const int32_t* __restrict__ stage_col,
                                           const double* __restrict__ stage_val,
                                           int64_t col_base, int32_t* __restrict__ out_col,
-                                          double* __restrict__ out_val, int dthr) {
+                                          double* __restrict__ out_val, int dthr, int hash) {
   const int lane = lane_id(), w = warp_id();
   const int cl = 1 << shift;
   const int words = f.words;
@@ -206,6 +274,7 @@ __device__ int64_t warp_chunks_accumulate(const FineSmem& f, int nch, int shift,
   uint32_t* skeys = NUMERIC ? f.skeys + (size_t)w * FINE_SORT_MAX : nullptr;
   const int wpl = (words + 31) / 32;  // bitmap words per lane, in column order
   const bool sorting = HYBRID && dthr > 1 && (!NUMERIC || f.svals != nullptr);
+  const bool hashing = HYBRID && NUMERIC && hash && f.svals != nullptr;
   const int ngr = sorting ? fine_merge_groups(f, nch, dthr) : nch;
   int64_t outp = 0;
   for (int r0 = 0; r0 < ngr; r0 += FNW) {
@@ -232,6 +301,16 @@ __device__ int64_t warp_chunks_accumulate(const FineSmem& f, int nch, int shift,
         else if (sort_e == 2) cnt = fine_sort_count<2>(key, cc, n, sub);
         else if (sort_e == 4) cnt = fine_sort_count<4>(key, cc, n, sub);
         else cnt = fine_sort_count<8>(key, cc, n, sub);
+      } else if (NUMERIC && hashing && n > 0 && n <= FINE_HASH_MAX) {
+        // hash-map accumulator, then the d distinct columns (compacted at
+        // the front of the table) are sorted and emitted like a sort chunk
+        // of d products
+        n = fine_hash_compact(stage_col + p0, stage_val + p0, n, cl - 1, skeys, svals);
+        sort_e = n <= 32 ? 1 : n <= 64 ? 2 : 4;
+        const int32_t* hc = reinterpret_cast<const int32_t*>(skeys);
+        if (sort_e == 1) cnt = fine_sort_count<1>(key, hc, n, 0);
+        else if (sort_e == 2) cnt = fine_sort_count<2>(key, hc, n, 0);
+        else cnt = fine_sort_count<4>(key, hc, n, 0);
       } else if (n > 0) {
         for (int p = p0 + lane; p < p1; p += 32) {
           const int idx = stage_col[p] & (cl - 1);

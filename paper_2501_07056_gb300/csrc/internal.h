@@ -138,6 +138,7 @@ struct FineArgs {
   const int32_t* hi;
   int32_t shift;            // fine chunk shift for this phase
   int32_t dense_chunk_threshold;
+  int32_t hash;             // numeric: hash-map accumulator for chunks <= 128 products
   int32_t* stage_col;
   double* stage_val;
   int64_t* out_cnt;
@@ -159,6 +160,7 @@ struct CoarseArgs {
   int32_t n_chunks;          // coarse chunks (m_C >> shift_coarse, rounded up)
   int32_t shift_fine;        // fine chunk shift inside a coarse chunk
   int32_t dense_chunk_threshold;
+  int32_t hash;               // numeric: hash-map accumulator for fine chunks <= 128 products
   // scratch (device)
   int32_t* col_cnt;          // n_B + 1   (A^CSC column counts / pointers)
   int64_t* col_ptr;          // n_B + 1

@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(FNT)
                  int64_t list_base, const int32_t* __restrict__ rows,
                  int32_t* __restrict__ bucket_cnt, const int64_t* __restrict__ bucket_out,
                  const int64_t* __restrict__ c_rp, int32_t* __restrict__ c_col,
-                 double* __restrict__ c_val, int dthr) {
+                 double* __restrict__ c_val, int dthr, int hash) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const int shift = sf < sc ? sf : sc;
   const FineSmem f = fine_carve(fsm, NUMERIC, shift, HYBRID);
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(FNT)
         f.off[1] = n;
       }
       __syncthreads();
-      cnt = warp_chunks_accumulate<NUMERIC, HYBRID>(f, 1, shift, cc, cv, col_base, oc, ov, dthr);
+      cnt = warp_chunks_accumulate<NUMERIC, HYBRID>(f, 1, shift, cc, cv, col_base, oc, ov, dthr, hash);
     } else {
       // histogram over the fine chunks of the coarse chunk
       for (int i = threadIdx.x; i < nch; i += FNT) f.cnt[i] = 0;
@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(FNT)
         if (NUMERIC) st_stream(&fv[pos], cv[p]);
       }
       __syncthreads();
-      cnt = warp_chunks_accumulate<NUMERIC, HYBRID>(f, nch, shift, fc, fv, col_base, oc, ov, dthr);
+      cnt = warp_chunks_accumulate<NUMERIC, HYBRID>(f, nch, shift, fc, fv, col_base, oc, ov, dthr, hash);
     }
     if (!NUMERIC && threadIdx.x == 0) bucket_cnt[(list_base + t) * nc + c] = (int32_t)cnt;
     __syncthreads();
@@ -531,15 +531,16 @@ static cudaError_t coarse_impl(CoarseArgs& a, cudaStream_t s) {
         a.counts, a.big_list, a.n_big, a.chunk_col, a.chunk_val, a.shift_coarse, a.n_chunks,
         a.list_base, a.rows, a.bucket_cnt, a.bucket_out, a.c_rp, a.c_col, a.c_val);
   } else {
+    // the sort and hash accumulators share the per-warp staging
+    const bool hybrid = a.dense_chunk_threshold > 1 || (NUMERIC && a.hash);
     const size_t smem = fine_smem_bytes(NUMERIC, a.shift_fine < a.shift_coarse ? a.shift_fine : a.shift_coarse,
-                                        a.dense_chunk_threshold > 1);
-    const bool hybrid = a.dense_chunk_threshold > 1;
+                                        hybrid);
     auto kern = hybrid ? k_bucket_big<NUMERIC, true> : k_bucket_big<NUMERIC, false>;
     CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<(unsigned)a.num_sms * 2, FNT, smem, s>>>(
         a.counts, a.big_list, a.n_big, a.chunk_col, a.chunk_val, a.fine_col, a.fine_val,
         a.shift_coarse, a.shift_fine, a.n_chunks, a.list_base, a.rows,
-        a.bucket_cnt, a.bucket_out, a.c_rp, a.c_col, a.c_val, a.dense_chunk_threshold);
+        a.bucket_cnt, a.bucket_out, a.c_rp, a.c_col, a.c_val, a.dense_chunk_threshold, a.hash);
   }
   count_launch();
   CK(cudaGetLastError());

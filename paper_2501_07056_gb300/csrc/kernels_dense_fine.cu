@@ -149,8 +149,8 @@ __global__ void __launch_bounds__(NT) k_fine_rows(FineArgs a) {
     });
     int32_t* oc = NUMERIC ? a.c_col + a.c_rp[row] : nullptr;
     double* ov = NUMERIC ? a.c_val + a.c_rp[row] : nullptr;
-    const int64_t count = warp_chunks_accumulate<NUMERIC, HYBRID>(f, nch, a.shift, slab_col, slab_val,
-                                                          col_base, oc, ov, a.dense_chunk_threshold);
+    const int64_t count = warp_chunks_accumulate<NUMERIC, HYBRID>(
+        f, nch, a.shift, slab_col, slab_val, col_base, oc, ov, a.dense_chunk_threshold, a.hash);
     if (!NUMERIC && threadIdx.x == 0) a.out_cnt[row] = count;
     __syncthreads();
   }
@@ -188,7 +188,8 @@ static cudaError_t launch_fine_rows_t(const FineArgs& a, unsigned blocks, size_t
 
 cudaError_t launch_fine_rows(bool numeric, const FineArgs& a, int grid, cudaStream_t s) {
   if (a.n_rows == 0) return cudaSuccess;
-  const bool hybrid = a.dense_chunk_threshold > 1;
+  // the sort and hash accumulators share the per-warp staging
+  const bool hybrid = a.dense_chunk_threshold > 1 || (numeric && a.hash);
   const size_t smem = fine_smem_bytes(numeric, a.shift, hybrid);
   int64_t blocks = grid;
   if (blocks > a.n_rows) blocks = a.n_rows;

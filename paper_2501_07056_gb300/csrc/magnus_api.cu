@@ -132,6 +132,7 @@ struct magnus_plan_s {
   int shift_coarse = 24;
   int n_chunks_coarse = 1;
   int dthr = 256;
+  int hash = 0;     // numeric fine chunks: hash-map accumulator
   int col_bits = 0;
   int64_t scratch_cap = 0;  // bytes
   // device arrays owned by the plan
@@ -359,7 +360,7 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
   }
   if (P.sort_threshold < 0 || P.sort_threshold > SORT_BLOCK_MAX + 1) return MAGNUS_INVALID_ARG;
   if (P.wide_sort_max < -1 || P.wide_sort_max > SORT_BLOCK_MAX) return MAGNUS_INVALID_ARG;
-  if (P.reserved != 0) return MAGNUS_INVALID_ARG;
+  if (P.chunk_accumulator != 0 && P.chunk_accumulator != 1) return MAGNUS_INVALID_ARG;
   pl->sort_T = P.sort_threshold > 0 ? P.sort_threshold : 256;
   const int64_t m_c = B->n_cols > 0 ? B->n_cols : 1;
   pl->col_bits = ceil_log2_i64(m_c);
@@ -393,6 +394,7 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
   // 16 products per chunk, and the sort's staging costs occupancy, so the
   // automatic value is 1 (dense only; the autotuner tries the hybrid).
   pl->dthr = P.dense_chunk_threshold > 0 ? std::min(P.dense_chunk_threshold, 257) : 1;
+  pl->hash = P.chunk_accumulator;
   for (int b = BIN_SORT32; b <= BIN_SORT1024; ++b) {
     const int sb = 4 + b;  // log2 of the bin capacity: 5, 6, 7, 8, 9, 10
     pl->key32[b] = (pl->col_bits + sb <= 32) ? 1 : 0;
@@ -435,7 +437,8 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
   // A fine row is staged whole in its block's slab; the slabs of all resident
   // blocks share the staging budget.  Rows with more products than a slab
   // are split across blocks by the coarse level instead.
-  pl->fine_grid_num = fine_rows_blocks_per_sm(true, pl->shift_fine, pl->dthr > 1) * pl->num_sms;
+  pl->fine_grid_num =
+      fine_rows_blocks_per_sm(true, pl->shift_fine, pl->dthr > 1 || pl->hash) * pl->num_sms;
   pl->fine_grid_sym = fine_rows_blocks_per_sm(false, pl->shift_fine_sym, pl->dthr > 1) * pl->num_sms;
   pl->fine_slab = std::min<int64_t>((int64_t)1 << 20,
                                     pl->scratch_cap / (12 * (int64_t)pl->fine_grid_num));
@@ -735,6 +738,7 @@ static int run_phase(magnus_plan_t pl, bool numeric, int64_t* out_cnt, const int
     a.hi = pl->hi;
     a.shift = shift;
     a.dense_chunk_threshold = pl->dthr;
+    a.hash = numeric ? pl->hash : 0;
     a.stage_col = scol;
     a.stage_val = sval;
     a.out_cnt = out_cnt;
@@ -768,6 +772,7 @@ static int run_phase(magnus_plan_t pl, bool numeric, int64_t* out_cnt, const int
       a.n_chunks = pl->n_chunks_coarse;
       a.shift_fine = pl->shift_fine;
       a.dense_chunk_threshold = pl->dthr;
+      a.hash = numeric ? pl->hash : 0;
       a.num_sms = pl->num_sms;
       MAG_TRY(scr.get(&a.col_cnt, (size_t)nB + 1));
       MAG_TRY(scr.get(&a.col_ptr, (size_t)nB + 1));
@@ -977,6 +982,7 @@ int magnus_numeric_noalloc(magnus_plan_t pl, const double* a_val, const double* 
     a.hi = pl->hi;
     a.shift = shift;
     a.dense_chunk_threshold = pl->dthr;
+    a.hash = pl->hash;
     a.stage_col = reinterpret_cast<int32_t*>(base);
     a.stage_val = reinterpret_cast<double*>(base + col_bytes);
     a.c_rp = c_row_ptr;

@@ -6,7 +6,8 @@
 // model values are starting points: the search is coordinate descent from the
 // automatic parameters over the sort threshold, the wide-row sort limit, the
 // coarse and fine chunk lengths and the fine-level hybrid threshold, each
-// dimension tried only when the rows it governs exist.  Every candidate
+// dimension tried only when the rows it governs exist; last, the fine
+// level's chunk accumulator (dense array or hash map).  Every candidate
 // computes the same C (parameters never change results beyond FP64 summation
 // order), so C is allocated once.  Results are cached per operand shape.
 #include <algorithm>
@@ -206,6 +207,7 @@ int magnus_autotune(const magnus_csr_t* A, const magnus_csr_t* B, const magnus_p
       {&magnus_params_t::chunk_len_coarse_log2, {11, 12, 13}, has_coarse},
       {&magnus_params_t::chunk_len_fine_log2, {7, 8, 9, 10}, has_fine || has_coarse},
       {&magnus_params_t::dense_chunk_threshold, {1, 32, 128, 257}, has_fine || has_coarse},
+      {&magnus_params_t::chunk_accumulator, {0, 1}, has_fine || has_coarse},
   };
   for (const Dim& d : dims) {
     if (st != MAGNUS_OK || !d.active) continue;

@@ -36,7 +36,8 @@ class Params(ctypes.Structure):
     _fields_ = [("sort_threshold", c_i32), ("force_category", c_i32),
                 ("chunk_len_fine_log2", c_i32), ("chunk_len_coarse_log2", c_i32),
                 ("dense_chunk_threshold", c_i32), ("validate", c_i32),
-                ("max_scratch_bytes", c_i64), ("l2_fetch_bytes", c_i32), ("numeric_graph", c_i32), ("wide_sort_max", c_i32), ("reserved", c_i32)]
+                ("max_scratch_bytes", c_i64), ("l2_fetch_bytes", c_i32), ("numeric_graph", c_i32), ("wide_sort_max", c_i32),
+                ("chunk_accumulator", c_i32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -248,7 +249,7 @@ class DeviceCSR:
 def make_params(sort_threshold=0, force_category=CAT_AUTO, chunk_len_fine_log2=0,
                 chunk_len_coarse_log2=0, dense_chunk_threshold=0, validate=0,
                 max_scratch_bytes=0, l2_fetch_bytes=0, numeric_graph=0,
-                wide_sort_max=0) -> Params:
+                wide_sort_max=0, chunk_accumulator=0) -> Params:
     p = magnus_params_default()
     p.sort_threshold = sort_threshold
     p.force_category = force_category
@@ -260,6 +261,7 @@ def make_params(sort_threshold=0, force_category=CAT_AUTO, chunk_len_fine_log2=0
     p.l2_fetch_bytes = l2_fetch_bytes
     p.numeric_graph = numeric_graph
     p.wide_sort_max = wide_sort_max
+    p.chunk_accumulator = chunk_accumulator
     return p
 
 

@@ -296,3 +296,36 @@ def test_chunk_merging_sparse_chunks(dthr, fine_log2, force):
     got = run_gpu(A, B, P(force_category=force, dense_chunk_threshold=dthr,
                           chunk_len_fine_log2=fine_log2, chunk_len_coarse_log2=15))
     assert_parity(got, A, B)
+
+
+@pytest.mark.parametrize("dthr", [1, 9])
+@pytest.mark.parametrize("force", [FINE, COARSE])
+@pytest.mark.parametrize("inp", ["rmat", "sparse", "dup"])
+def test_hash_chunk_accumulator(inp, force, dthr):
+    # chunk_accumulator = 1: fine chunks of at most 128 products accumulate
+    # in the warp's open-addressing table (linear probing), the distinct
+    # columns are sorted by the warp; larger chunks stay dense, chunks below
+    # dthr sort (merged).  R-MAT (duplicates on hub columns), sparse rows
+    # (chunks of 0-3 products), and every product of a row in a handful of
+    # columns (long probe chains on one slot).
+    if inp == "rmat":
+        A = B = inputs.rmat(12, 16, seed=4)
+        extra = dict(chunk_len_fine_log2=7, chunk_len_coarse_log2=15)
+    elif inp == "sparse":
+        A = inputs.ragged(600, 2000, 10, 40, seed=13, matrix_id=1)
+        B = inputs.ragged(2000, 1 << 16, 5, 40, seed=13, matrix_id=2)
+        extra = dict(chunk_len_fine_log2=8, chunk_len_coarse_log2=15)
+    else:
+        rng = np.random.default_rng(14)
+        n, m = 300, 1 << 15
+        rows = [sorted(rng.choice(n, size=rng.integers(1, 120), replace=False).tolist())
+                for _ in range(n)]
+        A = _csr(n, n, rows)
+        # B rows: a few fixed columns each (every chunk sees heavy duplication)
+        cols = np.sort(rng.choice(m, size=6, replace=False)).tolist()
+        B = _csr(n, m, [cols[: 1 + (i % 6)] for i in range(n)],
+                 np.concatenate([rng.uniform(-1, 1, 1 + (i % 6)) for i in range(n)]))
+        extra = dict(chunk_len_fine_log2=5, chunk_len_coarse_log2=14)
+    p = P(force_category=force, dense_chunk_threshold=dthr, chunk_accumulator=1, **extra)
+    got = run_gpu(A, B, p, same=A is B)
+    assert_parity(got, A, B)
