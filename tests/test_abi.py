@@ -120,3 +120,42 @@ def test_chunk_model_minimises_eq2(lib):
 def test_chunk_model_invalid(lib):
     with pytest.raises(magnus.MagnusError):
         magnus.magnus_chunk_model(0, 1, 1, 1)
+
+
+def _header_structs():
+    """Field lists of the `typedef struct { ... } name;` blocks of magnus.h,
+    as (name, C type, array length)."""
+    text = open(os.path.join(ROOT, "include", "magnus.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct \{(.*?)\}\s*(\w+);", text, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            m = re.match(r"(const )?([\w ]+?)\s*(\*?)\s*(\w+)(\[(\d+)\])?$", decl)
+            assert m, "cannot parse %r in %s" % (decl, name)
+            ctype = "ptr" if m.group(3) else m.group(2).strip()
+            fields.append((m.group(4), ctype, int(m.group(6)) if m.group(6) else 0))
+        out[name] = fields
+    return out
+
+
+@pytest.mark.parametrize("cname,pyname", [
+    ("magnus_csr_t", "CsrDesc"), ("magnus_params_t", "Params"),
+    ("magnus_plan_info_t", "PlanInfo"), ("magnus_tune_report_t", "TuneReport"),
+    ("magnus_microbench_t", "MicrobenchResult"), ("magnus_chunk_model_t", "ChunkModel"),
+])
+def test_binding_structs_match_header(cname, pyname):
+    # The ctypes mirrors of the ABI structs carry the header's fields in the
+    # header's order with the same widths, so a renamed or inserted field in
+    # either place fails here rather than as a shifted value at run time.
+    widths = {"int32_t": ctypes.sizeof(ctypes.c_int32), "int64_t": 8, "float": 4,
+              "double": 8, "ptr": ctypes.sizeof(ctypes.c_void_p)}
+    hdr = _header_structs()[cname]
+    py = getattr(magnus, pyname)._fields_
+    assert [f[0] for f in hdr] == [f[0] for f in py]
+    for (name, ctype, n), (_, pytype) in zip(hdr, py):
+        size = widths[ctype] * (n if n else 1)
+        assert ctypes.sizeof(pytype) == size, name
