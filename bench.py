@@ -506,7 +506,19 @@ def run_ours(args, dist):
                  "params": magnus.params_dict(params)}
         torch.cuda.empty_cache()
 
-    def step(keep):
+    stage = {k: [] for k in magnus.STAGES}
+
+    def retire(keep, record):
+        # The oldest plan's stage events have completed: the newer plan's
+        # setup synchronised the stream after them.  Freeing it (stream
+        # ordered) hands its memory to the next step's plan.
+        old = keep.pop(0)
+        if record:
+            for k, v in old.stage_times().items():
+                stage[k].append(v)
+        old.free()
+
+    def step(keep, record):
         plan = magnus.Plan(dA, dB, params, stream)
         plan.enable_timing(True)
         plan.symbolic()
@@ -515,21 +527,20 @@ def run_ours(args, dist):
         # reuses the memory in stream order for the next step's C
         del c_col, c_val
         keep.append(plan)
+        if len(keep) > 1:
+            retire(keep, record)
         return plan
 
     # warm-up (also gives the sizes)
     keep = []
     for _ in range(args.warmup):
-        plan = step(keep)
+        plan = step(keep, False)
         torch.cuda.synchronize()
-        if len(keep) > 1:
-            keep.pop(0).free()
     info = plan.info()
     nnz_c = info["nnz_c"]
     n_inter = info["n_interprod"]
-    for p in keep:
-        p.free()
-    keep = []
+    while keep:
+        retire(keep, False)
     torch.cuda.synchronize()
 
     clocks = ClockSampler(dev.index).start()
@@ -540,19 +551,15 @@ def run_ours(args, dist):
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        step(keep)
+        step(keep, True)
     ev1.record(stream)
     torch.cuda.synchronize()
     dist.barrier()
     n_launch = magnus.magnus_launch_count() - n_launch0
     clk = clocks.stop()
     ms_local = ev0.elapsed_time(ev1)
-    stage = {k: [] for k in magnus.STAGES}
-    for p in keep:
-        for k, v in p.stage_times().items():
-            stage[k].append(v)
-        p.free()
-    keep = []
+    while keep:
+        retire(keep, True)
     ms_max = dist.max(ms_local)
     total_units = dist.sum(2.0 * n_inter * args.steps)
     value = total_units / (ms_max * 1e-3) / 1e9
