@@ -443,6 +443,22 @@ class BatchPlan:
             pass
 
 
+_BLOCK_STREAMS: dict = {}
+
+
+def _block_streams(dev, n: int):
+    """The row-block streams of spgemm_host, created once per device and
+    reused by later calls: the caching allocator keeps freed blocks per
+    stream, so new streams on every call could not reuse the previous call's
+    memory for C and would allocate (and release) it again."""
+    import torch
+    key = (dev.type, dev.index if dev.index is not None else torch.cuda.current_device())
+    have = _BLOCK_STREAMS.setdefault(key, [])
+    while len(have) < n:
+        have.append(torch.cuda.Stream(dev))
+    return have[:n]
+
+
 def spgemm_host(A, B, params: Params | None = None, blocks: int = 4, device="cuda",
                 out=None, pinned=None):
     """C = A * B for host CSR operands with a host result, pipelined: A and B
@@ -474,7 +490,7 @@ def spgemm_host(A, B, params: Params | None = None, blocks: int = 4, device="cud
     nb = max(1, min(blocks, A.n_rows))
     targets = np.linspace(0, A.nnz, nb + 1)
     cuts = np.unique(np.concatenate(([0], np.searchsorted(A.row_ptr, targets[1:-1]), [A.n_rows])))
-    streams = [torch.cuda.Stream(dev) for _ in range(len(cuts) - 1)]
+    streams = _block_streams(dev, len(cuts) - 1)
     parts = []
     base = 0
 
