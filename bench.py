@@ -547,17 +547,19 @@ def run_ours(args, dist):
     dist.barrier()
     torch.cuda.synchronize()
     n_launch0 = magnus.magnus_launch_count()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
+    # one event per step boundary: the total, and the mean / median / min of
+    # the single steps
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs[0].record(stream)
+    for i in range(args.steps):
         step(keep, True)
-    ev1.record(stream)
+        evs[i + 1].record(stream)
     torch.cuda.synchronize()
     dist.barrier()
     n_launch = magnus.magnus_launch_count() - n_launch0
     clk = clocks.stop()
-    ms_local = ev0.elapsed_time(ev1)
+    ms_local = evs[0].elapsed_time(evs[-1])
+    step_list = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
     while keep:
         retire(keep, True)
     ms_max = dist.max(ms_local)
@@ -596,7 +598,10 @@ def run_ours(args, dist):
         "clocks": clk,
         "gpu_launches": n_launch,
         "detail": {"nnz_c": nnz_c, "autotune": tuned,
-                   "stage_ms": stage_ms, "t_over_t_ideal": (ms_max / args.steps) / t_ideal_ms,
+                   "stage_ms": stage_ms,
+                   "step_ms": {"mean": statistics.mean(step_list),
+                               "median": statistics.median(step_list), "min": min(step_list)},
+                   "t_over_t_ideal": (ms_max / args.steps) / t_ideal_ms,
                    "t_ideal_ms": t_ideal_ms, "rows_per_category": info["rows_per_category"],
                    "sort_threshold": info["sort_threshold"]},
     }
