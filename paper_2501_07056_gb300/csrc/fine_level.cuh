@@ -34,13 +34,15 @@ constexpr int FINE_HASH_LOG2 = 8;     // slots of a warp's hash table (in the so
 constexpr int FINE_HASH_MAX = 128;    // largest chunk the hash accumulator takes (load <= 1/2)
 
 struct FineSmem {
-  int32_t* cnt;     // [FINE_MAX_CHUNKS]     chunk histogram, then reorder cursor
+  int32_t* cnt;     // [FINE_MAX_CHUNKS]     chunk histogram, then reorder cursor, then
+                    //                       first chunk of each merged group
   int32_t* off;     // [FINE_MAX_CHUNKS + 1] chunk offsets in staging
   double* acc;      // [FNW << shift]        warp accumulators (numeric)
   uint32_t* bits;   // [FNW][words]          warp bitmaps
   int words;        // bitmap words per warp
   uint32_t* direct; // symbolic: block bitmap of a whole row (aliases the above)
-  int64_t* wcnt;    // [FNW + 1]             chunk counts of the current round
+  int64_t* wcnt;    // [FNW + 1]             chunk counts of the current round; [FNW]:
+                    //                       number of merged chunk groups
   double* svals;    // [FNW][FINE_SORT_MAX]  sort accumulator: values by position (numeric)
   uint32_t* skeys;  // [FNW][FINE_SORT_MAX]  sort accumulator: sorted keys (numeric)
 };
