@@ -292,7 +292,7 @@ magnus_plan_t magnus_batch_inner_plan(magnus_batch_t batch);
  * that: the runs use 16 evenly spaced row blocks of A holding about
  * sample_products products (a device copy of those rows).
  * A and B need values.  Results are cached per (device, shapes, nnz,
- * sample_products): a repeated call returns the cached set with
+ * sample_products, base parameters): a repeated call returns the cached set with
  * report->from_cache = 1.  The device memory of the trials (one C of the
  * tuned operand and the plans' scratch) is released before returning.
  * Synchronises `stream`.  Status codes as for magnus_plan. */

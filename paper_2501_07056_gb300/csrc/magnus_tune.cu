@@ -9,11 +9,13 @@
 // dimension tried only when the rows it governs exist; last, the fine
 // level's chunk accumulator (dense array or hash map).  Every candidate
 // computes the same C (parameters never change results beyond FP64 summation
-// order), so C is allocated once.  Results are cached per operand shape.
+// order), so C is allocated once.  Results are cached per operand shape and
+// base parameters.
 #include <algorithm>
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
 #include <vector>
 
@@ -35,7 +37,10 @@ namespace {
     if (_s != MAGNUS_OK) return _s; \
   } while (0)
 
-using Key = std::tuple<int, int64_t, int64_t, int64_t, int64_t, int64_t, int64_t, int64_t>;
+// device, operand shapes, sample size and the base parameters (as bytes: a
+// search from other base parameters, e.g. a forced category, is another entry)
+using Key = std::tuple<int, int64_t, int64_t, int64_t, int64_t, int64_t, int64_t, int64_t,
+                       std::string>;
 std::mutex g_tune_mu;
 std::map<Key, magnus_params_t> g_tune_cache;
 
@@ -104,7 +109,9 @@ int magnus_autotune(const magnus_csr_t* A, const magnus_csr_t* B, const magnus_p
   memset(&r, 0, sizeof(r));
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
-  const Key key{dev, A->n_rows, A->n_cols, A->nnz, B->n_rows, B->n_cols, B->nnz, sample_products};
+  const Key key{dev,       A->n_rows, A->n_cols, A->nnz,          B->n_rows,
+                B->n_cols, B->nnz,    sample_products,
+                std::string(reinterpret_cast<const char*>(&p0), sizeof(p0))};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);

@@ -42,3 +42,21 @@ def test_autotune_sampled_rows():
     assert 0 < rep["sampled_rows"] < A.n_rows
     got = run_gpu(A, B, best)
     assert_parity(got, A, B)
+
+
+def test_autotune_cache_keyed_by_base_params():
+    # The same operands tuned from another starting point (a forced
+    # category) are a separate cache entry, and the search keeps the base's
+    # fixed choices.
+    from paper_2501_07056_gb300 import magnus
+    A = inputs.rmat(11, 16, seed=5, matrix_id=1)
+    dA = magnus.DeviceCSR.from_host(A)
+    _, rep = magnus.autotune(dA, dA, max_trials=3)
+    base = magnus.make_params(force_category=3)
+    best, rep2 = magnus.autotune(dA, dA, base, max_trials=3)
+    assert rep2["from_cache"] == 0
+    assert best.force_category == 3
+    got = run_gpu(A, A, best, same=True)
+    assert_parity(got, A, A)
+    _, rep3 = magnus.autotune(dA, dA, base, max_trials=3)
+    assert rep3["from_cache"] == 1
