@@ -44,7 +44,8 @@ enum magnus_status {
   MAGNUS_OK = 0,
   MAGNUS_INVALID_ARG = 1,        /* NULL pointer, negative size, A.n_cols != B.n_rows */
   MAGNUS_UNSORTED_OR_DUP = 2,    /* validate=1 found an unsorted/duplicate/out-of-range column */
-  MAGNUS_INDEX_OVERFLOW = 3,     /* a size does not fit the index types (cols >= 2^31, rows >= 2^31) */
+  MAGNUS_INDEX_OVERFLOW = 3,     /* a size does not fit the index types (cols >= 2^31, rows >= 2^31,
+                                    nnz of B >= 2^40) */
   MAGNUS_OUT_OF_MEMORY = 4,      /* device allocation failed or the request exceeds the memory cap */
   MAGNUS_CUDA_ERROR = 5,         /* a CUDA runtime call failed; see magnus_last_cuda_error() */
   MAGNUS_TIMEOUT = 6,            /* a bounded device-side wait expired (reserved) */

@@ -58,7 +58,7 @@ struct Csr {
 // cudaGetLastError() of the launch.
 cudaError_t launch_validate(const Csr& M, int* d_flag, cudaStream_t s);
 cudaError_t launch_rowinfo(const Csr& A, const Csr& B, CatParams cp, int64_t* P, uint8_t* bin,
-                           int32_t* lo, int32_t* hi, int64_t* seg_bs, int32_t* seg_len,
+                           int32_t* lo, int32_t* hi, uint64_t* seg,
                            cudaStream_t s);
 
 // A range and id of a listed row (16 bytes, one vector load).
@@ -85,13 +85,28 @@ cudaError_t launch_exclusive_scan_i64(int64_t* a, int64_t n, int64_t* tmp, cudaS
 cudaError_t launch_scan_i32_to_i64(const int32_t* in, int64_t n, int64_t* out, int64_t* tmp,
                                    cudaStream_t s);
 
+// Segment table entry of a nonzero of A: the start of the B row it selects
+// (B.rowPtr[A.col[j]], low SEG_BS_BITS bits; B has fewer than 2^40
+// nonzeros, checked by magnus_plan) and the row's length (high bits,
+// saturated at 2^24 - 1: only rows of at most 1,024 products read the table,
+// and their B rows are that short).
+constexpr int SEG_BS_BITS = 40;
+__host__ __device__ __forceinline__ uint64_t seg_pack(int64_t bs, int64_t len) {
+  const int64_t l = len < ((int64_t)1 << (64 - SEG_BS_BITS)) - 1 ? len
+                                                                  : ((int64_t)1 << (64 - SEG_BS_BITS)) - 1;
+  return (uint64_t)bs | ((uint64_t)l << SEG_BS_BITS);
+}
+__host__ __device__ __forceinline__ int64_t seg_start(uint64_t x) {
+  return (int64_t)(x & ((1ull << SEG_BS_BITS) - 1));
+}
+__host__ __device__ __forceinline__ int seg_length(uint64_t x) { return (int)(x >> SEG_BS_BITS); }
+
 // Sort rows (warp per row).  cnt_out: per-row count (symbolic) written at
 // c_row_ptr-like array position row (count stored in out_cnt[row]).
 struct SortArgs {
   Csr A, B;
   const RowDesc* desc;  // descriptors of the bin's rows
-  const int64_t* seg_bs;  // per nonzero of A: B.rowPtr of its B row
-  const int32_t* seg_len; // per nonzero of A: length of its B row
+  const uint64_t* seg;    // per nonzero of A: its B row (seg_pack)
   int64_t n_rows;
   int key32;            // 1: (col << slot_bits | slot) fits 32 bits
   uint8_t* perm;        // sorted slot order, 32*E bytes per listed row

@@ -55,14 +55,13 @@ cudaError_t launch_validate(const Csr& M, int* d_flag, cudaStream_t s) {
 // product (from the first and last column of each referenced B row, which is
 // valid because rows are sorted), and the bin of the row.  V lanes per row.
 // Also writes the segment table: for every nonzero j of A, the start and the
-// length of the B row it selects (seg_bs[j] = B.rowPtr[A.col[j]], seg_len[j] =
-// nnz of that row), so later passes read it as a stream instead of gathering
-// B.rowPtr again.
+// length of the B row it selects (B.rowPtr[A.col[j]] and the row's nnz,
+// packed into one word by seg_pack), so later passes read it as a stream
+// instead of gathering B.rowPtr again.
 template <int V>
 __global__ void k_rowinfo(Csr A, Csr B, CatParams cp, int64_t* __restrict__ P,
                           uint8_t* __restrict__ bin, int32_t* __restrict__ lo_out,
-                          int32_t* __restrict__ hi_out, int64_t* __restrict__ seg_bs,
-                          int32_t* __restrict__ seg_len) {
+                          int32_t* __restrict__ hi_out, uint64_t* __restrict__ seg) {
   const int sub = threadIdx.x & (V - 1);
   const int64_t groups = (int64_t)gridDim.x * (blockDim.x / V);
   const unsigned gmask = (V == 32) ? FULL : (((1u << V) - 1) << ((threadIdx.x & 31) & ~(V - 1)));
@@ -83,12 +82,8 @@ __global__ void k_rowinfo(Csr A, Csr B, CatParams cp, int64_t* __restrict__ P,
       const int64_t b0 = B.rp[c], b1 = B.rp[c + 1];
       const int64_t b2 = two ? B.rp[c2] : 0, b3 = two ? B.rp[c2 + 1] : 0;
       p += (b1 - b0) + (b3 - b2);
-      seg_bs[j] = b0;
-      seg_len[j] = (int32_t)(b1 - b0);
-      if (two) {
-        seg_bs[j2] = b2;
-        seg_len[j2] = (int32_t)(b3 - b2);
-      }
+      seg[j] = seg_pack(b0, b1 - b0);
+      if (two) seg[j2] = seg_pack(b2, b3 - b2);
     }
 #pragma unroll
     for (int d = V / 2; d > 0; d >>= 1) p += __shfl_xor_sync(gmask, p, d, V);
@@ -153,7 +148,7 @@ __global__ void k_rowinfo(Csr A, Csr B, CatParams cp, int64_t* __restrict__ P,
 }
 
 cudaError_t launch_rowinfo(const Csr& A, const Csr& B, CatParams cp, int64_t* P, uint8_t* bin,
-                           int32_t* lo, int32_t* hi, int64_t* seg_bs, int32_t* seg_len,
+                           int32_t* lo, int32_t* hi, uint64_t* seg,
                            cudaStream_t s) {
   if (A.n_rows == 0) return cudaSuccess;
   const double avg = A.n_rows ? (double)A.nnz / (double)A.n_rows : 0.0;
@@ -162,12 +157,12 @@ cudaError_t launch_rowinfo(const Csr& A, const Csr& B, CatParams cp, int64_t* P,
   while (v < 32 && 2 * v < avg) v <<= 1;
   unsigned g = grid_cap(cdiv(A.n_rows * v, nt), 1 << 20);
   switch (v) {
-    case 1: k_rowinfo<1><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg_bs, seg_len); break;
-    case 2: k_rowinfo<2><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg_bs, seg_len); break;
-    case 4: k_rowinfo<4><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg_bs, seg_len); break;
-    case 8: k_rowinfo<8><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg_bs, seg_len); break;
-    case 16: k_rowinfo<16><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg_bs, seg_len); break;
-    default: k_rowinfo<32><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg_bs, seg_len); break;
+    case 1: k_rowinfo<1><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg); break;
+    case 2: k_rowinfo<2><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg); break;
+    case 4: k_rowinfo<4><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg); break;
+    case 8: k_rowinfo<8><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg); break;
+    case 16: k_rowinfo<16><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg); break;
+    default: k_rowinfo<32><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg); break;
   }
   count_launch();
   return cudaGetLastError();

@@ -63,8 +63,9 @@ __global__ void __launch_bounds__(NW * 32) k_sort_rows(SortArgs a) {
     if (base + grp < n) {
       if (NUMERIC) q.crp = a.c_rp[p1.d.row];
       if (l < p1.d.na) {
-        q.bs = a.seg_bs[p1.d.as + l];
-        q.L = a.seg_len[p1.d.as + l];
+        const uint64_t sg = a.seg[p1.d.as + l];
+        q.bs = seg_start(sg);
+        q.L = seg_length(sg);
         if (NUMERIC) q.av = a.A.val[p1.d.as + l];
       }
     }
@@ -91,8 +92,9 @@ __global__ void __launch_bounds__(NW * 32) k_sort_rows(SortArgs a) {
         L = p2.L;
         av = p2.av;
       } else if (j < d.na) {
-        bs = a.seg_bs[d.as + j];
-        L = a.seg_len[d.as + j];
+        const uint64_t sg = a.seg[d.as + j];
+        bs = seg_start(sg);
+        L = seg_length(sg);
         if (NUMERIC) av = a.A.val[d.as + j];
       }
       const unsigned nz = (__ballot_sync(FULL, L > 0) >> gshift) & gbits;

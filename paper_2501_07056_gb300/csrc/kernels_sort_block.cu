@@ -111,8 +111,9 @@ __global__ void __launch_bounds__((1 << CAPLOG) / BR) k_sort_rows_block(SortArgs
       int64_t bs = 0;
       double av = 0.0;
       if (j < d.na) {
-        L = a.seg_len[d.as + j];
-        bs = a.seg_bs[d.as + j];
+        const uint64_t sg = a.seg[d.as + j];
+        L = seg_length(sg);
+        bs = seg_start(sg);
         if (NUMERIC) av = a.A.val[d.as + j];
       }
       const int nz = L > 0 ? 1 : 0;
@@ -282,8 +283,9 @@ __global__ void __launch_bounds__(S5_NW * 32) k_sort512_symbolic(SortArgs a) {
       int L = 0;
       int64_t bs = 0;
       if (j < d.na) {
-        L = a.seg_len[d.as + j];
-        bs = a.seg_bs[d.as + j];
+        const uint64_t sg = a.seg[d.as + j];
+        L = seg_length(sg);
+        bs = seg_start(sg);
       }
       const unsigned nz = __ballot_sync(FULL, L > 0);
       const int inc = warp_inclusive_scan(L);

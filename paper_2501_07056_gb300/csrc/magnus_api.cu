@@ -143,8 +143,7 @@ struct magnus_plan_s {
   int32_t* hi = nullptr;
   int32_t* rows_sorted = nullptr;
   RowDesc* desc = nullptr;       // per listed row (bin order)
-  int64_t* seg_bs = nullptr;     // per nonzero of A
-  int32_t* seg_len = nullptr;
+  uint64_t* seg = nullptr;       // per nonzero of A (seg_pack)
   int64_t bin_off[NUM_BINS + 1] = {0};
   // fine rows (heaviest first), batches as list index ranges
   std::vector<int32_t> fine_rows;
@@ -426,8 +425,7 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
   MAG_TRY(plan_alloc(pl, &pl->hi, n + 1, s));
   MAG_TRY(plan_alloc(pl, &pl->rows_sorted, n + 1, s));
   MAG_TRY(plan_alloc(pl, &pl->desc, n + 1, s));
-  MAG_TRY(plan_alloc(pl, &pl->seg_bs, (size_t)A->nnz + 1, s));
-  MAG_TRY(plan_alloc(pl, &pl->seg_len, (size_t)A->nnz + 1, s));
+  MAG_TRY(plan_alloc(pl, &pl->seg, (size_t)A->nnz + 1, s));
   CatParams cp;
   cp.sort_threshold = pl->sort_T;
   cp.force = P.force_category;
@@ -453,8 +451,7 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
   // products sort in registers (one warp) or in one block instead of taking
   // the coarse level's four passes over their products.
   cp.wide_sort_max = P.wide_sort_max == 0 ? SORT_BLOCK_MAX : (P.wide_sort_max < 0 ? 0 : P.wide_sort_max);
-  CUDA_TRY(launch_rowinfo(pl->A, pl->B, cp, pl->P, pl->bin, pl->lo, pl->hi, pl->seg_bs,
-                          pl->seg_len, s));
+  CUDA_TRY(launch_rowinfo(pl->A, pl->B, cp, pl->P, pl->bin, pl->lo, pl->hi, pl->seg, s));
   int64_t* stats;
   MAG_TRY(plan_alloc(pl, &stats, 2 + NUM_BINS + 1, s));
   CUDA_TRY(launch_reduce_stats(pl->P, n, stats, s));
@@ -637,6 +634,8 @@ int magnus_plan(magnus_plan_t* plan, const magnus_csr_t* A, const magnus_csr_t* 
   MAG_TRY(check_csr(B));
   if (A->n_cols != B->n_rows) return MAGNUS_INVALID_ARG;
   if (A->nnz > 0 && B->n_rows == 0) return MAGNUS_INVALID_ARG;
+  // the segment table keeps B row starts in SEG_BS_BITS bits
+  if (B->nnz >= ((int64_t)1 << SEG_BS_BITS)) return MAGNUS_INDEX_OVERFLOW;
   cudaStream_t s = (cudaStream_t)stream;
   magnus_plan_t pl = new (std::nothrow) magnus_plan_s();
   if (!pl) return MAGNUS_OUT_OF_MEMORY;
@@ -664,8 +663,7 @@ static int run_phase(magnus_plan_t pl, bool numeric, int64_t* out_cnt, const int
       a.A = A;
       a.B = B;
       a.desc = pl->desc + pl->bin_off[b];
-      a.seg_bs = pl->seg_bs;
-      a.seg_len = pl->seg_len;
+      a.seg = pl->seg;
       a.n_rows = pl->bin_off[b + 1] - pl->bin_off[b];
       a.key32 = pl->key32[b];
       a.perm = pl->perm + pl->perm_off[b];
@@ -936,8 +934,7 @@ int magnus_numeric_noalloc(magnus_plan_t pl, const double* a_val, const double* 
     a.A = A;
     a.B = B;
     a.desc = pl->desc + pl->bin_off[b];
-    a.seg_bs = pl->seg_bs;
-    a.seg_len = pl->seg_len;
+    a.seg = pl->seg;
     a.n_rows = pl->bin_off[b + 1] - pl->bin_off[b];
     a.key32 = pl->key32[b];
     a.perm = pl->perm + pl->perm_off[b];

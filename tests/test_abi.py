@@ -79,6 +79,10 @@ def test_plan_rejects_bad_args_without_gpu(lib):
     big = magnus.CsrDesc(4, 1 << 32, 0, 8, 0, 0)
     Bb = magnus.CsrDesc(1 << 32, 5, 0, 8, 0, 0)
     assert lib.magnus_plan(ctypes.byref(h), ctypes.byref(big), ctypes.byref(Bb), None, None) == 3
+    # B row starts are kept in 40 bits of the segment table
+    A40 = magnus.CsrDesc(4, 5, 0, 8, 0, 0)
+    B40 = magnus.CsrDesc(5, 6, 1 << 40, 8, 8, 8)
+    assert lib.magnus_plan(ctypes.byref(h), ctypes.byref(A40), ctypes.byref(B40), None, None) == 3
     assert lib.magnus_numeric(None, None, None, None, None, None, None) == 1
     assert lib.magnus_symbolic(None, None, None, None) == 1
 
