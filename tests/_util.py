@@ -33,3 +33,18 @@ def random_pattern_csr(rng, n_rows, n_cols, density, lo=-1.0, hi=1.0) -> CSR:
     rp = np.zeros(n_rows + 1, np.int64)
     np.cumsum(lengths, out=rp[1:])
     return CSR(n_rows, n_cols, rp, cols.astype(np.int32), d[rows, cols].astype(np.float64))
+
+
+def golden(name: str) -> dict:
+    """The key = value entries of tests/golden/<name> (numbers printed in the
+    paper, each commented with its place there)."""
+    import os
+    out = {}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    for line in open(path):
+        line = line.split("#", 1)[0].strip()
+        if not line:
+            continue
+        key, val = (x.strip() for x in line.split("=", 1))
+        out[key] = float(val) if "." in val else int(val)
+    return out

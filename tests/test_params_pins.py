@@ -5,16 +5,19 @@ import math
 import pytest
 
 from oracle import params as P
+from tests._util import golden
 
 MB = 1 << 20
 S_CF = P.s_chunk_fine(4, 4, 64)   # 4 + 4 + 2*64 = 136 bytes (Section 3.5)
+PRINTED = golden("paper_printed_values.txt")
 
 
 def test_s_chunk_fine_value():
     assert S_CF == 136
 
 
-@pytest.mark.parametrize("l2,expect", [(MB, 1 << 30), (2 * MB, 1 << 32)])
+@pytest.mark.parametrize("l2,expect", [(MB, PRINTED["coarse_crossover_m_c_l2_1mb"]),
+                                        (2 * MB, PRINTED["coarse_crossover_m_c_l2_2mb"])])
 def test_coarse_crossovers_section_4_3(l2, expect):
     # Section 4.3: MAGNUS switches on the coarse level at m_C = 2^30 on SKX
     # (1 MB L2) and at 2^32 on SPR/EMR (2 MB L2), Table 1.  Eq. 5 reproduces
@@ -40,7 +43,7 @@ def test_reorder_breaking_point_section_4_1_2():
     # histogram, prefix-sum and active-line storage (n * s_chunkFine) exceeds
     # the 2 MB L2.
     n_break = (2 * MB) / S_CF
-    assert P.floor_pow2(n_break) == 1 << 13
+    assert P.floor_pow2(n_break) == PRINTED["reorder_breaking_point_chunks"]
     # and the 2^31 * 2^13 = 2^44 column statement that follows it
     assert (1 << 31) * (1 << 13) == 1 << 44
 
@@ -87,3 +90,16 @@ def test_eq6_eq7_two_level():
 
 def test_m_c_ceiled():
     assert P.plan(3 << 20, 2 * MB)["m_c"] == 1 << 22
+
+
+def test_golden_table3_transcription():
+    # The transcribed Table 3 columns agree with each other: nnz_A is 16 per
+    # row (edge factor 16, n = 2^scale) and nnz(A^2) / n is the printed
+    # average to its printed precision, so a mistyped digit fails here.
+    for scale in range(18, 24):
+        n = PRINTED["rmat16_scale%d_n" % scale]
+        assert n == 1 << scale
+        assert PRINTED["rmat16_scale%d_nnz_a" % scale] == 16 * n
+        avg = PRINTED["rmat16_scale%d_nnz_a2" % scale] / n
+        assert abs(avg - PRINTED["rmat16_scale%d_avg_a2" % scale]) < 0.05 + 1e-9
+
