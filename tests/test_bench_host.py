@@ -1,6 +1,7 @@
 """Host-side logic of bench.py (no GPU): the row and product samples of the
 CPU baselines, the row-product counts they rely on, the massive workload's
-partial host operands, and the served workload's expected product counts."""
+partial host operands, the served workload's expected product counts, and
+the byte counts behind T_ideal and the roofline (against access walks)."""
 import numpy as np
 
 import bench
@@ -54,3 +55,65 @@ def test_served_expected_products():
     ratio = np.array([e.products / x.products for e, x in zip(est, ex)])
     assert np.all(ratio > 0.7) and np.all(ratio < 1.4)
     assert abs(ratio.mean() - 1.0) < 0.1
+
+
+class _Tally:
+    """Byte counter for the access walk below."""
+
+    def __init__(self):
+        self.read = 0
+        self.write = 0
+
+
+def _gustavson_volume(A, B, nnz_c):
+    """Walks the two phases of a Gustavson SpGEMM and counts every element
+    read or written once per access, with int64 row pointers, int32 columns
+    and FP64 values: the accounting behind Section 4.3's ideal volumes (no
+    reuse of B rows, start and end pointer of every B row read in each
+    phase, values only in the numeric phase)."""
+    t = _Tally()
+    for phase in ("symbolic", "numeric"):
+        t.read += 8 * (A.n_rows + 1)  # A.rowPtr
+        for i in range(A.n_rows):
+            for j in range(A.row_ptr[i], A.row_ptr[i + 1]):
+                t.read += 4  # A.col[j]
+                if phase == "numeric":
+                    t.read += 8  # A.val[j]
+                k = A.col[j]
+                t.read += 8 + 8  # B.rowPtr[k], B.rowPtr[k + 1]
+                for _ in range(B.row_ptr[k], B.row_ptr[k + 1]):
+                    t.read += 4  # B.col
+                    if phase == "numeric":
+                        t.read += 8  # B.val
+    t.write += 8 * (A.n_rows + 1) + 12 * nnz_c  # C.rowPtr, C.col + C.val
+    return t.read + t.write
+
+
+def test_ideal_bytes_is_the_gustavson_access_count():
+    # bench.ideal_bytes (Eq. 8 + Eq. 9 with 8/4/8-byte types) equals a plain
+    # count of the accesses, so a dropped or doubled term fails here.
+    import oracle
+    A = inputs.ragged(60, 90, 0, 9, seed=4, matrix_id=1)
+    B = inputs.ragged(90, 120, 0, 9, seed=4, matrix_id=2)
+    C = oracle.spgemm(A, B)
+    nnz_c = int(C.row_ptr[-1])
+    P = int(bench.row_products(A, B).sum())
+    assert bench.ideal_bytes(A.n_rows, A.nnz, P, nnz_c) == _gustavson_volume(A, B, nnz_c)
+
+
+def test_numeric_sort_alg_bytes_is_the_numeric_access_count():
+    # The roofline's algorithmic bytes of the numeric sort-row kernel: the
+    # numeric phase alone, reading C.rowPtr (computed by the symbolic phase)
+    # instead of writing it.
+    import oracle
+    A = inputs.ragged(50, 70, 0, 8, seed=5, matrix_id=1)
+    B = inputs.ragged(70, 100, 0, 8, seed=5, matrix_id=2)
+    nnz_c = int(oracle.spgemm(A, B).row_ptr[-1])
+    read = 8 * (A.n_rows + 1) * 2  # A.rowPtr, C.rowPtr
+    for j in range(A.nnz):
+        k = A.col[j]
+        read += 4 + 8 + 16  # A.col, A.val, B.rowPtr[k], B.rowPtr[k + 1]
+        read += 12 * int(B.row_ptr[k + 1] - B.row_ptr[k])  # B.col + B.val
+    want = read + 12 * nnz_c
+    P = int(bench.row_products(A, B).sum())
+    assert bench.numeric_sort_alg_bytes(A.n_rows, A.nnz, P, nnz_c) == want
