@@ -12,7 +12,8 @@ steps.
 Output: one JSON line (rank 0).  ``value`` is whole-job GFLOP/s
 (2 x intermediate products / s, Section 5 definition of n_interProd), ``e2e``
 the same metric through the public API with host buffers (H2D of A and D2H of
-C inside the timed region, row blocks pipelined by magnus.spgemm_host),
+C inside the timed region; C is computed in row slabs by magnus_numeric_rows
+and each slab is copied back while the next computes, magnus.spgemm_host),
 ``roofline`` the dominant kernel's algorithmic bytes per launch over its
 measured duration against the measured HBM copy bandwidth, ``cpu_baseline``
 the CPU oracle on a bounded row sample.
@@ -83,7 +84,7 @@ WORKLOADS = {
                    "generator, drawn on the device), FP64 U(-1,1), seed 0",
 }
 CPU_SAMPLE_PRODUCTS = 1 << 29   # cpu_baseline: about 2-15 s of oracle time
-E2E_BLOCKS = 4                  # e2e: row blocks whose results are copied back while the next compute
+E2E_BLOCKS = 8                  # e2e: row slabs of C copied back while the next computes
 REF_STEP_PRODUCTS = 1 << 27     # reference arm: one step
 PROFILE_DIR = os.path.join(ROOT, "profiles")
 
@@ -97,7 +98,8 @@ def parse_args(argv=None):
     p.add_argument("--workload", default="uniform2^24", choices=sorted(WORKLOADS))
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--e2e-blocks", type=int, default=E2E_BLOCKS,
-                   help="e2e: row blocks whose results are copied back while the next compute")
+                   help="e2e: row slabs of C whose entries are copied back while the next "
+                        "compute")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--force-category", type=int, default=-1)
     p.add_argument("--sort-threshold", type=int, default=0)
@@ -850,11 +852,42 @@ def run_ablation(args, dist):
     }
 
 
+def _link_bandwidth(dst_host, src_host, dev, chunk=1 << 30):
+    """Plain pinned copies on one stream, into and out of the e2e buffers
+    (the same host pages): (H2D GB/s, D2H GB/s) over about one C's bytes."""
+    import torch
+    buf = torch.empty(chunk, dtype=torch.uint8, device=dev)
+    out = dst_host.view(torch.uint8)
+    inp = src_host.view(torch.uint8)
+    s = torch.cuda.current_stream()
+    res = []
+    for direction in ("h2d", "d2h"):
+        host = inp if direction == "h2d" else out
+        n = host.numel()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        done = 0
+        while done < n:
+            m = min(chunk, n - done)
+            if direction == "h2d":
+                buf[:m].copy_(host[done:done + m], non_blocking=True)
+            else:
+                host[done:done + m].copy_(buf[:m], non_blocking=True)
+            done += m
+        e1.record(s)
+        torch.cuda.synchronize()
+        res.append(n / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    del buf
+    return res[0], res[1]
+
+
 def run_e2e(args, dist, A, dev, params, n_inter, nnz_c):
     """Same metric through the public API with host buffers: every step
-    copies A and B from pinned host memory to the device, computes C in row
-    blocks (magnus.spgemm_host) and copies each block of C (row_ptr, col,
-    val) back to pinned host memory while the next blocks compute."""
+    copies A (which serves as both operands) from pinned host memory to the
+    device, plans the whole product and runs its symbolic phase, copies
+    C.rowPtr back, then computes C in row slabs (magnus_numeric_rows) whose
+    entries are copied back to pinned host memory while the next slab
+    computes (magnus.spgemm_host).  Every timed step is timed."""
     import torch
 
     from paper_2501_07056_gb300 import magnus
@@ -864,34 +897,43 @@ def run_e2e(args, dist, A, dev, params, n_inter, nnz_c):
     o_rp = torch.empty(A.n_rows + 1, dtype=torch.int64).pin_memory()
     o_col = torch.empty(nnz_c, dtype=torch.int32).pin_memory()
     o_val = torch.empty(nnz_c, dtype=torch.float64).pin_memory()
-    stream = torch.cuda.current_stream()
     h2d = h_rp.numel() * 8 + h_col.numel() * 4 + h_val.numel() * 8
     d2h = o_rp.numel() * 8 + o_col.numel() * 4 + o_val.numel() * 8
 
     pinned = ((h_rp, h_col, h_val), (h_rp, h_col, h_val))
+    parts = []
 
-    def step():
-        # C = A * A: A is copied once and serves as both operands
-        magnus.spgemm_host(A, A, params, blocks=args.e2e_blocks, device=dev, out=(o_rp, o_col, o_val),
-                           pinned=pinned)
+    def step(record):
+        t = {} if record else None
+        magnus.spgemm_host(A, A, params, blocks=args.e2e_blocks, device=dev,
+                           out=(o_rp, o_col, o_val), pinned=pinned, timing=t)
         torch.cuda.synchronize()
+        if record:
+            parts.append(t)
 
     for _ in range(max(1, args.warmup)):
-        step()
-    steps = max(1, min(args.steps, 10))
+        step(False)
+    link_h2d, link_d2h = _link_bandwidth(o_val, h_val, dev)
+    steps = max(1, args.steps)
     dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
-        step()
+        step(True)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     dist.barrier()
     dt_max = dist.max(dt)
     units = dist.sum(2.0 * n_inter * steps)
+    mean = {k: statistics.mean(p[k] for p in parts) for k in parts[0]} if parts else {}
     return {"value": units / dt_max / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
-            "row_blocks": args.e2e_blocks,
-            "d2h_bytes_per_step": d2h, "steps": steps, "ms_per_step": 1e3 * dt_max / steps}
+            "d2h_bytes_per_step": d2h, "row_slabs": args.e2e_blocks, "steps": steps,
+            "ms_per_step": 1e3 * dt_max / steps,
+            "parts_ms": mean,
+            "link_gbs": {"h2d": link_h2d, "d2h": link_d2h,
+                         "how": "plain pinned copies of 1 GB pieces on one stream into the "
+                                "e2e output buffer (D2H) and from the input (H2D)"},
+            "copy_floor_ms": 1e3 * (h2d / (link_h2d * 1e9) + d2h / (link_d2h * 1e9))}
 
 
 def main(argv=None):

@@ -51,7 +51,8 @@ enum magnus_status {
   MAGNUS_TIMEOUT = 6,            /* a bounded device-side wait expired (reserved) */
   MAGNUS_NOT_SYMBOLIC = 7,       /* magnus_numeric called before magnus_symbolic on this plan */
   MAGNUS_BAD_STATE = 8,          /* the plan was built for other inputs or is unusable */
-  MAGNUS_SCRATCH_LIMIT = 9       /* magnus_numeric_noalloc: the fixed staging buffer is too small */
+  MAGNUS_SCRATCH_LIMIT = 9,      /* magnus_numeric_noalloc: the fixed staging buffer is too small */
+  MAGNUS_WORKSPACE_TOO_SMALL = 10 /* a caller workspace smaller than magnus_workspace_size */
 };
 
 /* ---- row categories (Section 3.1) ------------------------------------- */
@@ -189,6 +190,59 @@ int magnus_symbolic(magnus_plan_t plan, int64_t* c_row_ptr, int64_t* nnz_c, void
 int magnus_numeric(magnus_plan_t plan, const double* a_val, const double* b_val,
                    const int64_t* c_row_ptr, int32_t* c_col, double* c_val, void* stream);
 
+/* ---- caller-owned workspace and row slabs -------------------------------
+ * The symbolic and numeric phases need device scratch beyond the plan's own
+ * arrays: the fine level's staging slabs (Algorithm 3), the coarse level's
+ * CSC copy of A, bucket counts and 12-byte-per-product staging (Algorithm 4;
+ * its batches are cut by the staging limit of Section 3.3), and the scan
+ * temporaries of C.rowPtr.  magnus_symbolic / magnus_numeric take it from
+ * the stream-ordered memory pool for the duration of the call.  The _ws
+ * variants take it from a caller-owned device region instead and allocate
+ * nothing.
+ *
+ * magnus_workspace_size  *bytes receives a size sufficient for every
+ *                        magnus_symbolic_ws, magnus_numeric_ws and
+ *                        magnus_numeric_rows call on this plan (host only, no
+ *                        device work).
+ * workspace              device pointer, 256-byte aligned, workspace_bytes
+ *                        long, owned by the caller; it must not be used by
+ *                        anything else until the call's work on `stream` has
+ *                        finished.  Too small: MAGNUS_WORKSPACE_TOO_SMALL
+ *                        before any work is enqueued.  Misaligned:
+ *                        MAGNUS_INVALID_ARG.
+ *
+ * magnus_numeric_rows - the numeric phase for rows [row_begin, row_end) of C
+ * only, on a plan of the whole product: the phase split of Section 2.1
+ * (C.rowPtr from the symbolic phase is an input of the numeric phase) makes
+ * every row's place in C known, so C can be produced slab by slab when it
+ * does not fit the device (the memory-bounded batching of rows of Section
+ * 3.3, applied to the output).
+ *   c_row_ptr   the whole C.rowPtr written by magnus_symbolic (device,
+ *               A.n_rows + 1 int64); it is read, not written.
+ *   c_col/c_val device, at least c_row_ptr[row_end] - c_row_ptr[row_begin]
+ *               entries: entry e of C (c_row_ptr[row_begin] <= e <
+ *               c_row_ptr[row_end]) is written at index e -
+ *               c_row_ptr[row_begin].  The slab's own row pointers are
+ *               c_row_ptr[row_begin..row_end] - c_row_ptr[row_begin].
+ *   workspace   NULL (scratch from the pool) or a caller region as above.
+ * 0 <= row_begin <= row_end <= A.n_rows, else MAGNUS_INVALID_ARG; an empty
+ * range returns MAGNUS_OK without work.  Results equal the same rows of
+ * magnus_numeric (within the value tolerance; structure identical).  Does
+ * not synchronise the stream; never captured in the plan's numeric graph.
+ * Rows of the coarse level are computed in the part of each coarse batch
+ * that lies in the range (the batch's histogram is recomputed unless the
+ * range covers the whole batch). */
+int magnus_workspace_size(magnus_plan_t plan, size_t* bytes);
+int magnus_symbolic_ws(magnus_plan_t plan, int64_t* c_row_ptr, int64_t* nnz_c, void* workspace,
+                       size_t workspace_bytes, void* stream);
+int magnus_numeric_ws(magnus_plan_t plan, const double* a_val, const double* b_val,
+                      const int64_t* c_row_ptr, int32_t* c_col, double* c_val, void* workspace,
+                      size_t workspace_bytes, void* stream);
+int magnus_numeric_rows(magnus_plan_t plan, int64_t row_begin, int64_t row_end,
+                        const double* a_val, const double* b_val, const int64_t* c_row_ptr,
+                        int32_t* c_col, double* c_val, void* workspace, size_t workspace_bytes,
+                        void* stream);
+
 /* magnus_numeric_noalloc - the numeric phase without any device allocation.
  * The paper has no counterpart: this entry point exists for callers that may
  * not allocate device memory once they are running, for example a solver that
@@ -207,8 +261,16 @@ int magnus_numeric(magnus_plan_t plan, const double* a_val, const double* b_val,
  * rows (force_category, very wide C, or rows with more products than a
  * slab), or whose slab alone exceeds the array, are rejected with
  * MAGNUS_SCRATCH_LIMIT before any work is enqueued.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, no allocation); the first call on a device may load
+ * the library's device code, so make that first call before any stream
+ * capture.  The fine rows run on magnus_plan_info().noalloc_fine_blocks
+ * blocks, one per staging slab that fits the array: a plan meant for this
+ * entry point should set max_scratch_bytes so that its slab (12 B per
+ * product of its heaviest fine row, at most 2^20 products) leaves room for
+ * about one slab per SM (e.g. max_scratch_bytes = 16 MB gives slabs of a
+ * few thousand products and the full resident wave), else the fine level
+ * runs on fewer blocks than the GPU has SMs.
  * All calls share the one array: calls that may overlap on the GPU (other
  * streams, other host threads) race on it and must be serialised by the
  * caller.  The row counter is cleared by every call (stream-ordered
@@ -374,6 +436,15 @@ typedef struct {
   int64_t coarse_dense_nnz;      /* last numeric call: entries of C those
                                     buckets produced */
   int64_t coarse_dense_buckets;  /* last numeric call: number of such buckets */
+  int64_t plan_bytes;            /* device memory owned by the plan */
+  int64_t workspace_bytes;       /* magnus_workspace_size of the plan */
+  int32_t noalloc_fine_blocks;   /* thread blocks magnus_numeric_noalloc runs the fine
+                                    rows on (its fixed buffer holds that many staging
+                                    slabs of 12 B x the plan's slab products; the
+                                    numeric pool path runs one resident wave); 0 when
+                                    the plan has no fine rows; -1 when that entry
+                                    point refuses the plan */
+  int32_t reserved;
 } magnus_plan_info_t;
 
 int magnus_plan_info(magnus_plan_t plan, magnus_plan_info_t* info);
@@ -396,6 +467,15 @@ enum magnus_stage {
 };
 int magnus_enable_timing(magnus_plan_t plan, int enable);
 int magnus_stage_times(magnus_plan_t plan, double* ms, int n);
+
+/* Device memory on the current device that new work may still use:
+ * *free_bytes is cudaMemGetInfo's free memory and *pool_idle_bytes the
+ * memory the device's default stream-ordered pool holds without using it
+ * (this library's scratch comes from that pool and reuses it first).
+ * A serving loop admits requests against their sum (the symbolic phase gives
+ * each C's exact size before it is allocated, Section 2.1).  Either pointer
+ * may be NULL. */
+int magnus_device_memory(size_t* free_bytes, size_t* pool_idle_bytes);
 
 /* Number of kernels this library has launched in this process. */
 uint64_t magnus_launch_count(void);

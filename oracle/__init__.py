@@ -8,8 +8,9 @@ generator, which holds no SpGEMM arithmetic.
 
 ``magnus_oracle.c`` holds the plain definitions (Eq. 1 with Algorithm 1's
 accumulation order, precise prediction of Section 2.1, and the chunk
-histogram of Algorithms 3/4); ``params.py`` holds the paper's chunk-count
-model (Eq. 2-7).  ``build()`` compiles the C file with gcc and
+histogram of Algorithms 3/4; ``spgemm_dense`` computes the same C with
+Algorithm 1's dense accumulator, bit-identical and linear in the products);
+``params.py`` holds the paper's chunk-count model (Eq. 2-7).  ``build()`` compiles the C file with gcc and
 ``-ffp-contract=off``.
 """
 from __future__ import annotations
@@ -51,6 +52,10 @@ def _load():
         lib.oracle_symbolic.restype = ctypes.c_int
         lib.oracle_numeric.argtypes = [p, p, p, p, p, p, p, i64, p, p, p, p]
         lib.oracle_numeric.restype = ctypes.c_int
+        lib.oracle_symbolic_dense.argtypes = [p, p, p, p, i64, p, i64, p]
+        lib.oracle_symbolic_dense.restype = ctypes.c_int
+        lib.oracle_numeric_dense.argtypes = [p, p, p, p, p, p, i64, p, i64, p, p, p, p]
+        lib.oracle_numeric_dense.restype = ctypes.c_int
         lib.oracle_chunk_histogram.argtypes = [p, p, p, p, p, i64, ctypes.c_int, i64, p]
         lib.oracle_chunk_histogram.restype = ctypes.c_int
         _lib = lib
@@ -142,6 +147,65 @@ def spgemm(A, B, rows=None, threads: int = 1) -> Result:
 
     _run_all(run, len(parts))
     return Result(rows, rp, col, val, ab)
+
+
+def _split_by_products(A, B, rows, parts):
+    """Contiguous pieces of ``rows`` holding about equal products."""
+    if parts <= 1 or rows.shape[0] < 2:
+        return [rows]
+    P = row_products(A, B, rows)
+    cs = np.cumsum(P)
+    cuts = np.searchsorted(cs, np.linspace(0, cs[-1], parts + 1)[1:-1], side="right")
+    return [r for r in np.split(rows, np.unique(cuts)) if r.shape[0] > 0]
+
+
+def spgemm_dense(A, B, rows=None, threads: int = 1) -> Result:
+    """The same result as ``spgemm`` (bit for bit), computed with Algorithm 1's
+    dense accumulator: linear in the products, for the full-size checks of
+    power-law matrices whose heavy rows hold millions of products.  Work is
+    split into pieces of about equal products."""
+    lib = _load()
+    rows = _c(np.arange(A.n_rows) if rows is None else rows, np.int64)
+    parts = _split_by_products(A, B, rows, 4 * threads)
+    cnts = [np.zeros(p.shape[0], np.int64) for p in parts]
+
+    def sym(k):
+        rc = lib.oracle_symbolic_dense(_ptr(A.row_ptr), _ptr(A.col), _ptr(B.row_ptr),
+                                       _ptr(B.col), B.n_cols, _ptr(parts[k]), parts[k].shape[0],
+                                       _ptr(cnts[k]))
+        if rc != 0:
+            raise MemoryError("oracle_symbolic_dense")
+
+    _run_pool(sym, len(parts), threads)
+    cnt = np.concatenate(cnts) if cnts else np.zeros(0, np.int64)
+    rp = np.zeros(rows.shape[0] + 1, np.int64)
+    np.cumsum(cnt, out=rp[1:])
+    nnz = int(rp[-1])
+    col = np.zeros(nnz, np.int32)
+    val = np.zeros(nnz, np.float64)
+    ab = np.zeros(nnz, np.float64)
+    starts = np.concatenate(([0], np.cumsum([p.shape[0] for p in parts])))
+
+    def num(k):
+        off = _c(rp[starts[k]:starts[k + 1]], np.int64)
+        rc = lib.oracle_numeric_dense(_ptr(A.row_ptr), _ptr(A.col), _ptr(A.val), _ptr(B.row_ptr),
+                                      _ptr(B.col), _ptr(B.val), B.n_cols, _ptr(parts[k]),
+                                      parts[k].shape[0], _ptr(off), _ptr(col), _ptr(val),
+                                      _ptr(ab))
+        if rc != 0:
+            raise MemoryError("oracle_numeric_dense")
+
+    _run_pool(num, len(parts), threads)
+    return Result(rows, rp, col, val, ab)
+
+
+def _run_pool(fn, n, threads):
+    if n == 1 or threads <= 1:
+        for k in range(n):
+            fn(k)
+        return
+    with _fut.ThreadPoolExecutor(min(threads, n)) as ex:
+        list(ex.map(fn, range(n)))
 
 
 def numeric_into(A, B, rows, off, col, val, ab=None) -> None:

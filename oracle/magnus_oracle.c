@@ -21,6 +21,10 @@
  *     distinct columns touched in each row.
  *   - Chunk histogram (Algorithm 3 / Algorithm 4 histogram step): the number
  *     of products of row i whose column falls in chunk (col >> shift).
+ *   - The symbolic and numeric results once more with Algorithm 1's dense
+ *     accumulator (oracle_*_dense, at the end of this file): the same sums in
+ *     the same order, bit-identical to the sort formulation, but linear in
+ *     the products, for the full-size checks of power-law matrices.
  *
  * The products of one row are materialised as (col, slot, value) triples and
  * sorted by (col, slot): this is the expand-sort-compress formulation of
@@ -162,5 +166,92 @@ int oracle_chunk_histogram(const int64_t* a_rp, const int32_t* a_col, const int6
         counts[t * n_chunks + h] += 1;
       }
   }
+  return 0;
+}
+
+/* The symbolic and numeric results again, by Algorithm 1 itself: one dense
+ * accumulator over all n_cols columns of C (value, sum of |terms|, touched
+ * flag).  Terms are added in traversal order (nonzeros of A_i in stored
+ * order, then the stored order of each B row), so every entry is the same
+ * sequence of additions into 0.0 as in the sort formulation above and the
+ * results are bit-identical to it; a row costs O(P_i + nnz_i log nnz_i)
+ * instead of O(P_i log P_i), which is what the heavy rows of a power-law
+ * matrix need.  The touched columns are listed as they are first reached and
+ * sorted before emission; the accumulator is cleared entry by entry after
+ * each row.  Returns 0, or -1 if memory could not be allocated. */
+int oracle_symbolic_dense(const int64_t* a_rp, const int32_t* a_col, const int64_t* b_rp,
+                          const int32_t* b_col, int64_t n_cols, const int64_t* rows,
+                          int64_t n_list, int64_t* cnt) {
+  unsigned char* seen = (unsigned char*)calloc((size_t)(n_cols > 0 ? n_cols : 1), 1);
+  int32_t* touched = (int32_t*)malloc((size_t)(n_cols > 0 ? n_cols : 1) * sizeof(int32_t));
+  if (!seen || !touched) {
+    free(seen);
+    free(touched);
+    return -1;
+  }
+  for (int64_t t = 0; t < n_list; ++t) {
+    int64_t i = rows[t], u = 0;
+    for (int64_t j = a_rp[i]; j < a_rp[i + 1]; ++j)
+      for (int64_t k = b_rp[a_col[j]]; k < b_rp[a_col[j] + 1]; ++k)
+        if (!seen[b_col[k]]) {
+          seen[b_col[k]] = 1;
+          touched[u++] = b_col[k];
+        }
+    for (int64_t q = 0; q < u; ++q) seen[touched[q]] = 0;
+    cnt[t] = u;
+  }
+  free(seen);
+  free(touched);
+  return 0;
+}
+
+int oracle_numeric_dense(const int64_t* a_rp, const int32_t* a_col, const double* a_val,
+                         const int64_t* b_rp, const int32_t* b_col, const double* b_val,
+                         int64_t n_cols, const int64_t* rows, int64_t n_list, const int64_t* off,
+                         int32_t* c_col, double* c_val, double* c_abs) {
+  const size_t nc = (size_t)(n_cols > 0 ? n_cols : 1);
+  double* acc = (double*)calloc(nc, sizeof(double));
+  double* sabs = (double*)calloc(nc, sizeof(double));
+  unsigned char* seen = (unsigned char*)calloc(nc, 1);
+  int32_t* touched = (int32_t*)malloc(nc * sizeof(int32_t));
+  if (!acc || !sabs || !seen || !touched) {
+    free(acc);
+    free(sabs);
+    free(seen);
+    free(touched);
+    return -1;
+  }
+  for (int64_t t = 0; t < n_list; ++t) {
+    int64_t i = rows[t], u = 0;
+    for (int64_t j = a_rp[i]; j < a_rp[i + 1]; ++j) {
+      int32_t r = a_col[j];
+      for (int64_t k = b_rp[r]; k < b_rp[r + 1]; ++k) {
+        int32_t c = b_col[k];
+        double prod = a_val[j] * b_val[k];
+        if (!seen[c]) {
+          seen[c] = 1;
+          touched[u++] = c;
+        }
+        acc[c] += prod;
+        sabs[c] += fabs(prod);
+      }
+    }
+    qsort(touched, (size_t)u, sizeof(int32_t), cmp_i32);
+    int64_t w = off[t];
+    for (int64_t q = 0; q < u; ++q) {
+      int32_t c = touched[q];
+      c_col[w] = c;
+      c_val[w] = acc[c];
+      if (c_abs) c_abs[w] = sabs[c];
+      ++w;
+      acc[c] = 0.0;
+      sabs[c] = 0.0;
+      seen[c] = 0;
+    }
+  }
+  free(acc);
+  free(sabs);
+  free(seen);
+  free(touched);
   return 0;
 }

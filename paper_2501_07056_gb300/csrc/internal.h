@@ -73,6 +73,13 @@ cudaError_t launch_bin_partition(const uint8_t* bin, int64_t n, int32_t* rows_ou
                                  int64_t* bin_counts_dev, int64_t* blk_scratch, int64_t nblk_cap,
                                  cudaStream_t s);
 int64_t bin_partition_blocks(int64_t n);
+// For a row range [r0, r1): per bin b, the positions [begin, end) of the
+// range's rows in the bin's list, relative to the bin's first entry
+// (rows_sorted is ascending within each bin).
+// out: 2 * NUM_BINS int64 (device).
+struct BinOffsets { int64_t v[NUM_BINS + 1]; };
+cudaError_t launch_bin_bounds(const int32_t* rows_sorted, BinOffsets off, int64_t r0, int64_t r1,
+                              int64_t* out, cudaStream_t s);
 cudaError_t launch_gather_i64(const int64_t* src, const int32_t* idx, int64_t n, int64_t* dst,
                               cudaStream_t s);
 cudaError_t launch_reduce_stats(const int64_t* P, int64_t n, int64_t* out2 /*sum,max*/,
@@ -119,6 +126,11 @@ struct SortArgs {
   const int64_t* c_rp;
   int32_t* c_col;
   double* c_val;
+  // numeric on a row range (magnus_numeric_rows); both NULL for the whole
+  // matrix.  range: device [begin, end) of the bin's list; c_base: device
+  // int64 subtracted from every output offset (C.rowPtr[row_begin]).
+  const int64_t* range;
+  const int64_t* c_base;
 };
 cudaError_t launch_sort_rows(int bin, bool numeric, const SortArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_sort_rows_block(int bin, bool numeric, const SortArgs& a, int num_sms,
@@ -136,6 +148,8 @@ struct DenseArgs {
   const int64_t* c_rp;
   int32_t* c_col;
   double* c_val;
+  const int64_t* range;   // as in SortArgs
+  const int64_t* c_base;
 };
 cudaError_t launch_dense_rows(bool numeric, const DenseArgs& a, int num_sms, cudaStream_t s);
 
@@ -160,6 +174,7 @@ struct FineArgs {
   const int64_t* c_rp;
   int32_t* c_col;
   double* c_val;
+  const int64_t* c_base;  // as in SortArgs (the row list is already the range's)
 };
 cudaError_t launch_fine_rows(bool numeric, const FineArgs& a, int grid, cudaStream_t s);
 // Resident blocks per SM of the fine-row kernel for a phase and chunk shift.
@@ -200,6 +215,7 @@ struct CoarseArgs {
   const int64_t* c_rp;
   int32_t* c_col;
   double* c_val;
+  const int64_t* c_base;     // as in SortArgs
   int num_sms;
   int64_t nnz_batch;         // nnz of A over the batch rows
   unsigned long long* big_stats;  // optional [3]: products, C entries, count of large buckets

@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(BK_NW * 32)
     k_bucket_small(const int64_t* __restrict__ offs, int64_t nbk, const int32_t* __restrict__ chunk_col,
                    const double* __restrict__ chunk_val, int sc, int nc, int64_t list_base,
                    const int32_t* __restrict__ rows, int32_t* __restrict__ bucket_cnt,
-                   const int64_t* __restrict__ bucket_out, const int64_t* __restrict__ c_rp,
+                   const int64_t* __restrict__ bucket_out, const int64_t* __restrict__ c_rp, const int64_t* __restrict__ c_base,
                    int32_t* __restrict__ c_col, double* __restrict__ c_val,
                    int32_t* __restrict__ big_list, int32_t* __restrict__ n_big,
                    unsigned long long* __restrict__ big_stats) {
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(BK_NW * 32)
     double* ov = nullptr;
     if (NUMERIC) {
       if (n == 0) continue;
-      const int64_t o = c_rp[rows[t]] + bucket_out[id];
+      const int64_t o = c_rp[rows[t]] - (c_base ? *c_base : 0) + bucket_out[id];
       oc = c_col + o;
       ov = c_val + o;
     }
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(FNT)
                  double* __restrict__ fine_val, int sc, int sf, int nc,
                  int64_t list_base, const int32_t* __restrict__ rows,
                  int32_t* __restrict__ bucket_cnt, const int64_t* __restrict__ bucket_out,
-                 const int64_t* __restrict__ c_rp, int32_t* __restrict__ c_col,
+                 const int64_t* __restrict__ c_rp, const int64_t* __restrict__ c_base, int32_t* __restrict__ c_col,
                  double* __restrict__ c_val, int dthr, int hash) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const int shift = sf < sc ? sf : sc;
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(FNT)
     int32_t* oc = nullptr;
     double* ov = nullptr;
     if (NUMERIC) {
-      const int64_t o = c_rp[rows[t]] + bucket_out[id];
+      const int64_t o = c_rp[rows[t]] - (c_base ? *c_base : 0) + bucket_out[id];
       oc = c_col + o;
       ov = c_val + o;
     }
@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(FNT)
                    const int32_t* __restrict__ n_big, const int32_t* __restrict__ chunk_col,
                    const double* __restrict__ chunk_val, int sc, int nc, int64_t list_base,
                    const int32_t* __restrict__ rows, int32_t* __restrict__ bucket_cnt,
-                   const int64_t* __restrict__ bucket_out, const int64_t* __restrict__ c_rp,
+                   const int64_t* __restrict__ bucket_out, const int64_t* __restrict__ c_rp, const int64_t* __restrict__ c_base,
                    int32_t* __restrict__ c_col, double* __restrict__ c_val) {
   extern __shared__ __align__(16) unsigned char dsm[];
   const int cl = 1 << sc;
@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(FNT)
     if (lane == 0) wcnt[w] = cnt;
     __syncthreads();
     if (NUMERIC) {
-      int64_t o = c_rp[rows[t]] + bucket_out[id];
+      int64_t o = c_rp[rows[t]] - (c_base ? *c_base : 0) + bucket_out[id];
       for (int i = 0; i < w; ++i) o += wcnt[i];
       const int64_t col_base = (int64_t)c << sc;
       const unsigned below = (1u << lane) - 1u;
@@ -511,11 +511,11 @@ static cudaError_t coarse_impl(CoarseArgs& a, cudaStream_t s) {
   if (k32)
     k_bucket_small<uint32_t, NUMERIC><<<gb, BK_NW * 32, 0, s>>>(
         a.counts, nbk, a.chunk_col, a.chunk_val, a.shift_coarse, a.n_chunks, a.list_base, a.rows,
-        a.bucket_cnt, a.bucket_out, a.c_rp, a.c_col, a.c_val, a.big_list, a.n_big, a.big_stats);
+        a.bucket_cnt, a.bucket_out, a.c_rp, a.c_base, a.c_col, a.c_val, a.big_list, a.n_big, a.big_stats);
   else
     k_bucket_small<uint64_t, NUMERIC><<<gb, BK_NW * 32, 0, s>>>(
         a.counts, nbk, a.chunk_col, a.chunk_val, a.shift_coarse, a.n_chunks, a.list_base, a.rows,
-        a.bucket_cnt, a.bucket_out, a.c_rp, a.c_col, a.c_val, a.big_list, a.n_big, a.big_stats);
+        a.bucket_cnt, a.bucket_out, a.c_rp, a.c_base, a.c_col, a.c_val, a.big_list, a.n_big, a.big_stats);
   count_launch();
   CK(cudaGetLastError());
   if (a.big_ev0) CK(cudaEventRecord(a.big_ev0, s));
@@ -529,7 +529,7 @@ static cudaError_t coarse_impl(CoarseArgs& a, cudaStream_t s) {
     if (per_sm < 1) per_sm = 1;
     k_bucket_dense<NUMERIC><<<(unsigned)(a.num_sms * per_sm), FNT, smem, s>>>(
         a.counts, a.big_list, a.n_big, a.chunk_col, a.chunk_val, a.shift_coarse, a.n_chunks,
-        a.list_base, a.rows, a.bucket_cnt, a.bucket_out, a.c_rp, a.c_col, a.c_val);
+        a.list_base, a.rows, a.bucket_cnt, a.bucket_out, a.c_rp, a.c_base, a.c_col, a.c_val);
   } else {
     // the sort and hash accumulators share the per-warp staging
     const bool hybrid = a.dense_chunk_threshold > 1 || (NUMERIC && a.hash);
@@ -540,7 +540,7 @@ static cudaError_t coarse_impl(CoarseArgs& a, cudaStream_t s) {
     kern<<<(unsigned)a.num_sms * 2, FNT, smem, s>>>(
         a.counts, a.big_list, a.n_big, a.chunk_col, a.chunk_val, a.fine_col, a.fine_val,
         a.shift_coarse, a.shift_fine, a.n_chunks, a.list_base, a.rows,
-        a.bucket_cnt, a.bucket_out, a.c_rp, a.c_col, a.c_val, a.dense_chunk_threshold, a.hash);
+        a.bucket_cnt, a.bucket_out, a.c_rp, a.c_base, a.c_col, a.c_val, a.dense_chunk_threshold, a.hash);
   }
   count_launch();
   CK(cudaGetLastError());

@@ -17,7 +17,11 @@ __global__ void __launch_bounds__(NT) k_dense_rows(DenseArgs a) {
   double* acc = reinterpret_cast<double*>(dsm);
   uint32_t* bits = reinterpret_cast<uint32_t*>(dsm + (NUMERIC ? (size_t)a.dense_cols * 8 : 0));
   __shared__ TileSmem<NT> ts;
-  for (int64_t t = blockIdx.x; t < a.n_rows; t += gridDim.x) {
+  // rows [first, n) of the bin's list: all of them, or a row range's
+  const int64_t first = (NUMERIC && a.range) ? a.range[0] : 0;
+  const int64_t n_end = (NUMERIC && a.range) ? a.range[1] : a.n_rows;
+  const int64_t cbase = (NUMERIC && a.c_base) ? *a.c_base : 0;
+  for (int64_t t = first + blockIdx.x; t < n_end; t += gridDim.x) {
     const int32_t row = a.rows[t];
     const int32_t lo = a.lo[row], hi = a.hi[row];
     const int range = hi - lo + 1;
@@ -32,7 +36,7 @@ __global__ void __launch_bounds__(NT) k_dense_rows(DenseArgs a) {
                                           atomicOr(&bits[idx >> 5], 1u << (idx & 31));
                                           if (NUMERIC) atomicAdd(&acc[idx], v);
                                         });
-    const int64_t outp = NUMERIC ? a.c_rp[row] : 0;
+    const int64_t outp = NUMERIC ? a.c_rp[row] - cbase : 0;
     const int64_t n = block_emit_bitmap<NT, NUMERIC>(bits, nwords, acc, lo, a.c_col, a.c_val,
                                                      outp, ts.ws);
     if (!NUMERIC && threadIdx.x == 0) a.out_cnt[row] = n;
@@ -147,8 +151,9 @@ __global__ void __launch_bounds__(NT) k_fine_rows(FineArgs a) {
       st_stream(&slab_col[pos], (int32_t)(col - col_base));
       if (NUMERIC) st_stream(&slab_val[pos], v);
     });
-    int32_t* oc = NUMERIC ? a.c_col + a.c_rp[row] : nullptr;
-    double* ov = NUMERIC ? a.c_val + a.c_rp[row] : nullptr;
+    const int64_t outp = NUMERIC ? a.c_rp[row] - (a.c_base ? *a.c_base : 0) : 0;
+    int32_t* oc = NUMERIC ? a.c_col + outp : nullptr;
+    double* ov = NUMERIC ? a.c_val + outp : nullptr;
     const int64_t count = warp_chunks_accumulate<NUMERIC, HYBRID>(
         f, nch, a.shift, slab_col, slab_val, col_base, oc, ov, a.dense_chunk_threshold, a.hash);
     if (!NUMERIC && threadIdx.x == 0) a.out_cnt[row] = count;

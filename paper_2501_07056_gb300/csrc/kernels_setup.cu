@@ -275,6 +275,32 @@ cudaError_t launch_row_desc(const int32_t* rows, int64_t n, const int64_t* a_rp,
   return cudaGetLastError();
 }
 
+// Row range [r0, r1) -> per bin, the positions of its rows in the bin's
+// list, relative to the bin's first entry (lower bounds of r0 and r1; each
+// bin's list is ascending by row).
+__global__ void k_bin_bounds(const int32_t* __restrict__ rows, BinOffsets off, int64_t r0,
+                             int64_t r1, int64_t* __restrict__ out) {
+  const int b = threadIdx.x;
+  if (b >= NUM_BINS) return;
+  for (int k = 0; k < 2; ++k) {
+    const int64_t key = k == 0 ? r0 : r1;
+    int64_t lo = off.v[b], hi = off.v[b + 1];
+    while (lo < hi) {
+      const int64_t mid = lo + ((hi - lo) >> 1);
+      if ((int64_t)rows[mid] < key) lo = mid + 1;
+      else hi = mid;
+    }
+    out[2 * b + k] = lo - off.v[b];
+  }
+}
+
+cudaError_t launch_bin_bounds(const int32_t* rows_sorted, BinOffsets off, int64_t r0, int64_t r1,
+                              int64_t* out, cudaStream_t s) {
+  k_bin_bounds<<<1, 32, 0, s>>>(rows_sorted, off, r0, r1, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
 __global__ void k_gather_i64(const int64_t* src, const int32_t* idx, int64_t n, int64_t* dst) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x)

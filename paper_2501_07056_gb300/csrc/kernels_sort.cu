@@ -43,7 +43,10 @@ __global__ void __launch_bounds__(NW * 32) k_sort_rows(SortArgs a) {
   const int gshift = grp * W;
   const unsigned gbits = (W == 32) ? FULL : ((1u << W) - 1u);
   const int64_t stride = (int64_t)gridDim.x * NW * G;
-  const int64_t n = a.n_rows;
+  // rows [first, n) of the bin's list: all of them, or a row range's
+  const int64_t first = (NUMERIC && a.range) ? a.range[0] : 0;
+  const int64_t n = (NUMERIC && a.range) ? a.range[1] : a.n_rows;
+  const int64_t cbase = (NUMERIC && a.c_base) ? *a.c_base : 0;
 
   // Level 1 of the load chain: the row descriptor (and the recorded order).
   struct Pre1 { RowDesc d; uint64_t perm; };
@@ -61,7 +64,7 @@ __global__ void __launch_bounds__(NW * 32) k_sort_rows(SortArgs a) {
   auto load2 = [&](int64_t base, const Pre1& p1) -> Pre2 {
     Pre2 q{0, 0, 0, 0.0};
     if (base + grp < n) {
-      if (NUMERIC) q.crp = a.c_rp[p1.d.row];
+      if (NUMERIC) q.crp = a.c_rp[p1.d.row] - cbase;
       if (l < p1.d.na) {
         const uint64_t sg = a.seg[p1.d.as + l];
         q.bs = seg_start(sg);
@@ -240,7 +243,7 @@ __global__ void __launch_bounds__(NW * 32) k_sort_rows(SortArgs a) {
   // group is finished, level 2 of the next group and level 1 of the one
   // after it are in flight.  The loop is written as two halves so that each
   // stage keeps its own registers (no copies of values still being loaded).
-  int64_t b = ((int64_t)blockIdx.x * NW + w) * G;
+  int64_t b = first + ((int64_t)blockIdx.x * NW + w) * G;
   Pre1 p1a = load1(b), p1b = load1(b + stride);
   Pre2 p2a = load2(b, p1a), p2b;
   while (b < n) {

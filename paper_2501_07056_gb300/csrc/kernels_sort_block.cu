@@ -98,8 +98,12 @@ __global__ void __launch_bounds__((1 << CAPLOG) / BR) k_sort_rows_block(SortArgs
   __shared__ int32_t s_ws[NWB + 1];
   __shared__ int32_t s_ws2[NWB + 1];
   const int t = threadIdx.x, lane = lane_id(), w = warp_id();
+  // rows [first, n) of the bin's list: all of them, or a row range's
+  const int64_t first = (NUMERIC && a.range) ? a.range[0] : 0;
+  const int64_t n = (NUMERIC && a.range) ? a.range[1] : a.n_rows;
+  const int64_t cbase = (NUMERIC && a.c_base) ? *a.c_base : 0;
 
-  for (int64_t idx = blockIdx.x; idx < a.n_rows; idx += gridDim.x) {
+  for (int64_t idx = first + blockIdx.x; idx < n; idx += gridDim.x) {
     const RowDesc d = a.desc[idx];
     const int64_t poff = a.perm2_off[idx];
     // 1. segments: the non-empty B rows referenced by the row, in stored
@@ -232,7 +236,7 @@ __global__ void __launch_bounds__((1 << CAPLOG) / BR) k_sort_rows_block(SortArgs
         if (lane < HW) s_pw[lane] = inc - c;
       }
       __syncthreads();
-      const int64_t crp = a.c_rp[d.row];
+      const int64_t crp = a.c_rp[d.row] - cbase;
 #pragma unroll
       for (int e = 0; e < BR; ++e) {
         const int q = e * NT + t;

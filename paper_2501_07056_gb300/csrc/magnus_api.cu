@@ -137,6 +137,7 @@ struct magnus_plan_s {
   int64_t scratch_cap = 0;  // bytes
   // device arrays owned by the plan
   std::vector<void*> owned;
+  int64_t owned_bytes = 0;
   int64_t* P = nullptr;
   uint8_t* bin = nullptr;
   int32_t* lo = nullptr;
@@ -206,6 +207,7 @@ int plan_alloc(magnus_plan_t pl, T** p, size_t count, cudaStream_t s) {
   void* v;
   MAG_TRY(dev_alloc(&v, count * sizeof(T), s));
   pl->owned.push_back(v);
+  pl->owned_bytes += (int64_t)(count * sizeof(T));
   *p = reinterpret_cast<T*>(v);
   return MAGNUS_OK;
 }
@@ -311,6 +313,8 @@ const char* magnus_strerror(int s) {
     case MAGNUS_SCRATCH_LIMIT:
       return "the allocation-free numeric entry point needs more staging than its fixed buffer "
              "(MAGNUS_NOALLOC_SCRATCH_BYTES) holds, or the plan has coarse rows";
+    case MAGNUS_WORKSPACE_TOO_SMALL:
+      return "the caller's workspace is smaller than magnus_workspace_size";
     default: return "unknown status";
   }
 }
@@ -318,6 +322,21 @@ const char* magnus_strerror(int s) {
 const char* magnus_last_cuda_error(void) { return g_cuda_err.c_str(); }
 
 uint64_t magnus_launch_count(void) { return launches_total(); }
+
+int magnus_device_memory(size_t* free_bytes, size_t* pool_idle_bytes) {
+  size_t fr = 0, tot = 0;
+  CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  cudaMemPool_t pool;
+  CUDA_TRY(cudaDeviceGetDefaultMemPool(&pool, dev));
+  uint64_t reserved = 0, used = 0;
+  CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved));
+  CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+  if (free_bytes) *free_bytes = fr;
+  if (pool_idle_bytes) *pool_idle_bytes = (size_t)(reserved > used ? reserved - used : 0);
+  return MAGNUS_OK;
+}
 
 void magnus_free(magnus_plan_t p) {
   if (!p) return;
@@ -649,12 +668,193 @@ int magnus_plan(magnus_plan_t* plan, const magnus_csr_t* A, const magnus_csr_t* 
   return MAGNUS_OK;
 }
 
-// Runs one phase (symbolic or numeric) over every category.
-static int run_phase(magnus_plan_t pl, bool numeric, int64_t* out_cnt, const int64_t* c_rp,
-                     int32_t* c_col, double* c_val, cudaStream_t s) {
-  Scratch scr(s);
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Scratch of one phase call.  Every device buffer a symbolic or numeric call
+// needs beyond the plan's own arrays is carved from one region: either the
+// caller's workspace or one stream-ordered allocation freed at the end of
+// the call.  The same carving, run without a base, measures the region
+// (magnus_workspace_size).  The categories run one after another on the
+// call's stream, so the fine level, the coarse level and the C.rowPtr scan
+// reuse the same bytes.
+namespace {
+
+struct Arena {
+  unsigned char* base = nullptr;  // NULL: measure only
+  size_t cap = 0, off = 0, peak = 0;
+  bool overflow = false;
+  template <typename T>
+  T* get(size_t count) {
+    const size_t a = (off + 255) & ~(size_t)255;
+    off = a + (count ? count : 1) * sizeof(T);
+    if (off > peak) peak = off;
+    if (!base) return nullptr;
+    if (off > cap) {
+      overflow = true;
+      return nullptr;
+    }
+    return reinterpret_cast<T*>(base + a);
+  }
+};
+
+// Coarse batches [b0, b1) of the coarse list, with the staging maxima.
+struct CoarseSizes {
+  int64_t maxP = 0, maxNnz = 0, maxRows = 0;
+};
+
+CoarseSizes coarse_sizes(magnus_plan_t pl) {
+  CoarseSizes z;
+  const size_t nbat = pl->coarse_batches.empty() ? 0 : pl->coarse_batches.size() - 1;
+  for (size_t bi = 0; bi < nbat; ++bi) {
+    int64_t p = 0, q = 0;
+    for (int64_t i = pl->coarse_batches[bi]; i < pl->coarse_batches[bi + 1]; ++i) {
+      p += pl->coarse_P[i];
+      q += pl->coarse_nnz[i];
+    }
+    z.maxP = std::max(z.maxP, p);
+    z.maxNnz = std::max(z.maxNnz, q);
+    z.maxRows = std::max(z.maxRows, pl->coarse_batches[bi + 1] - pl->coarse_batches[bi]);
+  }
+  return z;
+}
+
+// The fine rows of a phase stage their products unless the symbolic pass
+// counts them directly (one bitmap over a small, dense enough column range;
+// k_fine_rows applies the same test).
+bool fine_needs_staging(magnus_plan_t pl, bool numeric) {
+  if (numeric) return !pl->fine_rows.empty();
+  for (size_t i = 0; i < pl->fine_rows.size(); ++i) {
+    const int64_t range = (int64_t)pl->fine_hi[i] - pl->fine_lo[i] + 1;
+    if (!(range <= ((int64_t)1 << 19) && ((range + 31) >> 5) <= 4 * pl->fine_P[i])) return true;
+  }
+  return false;
+}
+
+struct PhaseScratch {
+  int64_t* bounds = nullptr;      // row range: per bin [begin, end) of the range's rows
+  int32_t* fine_sub = nullptr;    // row range: the range's fine rows (heaviest first)
+  int64_t* fine_sub_P = nullptr;
+  int32_t* queue = nullptr;       // fine: row counter
+  int32_t* scol = nullptr;        // fine: staging slabs
+  double* sval = nullptr;
+  CoarseArgs co{};                // coarse: scratch pointers
+  int64_t* scan_tmp = nullptr;    // symbolic: C.rowPtr scan
+};
+
+// Carves (or, with ar.base == NULL, measures) the scratch of one phase call.
+void carve_phase(magnus_plan_t pl, bool numeric, bool rows_mode, Arena& ar, PhaseScratch& ps) {
+  const int64_t nfine = (int64_t)pl->fine_rows.size();
+  if (rows_mode) {
+    ps.bounds = ar.get<int64_t>(2 * NUM_BINS);
+    if (nfine > 0) {
+      ps.fine_sub = ar.get<int32_t>((size_t)nfine);
+      ps.fine_sub_P = ar.get<int64_t>((size_t)nfine);
+    }
+  }
+  const size_t shared_start = ar.off;
+  // fine level
+  if (nfine > 0) {
+    ps.queue = ar.get<int32_t>(1);
+    if (fine_needs_staging(pl, numeric)) {
+      const size_t grid = (size_t)(numeric ? pl->fine_grid_num : pl->fine_grid_sym);
+      ps.scol = ar.get<int32_t>(grid * (size_t)pl->fine_slab);
+      if (numeric) ps.sval = ar.get<double>(grid * (size_t)pl->fine_slab);
+    }
+  }
+  // coarse level (reuses the fine level's bytes)
+  ar.off = shared_start;
+  if (!pl->coarse_batches.empty()) {
+    const CoarseSizes z = coarse_sizes(pl);
+    const int64_t nB = pl->B.n_rows;
+    const int64_t nbk = z.maxRows * pl->n_chunks_coarse;
+    CoarseArgs& a = ps.co;
+    a.col_cnt = ar.get<int32_t>((size_t)nB + 1);
+    a.col_ptr = ar.get<int64_t>((size_t)nB + 1);
+    a.csc_row = ar.get<int32_t>((size_t)z.maxNnz);
+    if (numeric) a.csc_val = ar.get<double>((size_t)z.maxNnz);
+    a.rows_b = ar.get<int32_t>((size_t)nB + 1);
+    a.item_off = ar.get<int64_t>((size_t)nB + 1);
+    a.n_rows_b = ar.get<int32_t>(2);
+    a.counts = ar.get<int64_t>((size_t)nbk + 1);
+    a.cursor = ar.get<unsigned long long>((size_t)nbk);
+    const bool fine_inside = pl->shift_coarse > 13;
+    a.chunk_col = ar.get<int32_t>((size_t)z.maxP);
+    if (fine_inside) a.fine_col = ar.get<int32_t>((size_t)z.maxP);
+    if (numeric) {
+      a.chunk_val = ar.get<double>((size_t)z.maxP);
+      if (fine_inside) a.fine_val = ar.get<double>((size_t)z.maxP);
+      a.bucket_out = ar.get<int64_t>((size_t)nbk);
+    }
+    a.scan_tmp = ar.get<int64_t>((size_t)scan_tmp_elems(std::max<int64_t>(nB, nbk)) + 2);
+    a.big_list = ar.get<int32_t>((size_t)nbk);
+    a.n_big = ar.get<int32_t>(2);
+  }
+  // the symbolic pass's C.rowPtr scan (after every category)
+  ar.off = shared_start;
+  if (!numeric) ps.scan_tmp = ar.get<int64_t>((size_t)scan_tmp_elems(pl->A.n_rows) + 2);
+  ar.off = ar.peak;
+}
+
+size_t phase_bytes(magnus_plan_t pl, bool numeric, bool rows_mode) {
+  Arena ar;
+  PhaseScratch ps;
+  carve_phase(pl, numeric, rows_mode, ar, ps);
+  return ar.peak;
+}
+
+// The region of one call: the caller's workspace, or one stream-ordered
+// allocation released (stream-ordered) when the call returns.
+struct PhaseRegion {
+  cudaStream_t s = nullptr;
+  void* owned = nullptr;
+  ~PhaseRegion() {
+    if (owned) cudaFreeAsync(owned, s);
+  }
+};
+
+int open_region(magnus_plan_t pl, bool numeric, bool rows_mode, void* ws, size_t ws_bytes,
+                cudaStream_t s, PhaseRegion& reg, PhaseScratch& ps) {
+  const size_t need = phase_bytes(pl, numeric, rows_mode);
+  Arena ar;
+  if (ws) {
+    if (ws_bytes < need) return MAGNUS_WORKSPACE_TOO_SMALL;
+    if (((uintptr_t)ws & 255) != 0) return MAGNUS_INVALID_ARG;
+    ar.base = static_cast<unsigned char*>(ws);
+    ar.cap = ws_bytes;
+  } else {
+    reg.s = s;
+    MAG_TRY(dev_alloc(&reg.owned, need, s));
+    ar.base = static_cast<unsigned char*>(reg.owned);
+    ar.cap = need;
+  }
+  carve_phase(pl, numeric, rows_mode, ar, ps);
+  return ar.overflow ? MAGNUS_WORKSPACE_TOO_SMALL : MAGNUS_OK;
+}
+
+}  // namespace
+
+
+// Runs one phase (symbolic or numeric) over every category.  With a row
+// range (numeric only) just the rows [r0, r1) are computed, and their
+// entries are written from c_col / c_val[0] on (offsets less
+// C.rowPtr[r0]).
+struct RowRange {
+  bool on = false;
+  int64_t r0 = 0, r1 = 0;
+};
+
+static int run_phase(magnus_plan_t pl, bool numeric, const RowRange& rr, int64_t* out_cnt,
+                     const int64_t* c_rp, int32_t* c_col, double* c_val, const PhaseScratch& ps,
+                     cudaStream_t s) {
   Csr A = pl->A, B = pl->B;
   const int st_base = numeric ? MAGNUS_STAGE_NUM_SORT : MAGNUS_STAGE_SYM_SORT;
+  const int64_t* c_base = rr.on ? c_rp + rr.r0 : nullptr;
+  if (rr.on) {
+    BinOffsets bo;
+    for (int b = 0; b <= NUM_BINS; ++b) bo.v[b] = pl->bin_off[b];
+    CUDA_TRY(launch_bin_bounds(pl->rows_sorted, bo, rr.r0, rr.r1, ps.bounds, s));
+  }
   // sort rows
   {
     StageTimer tm(pl, st_base + 0, s);
@@ -673,6 +873,8 @@ static int run_phase(magnus_plan_t pl, bool numeric, int64_t* out_cnt, const int
       a.c_rp = c_rp;
       a.c_col = c_col;
       a.c_val = c_val;
+      a.range = rr.on ? ps.bounds + 2 * b : nullptr;
+      a.c_base = c_base;
       if (b <= BIN_SORT256) CUDA_TRY(launch_sort_rows(b, numeric, a, pl->num_sms, s));
       else CUDA_TRY(launch_sort_rows_block(b, numeric, a, pl->num_sms, s));
     }
@@ -692,78 +894,85 @@ static int run_phase(magnus_plan_t pl, bool numeric, int64_t* out_cnt, const int
     a.c_rp = c_rp;
     a.c_col = c_col;
     a.c_val = c_val;
+    a.range = rr.on ? ps.bounds + 2 * BIN_DENSE : nullptr;
+    a.c_base = c_base;
     CUDA_TRY(launch_dense_rows(numeric, a, pl->num_sms, s));
   }
   int64_t staged = 0;
   // fine rows: one persistent launch; each block stages its row in its slab
   if (!pl->fine_rows.empty()) {
     StageTimer tm(pl, st_base + 2, s);
-    const int shift = numeric ? pl->shift_fine : pl->shift_fine_sym;
-    const int grid = numeric ? pl->fine_grid_num : pl->fine_grid_sym;
-    // The numeric pass stages every fine row.  The symbolic pass counts a
-    // row directly (no staging) when one bitmap over its range is small
-    // enough and dense enough; the kernel applies the same test.
-    bool need_stage = false;
-    for (size_t i = 0; i < pl->fine_rows.size(); ++i) {
-      const int64_t range = (int64_t)pl->fine_hi[i] - pl->fine_lo[i] + 1;
-      const bool direct = !numeric && range <= ((int64_t)1 << 19) &&
-                          ((range + 31) >> 5) <= 4 * pl->fine_P[i];
-      if (!direct) {
-        need_stage = true;
-        if (numeric) staged += pl->fine_P[i];
+    const int32_t* rows = pl->fine_rows_d;
+    const int64_t* rows_P = pl->fine_P_d;
+    int64_t nf = (int64_t)pl->fine_rows.size();
+    if (rr.on) {
+      // the range's fine rows, still heaviest first
+      std::vector<int32_t> sub;
+      std::vector<int64_t> subP;
+      for (size_t i = 0; i < pl->fine_rows.size(); ++i) {
+        if (pl->fine_rows[i] >= rr.r0 && pl->fine_rows[i] < rr.r1) {
+          sub.push_back(pl->fine_rows[i]);
+          subP.push_back(pl->fine_P[i]);
+        }
       }
+      nf = (int64_t)sub.size();
+      if (nf > 0) {
+        CUDA_TRY(cudaMemcpyAsync(ps.fine_sub, sub.data(), sub.size() * 4, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(ps.fine_sub_P, subP.data(), subP.size() * 8,
+                                 cudaMemcpyHostToDevice, s));
+        // pageable sources: the copies have left the vectors when the calls return
+      }
+      rows = ps.fine_sub;
+      rows_P = ps.fine_sub_P;
+      for (int64_t p : subP) staged += p;
+    } else if (numeric) {
+      for (int64_t p : pl->fine_P) staged += p;
     }
-    int32_t* scol = nullptr;
-    double* sval = nullptr;
-    int32_t* queue = nullptr;
-    MAG_TRY(scr.get(&queue, 1));
-    CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(int32_t), s));
-    if (need_stage) {
-      MAG_TRY(scr.get(&scol, (size_t)grid * pl->fine_slab));
-      if (numeric) MAG_TRY(scr.get(&sval, (size_t)grid * pl->fine_slab));
-      pl->scratch_used = std::max<int64_t>(pl->scratch_used,
-                                           (int64_t)grid * pl->fine_slab * (numeric ? 12 : 4));
+    if (nf > 0) {
+      const int shift = numeric ? pl->shift_fine : pl->shift_fine_sym;
+      const int grid = numeric ? pl->fine_grid_num : pl->fine_grid_sym;
+      CUDA_TRY(cudaMemsetAsync(ps.queue, 0, sizeof(int32_t), s));
+      if (ps.scol)
+        pl->scratch_used = std::max<int64_t>(pl->scratch_used,
+                                             (int64_t)grid * pl->fine_slab * (numeric ? 12 : 4));
+      FineArgs a{};
+      a.A = A;
+      a.B = B;
+      a.rows = rows;
+      a.n_rows = nf;
+      a.slab_elems = pl->fine_slab;
+      a.queue = ps.queue;
+      a.row_products = rows_P;
+      a.lo = pl->lo;
+      a.hi = pl->hi;
+      a.shift = shift;
+      a.dense_chunk_threshold = pl->dthr;
+      a.hash = numeric ? pl->hash : 0;
+      a.stage_col = ps.scol;
+      a.stage_val = ps.sval;
+      a.out_cnt = out_cnt;
+      a.c_rp = c_rp;
+      a.c_col = c_col;
+      a.c_val = c_val;
+      a.c_base = c_base;
+      CUDA_TRY(launch_fine_rows(numeric, a, grid, s));
     }
-    FineArgs a{};
-    a.A = A;
-    a.B = B;
-    a.rows = pl->fine_rows_d;
-    a.n_rows = (int64_t)pl->fine_rows.size();
-    a.slab_elems = pl->fine_slab;
-    a.queue = queue;
-    a.row_products = pl->fine_P_d;
-    a.lo = pl->lo;
-    a.hi = pl->hi;
-    a.shift = shift;
-    a.dense_chunk_threshold = pl->dthr;
-    a.hash = numeric ? pl->hash : 0;
-    a.stage_col = scol;
-    a.stage_val = sval;
-    a.out_cnt = out_cnt;
-    a.c_rp = c_rp;
-    a.c_col = c_col;
-    a.c_val = c_val;
-    CUDA_TRY(launch_fine_rows(numeric, a, grid, s));
   }
-  // coarse rows, batch by batch
+  // coarse rows, batch by batch (a row range runs the part of each batch
+  // inside it)
   {
     StageTimer tm(pl, st_base + 3, s);
     const size_t nbat = pl->coarse_batches.empty() ? 0 : pl->coarse_batches.size() - 1;
     if (nbat > 0) {
-      int64_t maxP = 0, maxNnz = 0, maxRows = 0;
-      for (size_t bi = 0; bi < nbat; ++bi) {
-        int64_t p = 0, z = 0;
-        for (int64_t i = pl->coarse_batches[bi]; i < pl->coarse_batches[bi + 1]; ++i) {
-          p += pl->coarse_P[i];
-          z += pl->coarse_nnz[i];
-        }
-        maxP = std::max(maxP, p);
-        maxNnz = std::max(maxNnz, z);
-        maxRows = std::max(maxRows, pl->coarse_batches[bi + 1] - pl->coarse_batches[bi]);
+      int64_t i0 = 0, i1 = (int64_t)pl->coarse_rows.size();
+      if (rr.on) {
+        // the coarse list is ascending by row (bin order); rows fit int32
+        i0 = std::lower_bound(pl->coarse_rows.begin(), pl->coarse_rows.end(), (int32_t)rr.r0) -
+             pl->coarse_rows.begin();
+        i1 = std::lower_bound(pl->coarse_rows.begin(), pl->coarse_rows.end(), (int32_t)rr.r1) -
+             pl->coarse_rows.begin();
       }
-      const int64_t nB = B.n_rows;
-      const int64_t nbk = maxRows * pl->n_chunks_coarse;
-      CoarseArgs a{};
+      CoarseArgs a = ps.co;
       a.A = A;
       a.B = B;
       a.shift_coarse = pl->shift_coarse;
@@ -772,28 +981,10 @@ static int run_phase(magnus_plan_t pl, bool numeric, int64_t* out_cnt, const int
       a.dense_chunk_threshold = pl->dthr;
       a.hash = numeric ? pl->hash : 0;
       a.num_sms = pl->num_sms;
-      MAG_TRY(scr.get(&a.col_cnt, (size_t)nB + 1));
-      MAG_TRY(scr.get(&a.col_ptr, (size_t)nB + 1));
-      MAG_TRY(scr.get(&a.csc_row, (size_t)maxNnz));
-      if (numeric) MAG_TRY(scr.get(&a.csc_val, (size_t)maxNnz));
-      MAG_TRY(scr.get(&a.rows_b, (size_t)nB + 1));
-      MAG_TRY(scr.get(&a.item_off, (size_t)nB + 1));
-      MAG_TRY(scr.get(&a.n_rows_b, 2));
-      MAG_TRY(scr.get(&a.counts, (size_t)nbk + 1));
-      MAG_TRY(scr.get(&a.cursor, (size_t)nbk));
+      const CoarseSizes z = coarse_sizes(pl);
       const bool fine_inside = pl->shift_coarse > 13;
-      MAG_TRY(scr.get(&a.chunk_col, (size_t)maxP));
-      if (fine_inside) MAG_TRY(scr.get(&a.fine_col, (size_t)maxP));
-      if (numeric) {
-        MAG_TRY(scr.get(&a.chunk_val, (size_t)maxP));
-        if (fine_inside) MAG_TRY(scr.get(&a.fine_val, (size_t)maxP));
-        MAG_TRY(scr.get(&a.bucket_out, (size_t)nbk));
-      }
-      MAG_TRY(scr.get(&a.scan_tmp, (size_t)scan_tmp_elems(std::max<int64_t>(nB, nbk)) + 2));
-      MAG_TRY(scr.get(&a.big_list, (size_t)nbk));
-      MAG_TRY(scr.get(&a.n_big, 2));
       pl->scratch_used = std::max<int64_t>(pl->scratch_used,
-                                           maxP * (numeric ? 12 : 4) * (fine_inside ? 2 : 1));
+                                           z.maxP * (numeric ? 12 : 4) * (fine_inside ? 2 : 1));
       a.bucket_cnt = pl->bucket_cnt;
       if (numeric) {
         a.big_stats = pl->big_stats;
@@ -812,22 +1003,28 @@ static int run_phase(magnus_plan_t pl, bool numeric, int64_t* out_cnt, const int
       a.c_rp = c_rp;
       a.c_col = c_col;
       a.c_val = c_val;
+      a.c_base = c_base;
+      int used = 0;
       for (size_t bi = 0; bi < nbat; ++bi) {
-        const int64_t r0 = pl->coarse_batches[bi], r1 = pl->coarse_batches[bi + 1];
+        const int64_t b0 = pl->coarse_batches[bi], b1 = pl->coarse_batches[bi + 1];
+        const int64_t r0 = std::max(b0, i0), r1 = std::min(b1, i1);
+        if (r0 >= r1) continue;
         a.rows = pl->coarse_rows_d + r0;
         a.n_rows = r1 - r0;
         a.list_base = r0;
-        int64_t z = 0;
+        int64_t nz = 0;
         for (int64_t i = r0; i < r1; ++i) {
-          z += pl->coarse_nnz[i];
-          staged += pl->coarse_P[i];
+          nz += pl->coarse_nnz[i];
+          if (numeric) staged += pl->coarse_P[i];
         }
-        a.nnz_batch = z;
-        a.saved_offs = pl->coarse_offs ? pl->coarse_offs + pl->coarse_offs_at[bi] : nullptr;
+        a.nnz_batch = nz;
+        // the bucket offsets kept by the symbolic pass cover whole batches
+        const bool whole = r0 == b0 && r1 == b1;
+        a.saved_offs = (pl->coarse_offs && whole) ? pl->coarse_offs + pl->coarse_offs_at[bi] : nullptr;
         if (pl->timing) {
-          a.big_ev0 = pl->big_ev[ph][2 * bi];
-          a.big_ev1 = pl->big_ev[ph][2 * bi + 1];
-          pl->big_ev_used[ph] = (int)bi + 1;
+          a.big_ev0 = pl->big_ev[ph][2 * used];
+          a.big_ev1 = pl->big_ev[ph][2 * used + 1];
+          pl->big_ev_used[ph] = ++used;
         }
         CUDA_TRY(run_coarse_batch(numeric, a, s));
       }
@@ -837,22 +1034,21 @@ static int run_phase(magnus_plan_t pl, bool numeric, int64_t* out_cnt, const int
   return MAGNUS_OK;
 }
 
-int magnus_symbolic(magnus_plan_t pl, int64_t* c_row_ptr, int64_t* nnz_c, void* stream) {
-  if (!pl || !c_row_ptr || !nnz_c) return MAGNUS_INVALID_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
+static int symbolic_impl(magnus_plan_t pl, int64_t* c_row_ptr, int64_t* nnz_c, void* ws,
+                         size_t ws_bytes, cudaStream_t s) {
   pl->last_stream = s;
   pl->symbolic_done = false;
   for (int i = 0; i < MAGNUS_STAGE_COUNT; ++i) pl->ev_used[i] = false;
   pl->big_ev_used[0] = pl->big_ev_used[1] = 0;
   const int64_t n = pl->A.n_rows;
+  PhaseRegion reg;
+  PhaseScratch ps;
+  MAG_TRY(open_region(pl, false, false, ws, ws_bytes, s, reg, ps));
   CUDA_TRY(cudaMemsetAsync(c_row_ptr, 0, (size_t)(n + 1) * sizeof(int64_t), s));
-  MAG_TRY(run_phase(pl, false, c_row_ptr, nullptr, nullptr, nullptr, s));
+  MAG_TRY(run_phase(pl, false, RowRange{}, c_row_ptr, nullptr, nullptr, nullptr, ps, s));
   {
     StageTimer tm(pl, MAGNUS_STAGE_SYM_SCAN, s);
-    Scratch scr(s);
-    int64_t* tmp;
-    MAG_TRY(scr.get(&tmp, (size_t)scan_tmp_elems(n) + 2));
-    CUDA_TRY(launch_exclusive_scan_i64(c_row_ptr, n, tmp, s));
+    CUDA_TRY(launch_exclusive_scan_i64(c_row_ptr, n, ps.scan_tmp, s));
   }
   int64_t h = 0;
   CUDA_TRY(cudaMemcpyAsync(&h, c_row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -863,48 +1059,118 @@ int magnus_symbolic(magnus_plan_t pl, int64_t* c_row_ptr, int64_t* nnz_c, void* 
   return MAGNUS_OK;
 }
 
-int magnus_numeric(magnus_plan_t pl, const double* a_val, const double* b_val,
-                   const int64_t* c_row_ptr, int32_t* c_col, double* c_val, void* stream) {
+static int numeric_impl(magnus_plan_t pl, const RowRange& rr, const double* a_val,
+                        const double* b_val, const int64_t* c_row_ptr, int32_t* c_col,
+                        double* c_val, void* ws, size_t ws_bytes, cudaStream_t s) {
   if (!pl || !c_row_ptr) return MAGNUS_INVALID_ARG;
   if (!pl->symbolic_done) return MAGNUS_NOT_SYMBOLIC;
   if ((pl->A.nnz > 0 && !a_val) || (pl->B.nnz > 0 && !b_val)) return MAGNUS_INVALID_ARG;
   if (pl->nnz_c > 0 && (!c_col || !c_val)) return MAGNUS_INVALID_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
   pl->last_stream = s;
   for (int i = MAGNUS_STAGE_NUM_SORT; i <= MAGNUS_STAGE_NUM_COARSE; ++i) pl->ev_used[i] = false;
   pl->big_ev_used[1] = 0;
   pl->A.val = a_val;
   pl->B.val = b_val;
-  if (pl->use_graph && !pl->timing && s != nullptr) {
-    const void* key[5] = {a_val, b_val, c_row_ptr, c_col, c_val};
-    return pl->graph.run(key, 5, s, [&]() { return run_phase(pl, true, nullptr, c_row_ptr, c_col, c_val, s); });
+  auto body = [&]() -> int {
+    PhaseRegion reg;
+    PhaseScratch ps;
+    MAG_TRY(open_region(pl, true, rr.on, ws, ws_bytes, s, reg, ps));
+    return run_phase(pl, true, rr, nullptr, c_row_ptr, c_col, c_val, ps, s);
+  };
+  if (!rr.on && pl->use_graph && !pl->timing && s != nullptr) {
+    const void* key[6] = {a_val, b_val, c_row_ptr, c_col, c_val, ws};
+    return pl->graph.run(key, 6, s, body);
   }
-  return run_phase(pl, true, nullptr, c_row_ptr, c_col, c_val, s);
+  return body();
 }
+
+extern "C" {
+
+int magnus_symbolic(magnus_plan_t pl, int64_t* c_row_ptr, int64_t* nnz_c, void* stream) {
+  if (!pl || !c_row_ptr || !nnz_c) return MAGNUS_INVALID_ARG;
+  return symbolic_impl(pl, c_row_ptr, nnz_c, nullptr, 0, (cudaStream_t)stream);
+}
+
+int magnus_symbolic_ws(magnus_plan_t pl, int64_t* c_row_ptr, int64_t* nnz_c, void* workspace,
+                       size_t workspace_bytes, void* stream) {
+  if (!pl || !c_row_ptr || !nnz_c || !workspace) return MAGNUS_INVALID_ARG;
+  return symbolic_impl(pl, c_row_ptr, nnz_c, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+int magnus_numeric(magnus_plan_t pl, const double* a_val, const double* b_val,
+                   const int64_t* c_row_ptr, int32_t* c_col, double* c_val, void* stream) {
+  return numeric_impl(pl, RowRange{}, a_val, b_val, c_row_ptr, c_col, c_val, nullptr, 0,
+                      (cudaStream_t)stream);
+}
+
+int magnus_numeric_ws(magnus_plan_t pl, const double* a_val, const double* b_val,
+                      const int64_t* c_row_ptr, int32_t* c_col, double* c_val, void* workspace,
+                      size_t workspace_bytes, void* stream) {
+  if (!workspace) return MAGNUS_INVALID_ARG;
+  return numeric_impl(pl, RowRange{}, a_val, b_val, c_row_ptr, c_col, c_val, workspace,
+                      workspace_bytes, (cudaStream_t)stream);
+}
+
+int magnus_numeric_rows(magnus_plan_t pl, int64_t row_begin, int64_t row_end, const double* a_val,
+                        const double* b_val, const int64_t* c_row_ptr, int32_t* c_col,
+                        double* c_val, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!pl) return MAGNUS_INVALID_ARG;
+  if (row_begin < 0 || row_end < row_begin || row_end > pl->A.n_rows) return MAGNUS_INVALID_ARG;
+  if (!pl->symbolic_done) return MAGNUS_NOT_SYMBOLIC;
+  if (row_begin == row_end) return MAGNUS_OK;
+  RowRange rr;
+  rr.on = true;
+  rr.r0 = row_begin;
+  rr.r1 = row_end;
+  // the slab's entries may be fewer than nnz(C): only NULL outputs of an
+  // empty C are accepted, as for magnus_numeric
+  return numeric_impl(pl, rr, a_val, b_val, c_row_ptr, c_col, c_val, workspace, workspace_bytes,
+                      (cudaStream_t)stream);
+}
+
+int magnus_workspace_size(magnus_plan_t pl, size_t* bytes) {
+  if (!pl || !bytes) return MAGNUS_INVALID_ARG;
+  size_t b = phase_bytes(pl, false, false);
+  b = std::max(b, phase_bytes(pl, true, false));
+  b = std::max(b, phase_bytes(pl, true, true));
+  *bytes = b;
+  return MAGNUS_OK;
+}
+
+}  // extern "C"
+
+
+extern "C" {
 
 // ---------------------------------------------------------------------------
 // Allocation-free numeric phase: the fine-level staging lives in this static
 // device array instead of the stream-ordered pool.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[MAGNUS_NOALLOC_SCRATCH_BYTES];
 
-// Device address of g_noalloc_scratch on the current device, looked up once
-// per device (host code may not use the symbol itself as a device pointer).
+// Device address of g_noalloc_scratch on the current device (host code may
+// not use the symbol itself as a device pointer).  Looked up on every call:
+// the lookup allocates nothing, and a cached address would dangle after the
+// device's context is destroyed and created again.
 static int noalloc_scratch_address(unsigned char** out) {
-  static std::mutex mu;
-  static void* addr[128] = {};
-  int dev = 0;
-  CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 128) return MAGNUS_INVALID_ARG;
-  std::lock_guard<std::mutex> lock(mu);
-  if (!addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) return cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e,
-                                                  "cudaGetSymbolAddress(g_noalloc_scratch)");
-    addr[dev] = p;
-  }
-  *out = reinterpret_cast<unsigned char*>(addr[dev]);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    return cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e,
+                     "cudaGetSymbolAddress(g_noalloc_scratch)");
+  *out = reinterpret_cast<unsigned char*>(p);
   return MAGNUS_OK;
+}
+
+// Fine blocks of the allocation-free numeric phase: as many staging slabs as
+// fit the fixed array (after its 512-byte counter area), at most one resident
+// wave; 0 without fine rows, -1 when the plan is refused.
+static int noalloc_fine_grid(magnus_plan_t pl) {
+  if (!pl->coarse_rows.empty()) return -1;
+  if (pl->fine_rows.empty()) return 0;
+  const size_t slab_bytes = (((size_t)pl->fine_slab * 12) + 255) & ~(size_t)255;
+  const size_t avail = MAGNUS_NOALLOC_SCRATCH_BYTES - 512;
+  if (slab_bytes > avail) return -1;
+  return (int)std::min<size_t>((size_t)pl->fine_grid_num, avail / slab_bytes);
 }
 
 int magnus_numeric_noalloc(magnus_plan_t pl, const double* a_val, const double* b_val,
@@ -913,15 +1179,12 @@ int magnus_numeric_noalloc(magnus_plan_t pl, const double* a_val, const double* 
   if (!pl->symbolic_done) return MAGNUS_NOT_SYMBOLIC;
   if ((pl->A.nnz > 0 && !a_val) || (pl->B.nnz > 0 && !b_val)) return MAGNUS_INVALID_ARG;
   if (pl->nnz_c > 0 && (!c_col || !c_val)) return MAGNUS_INVALID_ARG;
-  if (!pl->coarse_rows.empty()) return MAGNUS_SCRATCH_LIMIT;
   // The fine kernel stages one row per block in a slab of fine_slab products;
   // the fixed buffer holds the row counter and as many slabs as fit, and the
   // persistent grid is limited to that many blocks.
+  const int grid = noalloc_fine_grid(pl);
+  if (grid < 0) return MAGNUS_SCRATCH_LIMIT;
   const int shift = pl->shift_fine;
-  const size_t slab_bytes = (((size_t)pl->fine_slab * 12) + 255) & ~(size_t)255;
-  const size_t avail = MAGNUS_NOALLOC_SCRATCH_BYTES - 512;  // counter + alignment
-  if (!pl->fine_rows.empty() && slab_bytes > avail) return MAGNUS_SCRATCH_LIMIT;
-  const int grid = (int)std::min<size_t>((size_t)pl->fine_grid_num, avail / slab_bytes);
   unsigned char* scratch = nullptr;
   MAG_TRY(noalloc_scratch_address(&scratch));
   cudaStream_t s = (cudaStream_t)stream;
@@ -1015,6 +1278,13 @@ int magnus_plan_info(magnus_plan_t pl, magnus_plan_info_t* info) {
   info->key_bits32 = pl->key32[BIN_SORT256];
   info->n_batches_fine = pl->fine_rows.empty() ? 0 : 1;
   info->n_batches_coarse = pl->coarse_batches.empty() ? 0 : (int)pl->coarse_batches.size() - 1;
+  info->plan_bytes = pl->owned_bytes;
+  {
+    size_t ws = 0;
+    magnus_workspace_size(pl, &ws);
+    info->workspace_bytes = (int64_t)ws;
+  }
+  info->noalloc_fine_blocks = noalloc_fine_grid(pl);
   if (pl->big_stats) {
     unsigned long long h[3] = {0, 0, 0};
     CUDA_TRY(cudaMemcpy(h, pl->big_stats, sizeof(h), cudaMemcpyDeviceToHost));

@@ -51,7 +51,8 @@ class PlanInfo(ctypes.Structure):
                 ("dense_chunk_threshold", c_i32), ("key_bits32", c_i32),
                 ("n_batches_fine", c_i32), ("n_batches_coarse", c_i32),
                 ("coarse_dense_products", c_i64), ("coarse_dense_nnz", c_i64),
-                ("coarse_dense_buckets", c_i64)]
+                ("coarse_dense_buckets", c_i64), ("plan_bytes", c_i64),
+                ("workspace_bytes", c_i64), ("noalloc_fine_blocks", c_i32), ("reserved", c_i32)]
 
     def as_dict(self):
         d = {}
@@ -100,6 +101,11 @@ SIGNATURES = {
     "magnus_symbolic": (c_i32, [c_p, c_p, ctypes.POINTER(c_i64), c_p]),
     "magnus_numeric": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_p, c_p]),
     "magnus_numeric_noalloc": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_p, c_p]),
+    "magnus_workspace_size": (c_i32, [c_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "magnus_symbolic_ws": (c_i32, [c_p, c_p, ctypes.POINTER(c_i64), c_p, ctypes.c_size_t, c_p]),
+    "magnus_numeric_ws": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_p, c_p, ctypes.c_size_t, c_p]),
+    "magnus_numeric_rows": (c_i32, [c_p, c_i64, c_i64, c_p, c_p, c_p, c_p, c_p, c_p,
+                                    ctypes.c_size_t, c_p]),
     "magnus_free": (None, [c_p]),
     "magnus_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "magnus_last_cuda_error": (ctypes.c_char_p, []),
@@ -107,6 +113,8 @@ SIGNATURES = {
     "magnus_enable_timing": (c_i32, [c_p, ctypes.c_int]),
     "magnus_stage_times": (c_i32, [c_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "magnus_launch_count": (c_u64, []),
+    "magnus_device_memory": (c_i32, [ctypes.POINTER(ctypes.c_size_t),
+                                     ctypes.POINTER(ctypes.c_size_t)]),
     "magnus_plan_batched": (c_i32, [ctypes.POINTER(c_p), c_i32, ctypes.POINTER(CsrDesc),
                                     ctypes.POINTER(CsrDesc), ctypes.POINTER(Params), c_p]),
     "magnus_batch_layout": (c_i32, [c_p, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
@@ -184,6 +192,35 @@ def magnus_numeric_noalloc(plan: int, a_val: int, b_val: int, c_row_ptr: int, c_
            "magnus_numeric_noalloc")
 
 
+def magnus_workspace_size(plan: int) -> int:
+    n = ctypes.c_size_t()
+    _check(_lib().magnus_workspace_size(c_p(plan), ctypes.byref(n)), "magnus_workspace_size")
+    return n.value
+
+
+def magnus_symbolic_ws(plan: int, c_row_ptr: int, workspace: int, workspace_bytes: int,
+                       stream: int) -> int:
+    nnz = c_i64()
+    _check(_lib().magnus_symbolic_ws(c_p(plan), c_p(c_row_ptr), ctypes.byref(nnz), c_p(workspace),
+                                     workspace_bytes, c_p(stream)), "magnus_symbolic_ws")
+    return nnz.value
+
+
+def magnus_numeric_ws(plan: int, a_val: int, b_val: int, c_row_ptr: int, c_col: int, c_val: int,
+                      workspace: int, workspace_bytes: int, stream: int) -> None:
+    _check(_lib().magnus_numeric_ws(c_p(plan), c_p(a_val), c_p(b_val), c_p(c_row_ptr),
+                                    c_p(c_col), c_p(c_val), c_p(workspace), workspace_bytes,
+                                    c_p(stream)), "magnus_numeric_ws")
+
+
+def magnus_numeric_rows(plan: int, row_begin: int, row_end: int, a_val: int, b_val: int,
+                        c_row_ptr: int, c_col: int, c_val: int, workspace: int,
+                        workspace_bytes: int, stream: int) -> None:
+    _check(_lib().magnus_numeric_rows(c_p(plan), row_begin, row_end, c_p(a_val), c_p(b_val),
+                                      c_p(c_row_ptr), c_p(c_col), c_p(c_val), c_p(workspace),
+                                      workspace_bytes, c_p(stream)), "magnus_numeric_rows")
+
+
 def magnus_free(plan: int) -> None:
     if plan:
         _lib().magnus_free(c_p(plan))
@@ -207,6 +244,14 @@ def magnus_stage_times(plan: int) -> dict:
 
 def magnus_launch_count() -> int:
     return int(_lib().magnus_launch_count())
+
+
+def magnus_device_memory() -> tuple:
+    """(free device bytes, bytes the stream-ordered pool holds unused)."""
+    fr, idle = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(_lib().magnus_device_memory(ctypes.byref(fr), ctypes.byref(idle)),
+           "magnus_device_memory")
+    return fr.value, idle.value
 
 
 def magnus_chunk_model(m_c: int, smem_bytes: int, l2_bytes: int, resident_blocks: int) -> dict:
@@ -297,6 +342,25 @@ class Plan:
                        bv.data_ptr() if bv.numel() else 0, self.c_row_ptr.data_ptr(),
                        c_col.data_ptr(), c_val.data_ptr(), self.stream.cuda_stream)
         return c_col[:self.nnz_c], c_val[:self.nnz_c]
+
+    def numeric_rows(self, row_begin: int, row_end: int, c_col, c_val, a_val=None, b_val=None,
+                     workspace=None):
+        """magnus_numeric_rows: rows [row_begin, row_end) of C into c_col /
+        c_val (device tensors holding at least that slab's entries, written
+        from index 0).  ``workspace``: optional uint8 device tensor of at
+        least workspace_size() bytes (else scratch comes from the pool)."""
+        av = self.A.val if a_val is None else a_val
+        bv = self.B.val if b_val is None else b_val
+        ws = workspace.data_ptr() if workspace is not None else 0
+        wsb = workspace.numel() * workspace.element_size() if workspace is not None else 0
+        magnus_numeric_rows(self.handle, row_begin, row_end, av.data_ptr() if av.numel() else 0,
+                            bv.data_ptr() if bv.numel() else 0, self.c_row_ptr.data_ptr(),
+                            c_col.data_ptr() if c_col.numel() else 0,
+                            c_val.data_ptr() if c_val.numel() else 0, ws, wsb,
+                            self.stream.cuda_stream)
+
+    def workspace_size(self) -> int:
+        return magnus_workspace_size(self.handle)
 
     def info(self) -> dict:
         return magnus_plan_info(self.handle)
@@ -443,32 +507,37 @@ class BatchPlan:
             pass
 
 
-_BLOCK_STREAMS: dict = {}
+_COPY_STREAMS: dict = {}
 
 
-def _block_streams(dev, n: int):
-    """The row-block streams of spgemm_host, created once per device and
-    reused by later calls: the caching allocator keeps freed blocks per
-    stream, so new streams on every call could not reuse the previous call's
-    memory for C and would allocate (and release) it again."""
+def _copy_stream(dev):
+    """The copy-back stream of spgemm_host, created once per device and
+    reused by later calls (a new stream per call would create driver streams
+    without bound)."""
     import torch
     key = (dev.type, dev.index if dev.index is not None else torch.cuda.current_device())
-    have = _BLOCK_STREAMS.setdefault(key, [])
-    while len(have) < n:
-        have.append(torch.cuda.Stream(dev))
-    return have[:n]
+    if key not in _COPY_STREAMS:
+        _COPY_STREAMS[key] = torch.cuda.Stream(dev)
+    return _COPY_STREAMS[key]
 
 
 def spgemm_host(A, B, params: Params | None = None, blocks: int = 4, device="cuda",
-                out=None, pinned=None):
-    """C = A * B for host CSR operands with a host result, pipelined: A and B
-    are copied to the device, A's rows are cut into ``blocks`` row blocks
-    (balanced by nonzeros), each planned and computed on its own stream, and
-    each block's rows of C are copied back while the next blocks compute.
+                out=None, pinned=None, timing=None):
+    """C = A * B for host CSR operands with a host result.
+
+    A and B are copied to the device; one plan and the symbolic phase cover
+    the whole product; C.rowPtr is copied back and cuts C into ``blocks``
+    slabs of about equal entries.  Each slab is computed by
+    magnus_numeric_rows into one of two device slab buffers and copied back
+    to host memory while the next slab computes, so the device holds two
+    slabs of C, not all of it.
     ``pinned``: optional (A, B) pinned host copies (torch tensors
     (row_ptr, col, val)) to copy from; ``out``: optional pinned host tensors
-    (row_ptr, col, val) large enough for C (else allocated).  Returns
-    (row_ptr, col, val) host tensors (views of ``out`` when given)."""
+    (row_ptr, col, val) large enough for C (else allocated).  ``timing``:
+    optional dict that receives the device time of each part (ms, CUDA
+    events): h2d, plan_symbolic, rowptr_d2h, numeric (sum over slabs), d2h
+    (first slab copy start to last copy end), total.  Returns (row_ptr,
+    col, val) host tensors (views of ``out`` when given)."""
     import numpy as np
     import torch
     dev = torch.device(device)
@@ -477,6 +546,11 @@ def spgemm_host(A, B, params: Params | None = None, blocks: int = 4, device="cud
         pinned = (pa, pa if B is A else
                   tuple(torch.from_numpy(x).pin_memory() for x in (B.row_ptr, B.col, B.val)))
     main = torch.cuda.current_stream(dev)
+    cs = _copy_stream(dev)
+    ev = (lambda: torch.cuda.Event(enable_timing=True)) if timing is not None else \
+        (lambda: torch.cuda.Event())
+    t0 = ev()
+    t0.record(main)
     (arp, acol, aval), (brp, bcol, bval) = pinned
     dA = DeviceCSR(A.n_rows, A.n_cols, arp.to(dev, non_blocking=True),
                    acol.to(dev, non_blocking=True), aval.to(dev, non_blocking=True))
@@ -485,51 +559,68 @@ def spgemm_host(A, B, params: Params | None = None, blocks: int = 4, device="cud
     else:
         dB = DeviceCSR(B.n_rows, B.n_cols, brp.to(dev, non_blocking=True),
                        bcol.to(dev, non_blocking=True), bval.to(dev, non_blocking=True))
-    up = torch.cuda.Event()
-    up.record(main)
-    nb = max(1, min(blocks, A.n_rows))
-    targets = np.linspace(0, A.nnz, nb + 1)
-    cuts = np.unique(np.concatenate(([0], np.searchsorted(A.row_ptr, targets[1:-1]), [A.n_rows])))
-    streams = _block_streams(dev, len(cuts) - 1)
-    parts = []
-    base = 0
-
-    def copy_back(part, o_rp, o_col, o_val):
-        r0, r1, nnz, plan, col, val, s, off = part
-        with torch.cuda.stream(s):
-            # the block's row pointers, shifted by the entries before it
-            o_rp[r0:r1].copy_(plan.c_row_ptr[:r1 - r0] + off, non_blocking=True)
-            o_col[off:off + nnz].copy_(col, non_blocking=True)
-            o_val[off:off + nnz].copy_(val, non_blocking=True)
-
-    for k, s in enumerate(streams):
-        r0, r1 = int(cuts[k]), int(cuts[k + 1])
-        z0, z1 = int(A.row_ptr[r0]), int(A.row_ptr[r1])
-        s.wait_event(up)
-        with torch.cuda.stream(s):
-            Ak = DeviceCSR(r1 - r0, A.n_cols, dA.row_ptr[r0:r1 + 1] - z0, dA.col[z0:z1],
-                           dA.val[z0:z1])
-            plan = Plan(Ak, dB, params, s)
-            nnz = plan.symbolic()
-            col, val = plan.numeric()
-        part = (r0, r1, nnz, plan, col, val, s, base)
-        base += nnz
-        parts.append(part)
-        if out is not None:  # copy this block back while the next ones compute
-            copy_back(part, *out)
-    total = base
-    if out is None:
-        out = (torch.empty(A.n_rows + 1, dtype=torch.int64).pin_memory(),
-               torch.empty(max(total, 1), dtype=torch.int32).pin_memory(),
-               torch.empty(max(total, 1), dtype=torch.float64).pin_memory())
-        for part in parts:
-            copy_back(part, *out)
-    o_rp, o_col, o_val = out
-    for part in parts:
-        part[6].synchronize()
-        part[3].free()
-    o_rp[A.n_rows] = total
-    return o_rp, o_col[:total], o_val[:total]
+    t_h2d = ev()
+    t_h2d.record(main)
+    plan = Plan(dA, dB, params, main)
+    try:
+        nnz = plan.symbolic()
+        t_sym = ev()
+        t_sym.record(main)
+        if out is None:
+            out = (torch.empty(A.n_rows + 1, dtype=torch.int64).pin_memory(),
+                   torch.empty(max(nnz, 1), dtype=torch.int32).pin_memory(),
+                   torch.empty(max(nnz, 1), dtype=torch.float64).pin_memory())
+        o_rp, o_col, o_val = out
+        o_rp[:A.n_rows + 1].copy_(plan.c_row_ptr)
+        t_rp = ev()
+        t_rp.record(main)
+        rp = o_rp.numpy()
+        nb = max(1, min(blocks, A.n_rows))
+        cuts = np.searchsorted(rp[:A.n_rows + 1], np.linspace(0, nnz, nb + 1)[1:-1], side="left")
+        cuts = np.unique(np.concatenate(([0], cuts, [A.n_rows]))).astype(np.int64)
+        slabs = [(int(cuts[k]), int(cuts[k + 1])) for k in range(len(cuts) - 1)]
+        most = max(int(rp[r1] - rp[r0]) for r0, r1 in slabs)
+        bufs = [(torch.empty(max(most, 1), dtype=torch.int32, device=dev),
+                 torch.empty(max(most, 1), dtype=torch.float64, device=dev))
+                for _ in range(min(2, len(slabs)))]
+        copied = [None] * len(bufs)
+        marks = []
+        for k, (r0, r1) in enumerate(slabs):
+            col, val = bufs[k % len(bufs)]
+            if copied[k % len(bufs)] is not None:  # the buffer's previous slab is home
+                main.wait_event(copied[k % len(bufs)])
+            c0 = ev()
+            c0.record(main)
+            plan.numeric_rows(r0, r1, col, val)
+            c1 = ev()
+            c1.record(main)
+            cs.wait_event(c1)
+            e0, e1 = int(rp[r0]), int(rp[r1])
+            with torch.cuda.stream(cs):
+                d0 = ev()
+                d0.record(cs)
+                o_col[e0:e1].copy_(col[:e1 - e0], non_blocking=True)
+                o_val[e0:e1].copy_(val[:e1 - e0], non_blocking=True)
+                d1 = ev()
+                d1.record(cs)
+            copied[k % len(bufs)] = d1
+            marks.append((c0, c1, d0, d1))
+        for col, val in bufs:  # the copy stream reads them after the loop
+            col.record_stream(cs)
+            val.record_stream(cs)
+        cs.synchronize()
+        main.synchronize()
+        if timing is not None:
+            timing.update(
+                h2d=t0.elapsed_time(t_h2d), plan_symbolic=t_h2d.elapsed_time(t_sym),
+                rowptr_d2h=t_sym.elapsed_time(t_rp),
+                numeric=sum(c0.elapsed_time(c1) for c0, c1, _, _ in marks),
+                d2h=marks[0][2].elapsed_time(marks[-1][3]) if marks else 0.0,
+                total=t0.elapsed_time(marks[-1][3]) if marks else t0.elapsed_time(t_rp),
+                slabs=len(slabs))
+    finally:
+        plan.free()
+    return o_rp[:A.n_rows + 1], o_col[:nnz], o_val[:nnz]
 
 
 def spgemm(A: DeviceCSR, B: DeviceCSR, params: Params | None = None, stream=None) -> DeviceCSR:

@@ -8,9 +8,11 @@ resident until the request completes, and runs a loop that
   * whenever one of its CUDA streams is idle, takes the oldest pending
     requests (up to a product and request budget) and plans them as one
     batch (``BatchPlan``: every launch serves the rows of all of them),
-  * runs the symbolic phase, which gives the exact size of every C, and
-    allocates the outputs only if they fit the free device memory it may use
-    (otherwise the batch waits, planned, until earlier outputs are freed),
+  * plans a batch only if an estimate of its plan and operands fits the
+    device memory still free, then runs the symbolic phase, which gives the
+    exact size of every C, and allocates the outputs and the numeric
+    scratch only if they fit the free device memory (otherwise the batch
+    waits, planned, until earlier batches retire and free theirs),
   * enqueues the numeric phase and goes on with the next batch on another
     stream, so batches overlap on the device, and
   * retires a batch when its completion event fires: each request's latency
@@ -46,43 +48,67 @@ class Request:
 class Scheduler:
     """FIFO admission and batch formation (no GPU).
 
-    ``max_products`` / ``max_requests`` bound one batch; ``mem_budget`` bounds
-    the output bytes of all batches in flight."""
+    ``max_products`` / ``max_requests`` bound one batch.  Memory admission:
+    with ``mem_source`` (a callable returning the device bytes new work may
+    still use, read at every decision) a batch is admitted when what it
+    still has to allocate fits that figure; otherwise ``mem_budget`` bounds
+    the bytes of all batches in flight.  A batch is always admitted when
+    nothing is in flight (it may then fail with an out-of-memory error
+    instead of waiting forever)."""
 
-    def __init__(self, max_products: int, max_requests: int, mem_budget: int):
+    def __init__(self, max_products: int, max_requests: int, mem_budget: int | None = None,
+                 mem_source=None):
+        if mem_budget is None and mem_source is None:
+            raise ValueError("need a memory budget or a source of free memory")
         self.max_products = max_products
         self.max_requests = max_requests
         self.mem_budget = mem_budget
+        self.mem_source = mem_source
         self.pending: collections.deque = collections.deque()
         self.mem_in_use = 0
+        self.in_flight = 0
 
     def admit(self, reqs):
         for r in reqs:
             self.pending.append(r)
 
-    def next_batch(self):
-        """The oldest pending requests that fit one batch (at least one)."""
-        if not self.pending:
-            return []
+    def peek_batch(self):
+        """The requests next_batch would take, left pending."""
         out, prods = [], 0
-        while self.pending and len(out) < self.max_requests:
-            r = self.pending[0]
-            if out and prods + r.products > self.max_products:
+        for r in self.pending:
+            if len(out) >= self.max_requests or (out and prods + r.products > self.max_products):
                 break
-            out.append(self.pending.popleft())
+            out.append(r)
             prods += r.products
         return out
 
-    def reserve(self, nbytes: int) -> bool:
-        """Reserve output memory for a batch if it fits (a batch that alone
-        exceeds the budget is admitted when nothing else is in flight)."""
-        if self.mem_in_use + nbytes <= self.mem_budget or self.mem_in_use == 0:
-            self.mem_in_use += nbytes
+    def next_batch(self):
+        """The oldest pending requests that fit one batch (at least one)."""
+        out = self.peek_batch()
+        for _ in out:
+            self.pending.popleft()
+        return out
+
+    def fits(self, nbytes: int) -> bool:
+        """Whether work that still has to allocate ``nbytes`` may start now."""
+        if self.in_flight == 0:
             return True
-        return False
+        if self.mem_source is not None:
+            return nbytes <= self.mem_source()
+        return self.mem_in_use + nbytes <= self.mem_budget
+
+    def reserve(self, nbytes: int) -> bool:
+        """Admit a batch whose allocations still to come are ``nbytes`` if
+        they fit (a batch is admitted when nothing else is in flight)."""
+        if not self.fits(nbytes):
+            return False
+        self.mem_in_use += nbytes
+        self.in_flight += 1
+        return True
 
     def release(self, nbytes: int):
         self.mem_in_use -= nbytes
+        self.in_flight -= 1
 
 
 class _Flight:
@@ -94,20 +120,43 @@ class Server:
     ``executor.operands(req, stream) -> (A: DeviceCSR, B: DeviceCSR)``."""
 
     def __init__(self, executor, params=None, mode="batched", n_streams=2,
-                 max_products=1 << 31, max_requests=64, mem_budget=48 << 30,
-                 keep_results=False, device="cuda"):
+                 max_products=1 << 31, max_requests=64, mem_budget=None,
+                 mem_reserve=2 << 30, mem_source=None, keep_results=False, device="cuda"):
+        """Admission is by free device memory (``free_memory()``, less
+        ``mem_reserve`` bytes kept back), unless ``mem_source`` replaces that
+        figure or a fixed ``mem_budget`` of bytes in flight is given."""
         import torch
         self.torch = torch
         self.executor = executor
         self.params = params
         self.mode = mode
         self.device = torch.device(device)
+        self.mem_reserve = mem_reserve
         n = 1 if mode == "single" else max(1, n_streams)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(n)]
-        self.sched = Scheduler(max_products, 1 if mode == "single" else max_requests, mem_budget)
+        if mem_budget is None and mem_source is None:
+            mem_source = self.free_memory
+        self.sched = Scheduler(max_products, 1 if mode == "single" else max_requests,
+                               mem_budget=mem_budget, mem_source=mem_source)
         self.keep_results = keep_results
         self.results = {}
         self.executed_products = 0
+        self.plan_waits = 0       # batches whose planning waited for memory
+        self.launch_waits = 0     # planned batches whose launch waited for memory
+
+    def free_memory(self) -> int:
+        """Device bytes new work may use: free device memory, plus what the
+        library's stream-ordered pool and PyTorch's caching allocator hold
+        unused (each reuses its own first), less the reserve."""
+        from . import magnus
+        torch = self.torch
+        free, pool_idle = magnus.magnus_device_memory()
+        cached = torch.cuda.memory_reserved(self.device) - torch.cuda.memory_allocated(self.device)
+        return free + pool_idle + cached - self.mem_reserve
+
+    def _estimate(self, reqs) -> int:
+        est = getattr(self.executor, "estimate_bytes", None)
+        return sum(est(r) for r in reqs) if est is not None else 0
 
     # -- one batch -----------------------------------------------------------
     def _plan(self, reqs, stream, batch_id):
@@ -127,8 +176,12 @@ class Server:
                 plan = magnus.BatchPlan([a for a, _ in ops], [b for _, b in ops], self.params, stream)
                 offs = plan.symbolic()
         f.plan = plan
-        self.executed_products += plan.info()["n_interprod"]
-        f.nbytes = 12 * offs[-1] + 8 * (sum(a.n_rows for a, _ in ops) + 1)
+        info = plan.info()
+        self.executed_products += info["n_interprod"]
+        # still to allocate: C (row pointers, columns, values) and the
+        # numeric phase's scratch
+        f.nbytes = (12 * offs[-1] + 8 * (sum(a.n_rows for a, _ in ops) + 1)
+                    + info["workspace_bytes"])
         for i, r in enumerate(reqs):
             r.nnz = offs[i + 1] - offs[i]
         return f
@@ -166,6 +219,7 @@ class Server:
         flights = []
         waiting = None           # a planned batch whose outputs do not fit yet
         batch_id = 0
+        plan_blocked = False
         t0 = time.perf_counter()
         while nxt < len(order) or flights or waiting is not None or self.sched.pending:
             now = time.perf_counter() - t0
@@ -189,7 +243,14 @@ class Server:
                 flights.append(waiting)
                 waiting = None
                 progressed = True
-            if waiting is None and idle and self.sched.pending:
+            if (waiting is None and idle and self.sched.pending
+                    and not self.sched.fits(self._estimate(self.sched.peek_batch()))):
+                # planning the next batch waits for memory
+                if not plan_blocked:
+                    self.plan_waits += 1
+                plan_blocked = True
+            elif waiting is None and idle and self.sched.pending:
+                plan_blocked = False
                 reqs = self.sched.next_batch()
                 stream = idle.pop()
                 t = time.perf_counter() - t0
@@ -202,6 +263,7 @@ class Server:
                     flights.append(f)
                 else:
                     waiting = f
+                    self.launch_waits += 1
                 progressed = True
             if not progressed:
                 if flights:
@@ -232,6 +294,17 @@ class StencilTimesRandom:
         self.seed = seed
         self.b_kmin, self.b_kmax = b_kmin, b_kmax
         self.stencils = {}
+
+    def estimate_bytes(self, req) -> int:
+        """Device bytes planning a request takes before its C is sized: B
+        (about (b_kmin + b_kmax) / 2 entries per row, 12 B each, plus row
+        pointers), the plan's per-row arrays (about 48 B per row), its
+        segment table (8 B per nonzero of the stencil) and the sort order of
+        its products (at most 2 B per product)."""
+        k = req.payload[0]
+        n = k ** 3
+        nnz_b = n * (self.b_kmin + self.b_kmax) // 2
+        return 8 * (n + 1) + 12 * nnz_b + 48 * n + 8 * (3 * k - 2) ** 3 + 2 * req.products
 
     def operands(self, req, stream):
         from . import gen_device

@@ -26,7 +26,7 @@ def _check_product(bp, i, A, B):
     rp = C.row_ptr.cpu().numpy()
     col = C.col.cpu().numpy()
     val = C.val.cpu().numpy()
-    ref = oracle.spgemm(A, B)
+    ref = oracle.spgemm(A, B, threads=8)
     assert np.array_equal(rp, ref.row_ptr), "product %d row_ptr" % i
     assert np.array_equal(col, ref.col), "product %d columns" % i
     ok = values_close(val, ref.val, ref.abs)
@@ -168,6 +168,32 @@ def test_batched_device_drawn_workload_sampled():
     bp.numeric()
     torch.cuda.synchronize()
     for i in [0, 1, int(np.argmax(ns)), int(np.argmin(ns)), 50, 95]:
+        n = int(ns[i])
+        A = inputs.ragged_ctr(n, n, 2, 32, 0, 2 * i + 1)
+        B = inputs.ragged_ctr(n, n, 2, 32, 0, 2 * i + 2)
+        _check_product(bp, i, A, B)
+    bp.free()
+
+
+def test_batched_config_shape_first_wave():
+    """The batched workload exactly as the benchmark runs it: the first of
+    its four waves (products 0..1023 of 4096, n_i log-uniform in
+    [256, 65536], 2-32 nnz per row, drawn on the device from the same matrix
+    ids) in one batched plan with the automatic parameters; 130 products
+    (every eighth, the largest and the smallest) are checked against the
+    oracle entry by entry."""
+    import torch
+    from paper_2501_07056_gb300 import gen_device, magnus
+    ns = inputs.batched_sizes(4096, seed=0)[:1024]
+    As = [gen_device.ragged(int(n), int(n), 2, 32, 0, 2 * i + 1) for i, n in enumerate(ns)]
+    Bs = [gen_device.ragged(int(n), int(n), 2, 32, 0, 2 * i + 2) for i, n in enumerate(ns)]
+    bp = magnus.BatchPlan(As, Bs)
+    bp.symbolic()
+    bp.numeric()
+    torch.cuda.synchronize()
+    check = sorted(set(range(0, 1024, 8)) | {int(np.argmax(ns)), int(np.argmin(ns))})
+    assert len(check) >= 64
+    for i in check:
         n = int(ns[i])
         A = inputs.ragged_ctr(n, n, 2, 32, 0, 2 * i + 1)
         B = inputs.ragged_ctr(n, n, 2, 32, 0, 2 * i + 2)

@@ -2,14 +2,16 @@
 configuration bench.py times (automatic parameters).
 
   * uniform n = 2^24, 8 nnz/row, C = A*A (1.07e9 products): C.rowPtr is
-    compared with the oracle's precise prediction for every row; values are
-    compared on sampled rows; the row-sum invariant C*1 = A*(A*1) is checked
-    for every row.
+    compared with the oracle's precise prediction for every row, and every
+    entry of C (column and value) with the oracle's, in row slabs; the
+    row-sum invariant C*1 = A*(A*1) is checked for every row.
   * R-MAT scale 20, edge factor 16, C = A*A (2.09e10 products, nnz(C) about
-    1e10, 120 GB of output): the heaviest rows and random rows are compared
-    with the oracle; the row-sum invariant is checked for every row; nnz(C) is
-    checked against the band of Table 3 (9.94e9 for scale 20; the paper's
-    generator keeps duplicate edges, this one merges them).
+    1e10, 116 GB of output): every entry of C is compared with the oracle's
+    (the dense-accumulator form, linear in the products, in row slabs of
+    about 2^28 entries compared on the device); the row-sum invariant is
+    checked for every row; nnz(C) is checked against the band of Table 3
+    (9.94e9 for scale 20; the paper's generator keeps duplicate edges, this
+    one merges them).
 
 The row-sum check: in exact arithmetic sum_c C_ic = sum_j A_ij (sum_k B_jk).
 Both sides are computed in FP64 by different routes, so they may differ by
@@ -23,7 +25,6 @@ import pytest
 
 import oracle
 from paper_2501_07056_gb300 import inputs
-from tests._util import values_close
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -83,17 +84,37 @@ def _row_sum_check(dA, rp, val):
     assert bad == 0, "%d rows break the row-sum invariant" % bad
 
 
-def _sampled_rows(A, rp_host, col, val, rows):
-    ref = oracle.spgemm(A, A, rows=np.asarray(rows, np.int64), threads=THREADS)
-    for t, i in enumerate(rows):
-        s, e = int(rp_host[i]), int(rp_host[i + 1])
-        rc, rv, ra = ref.row(t)
-        assert e - s == rc.size, "row %d: nnz %d vs oracle %d" % (i, e - s, rc.size)
-        c = col[s:e].cpu().numpy()
-        v = val[s:e].cpu().numpy()
-        assert np.array_equal(c, rc), "row %d columns differ" % i
-        ok = values_close(v, rv, ra)
-        assert ok.all(), "row %d: %d values differ" % (i, int((~ok).sum()))
+def _compare_all_rows(A, rp_host, col, val, slab_entries, dense_oracle):
+    """Every row of C against the oracle, in row slabs of about
+    ``slab_entries`` entries: the oracle's slab is uploaded and compared on
+    the device (columns bit-exact, values within 1e-12 * max(|ref|,
+    sum |terms|)).  Returns the number of rows and entries compared."""
+    import torch
+    n = A.n_rows
+    r0, rows_done, entries_done = 0, 0, 0
+    while r0 < n:
+        r1 = int(np.searchsorted(rp_host, rp_host[r0] + slab_entries, side="right")) - 1
+        r1 = min(max(r1, r0 + 1), n)
+        rows = np.arange(r0, r1, dtype=np.int64)
+        fn = oracle.spgemm_dense if dense_oracle else oracle.spgemm
+        ref = fn(A, A, rows=rows, threads=THREADS)
+        e0, e1 = int(rp_host[r0]), int(rp_host[r1])
+        assert np.array_equal(ref.row_ptr + e0, rp_host[r0:r1 + 1]), "rows %d..%d" % (r0, r1)
+        if e1 > e0:
+            rc = torch.from_numpy(ref.col).cuda()
+            assert torch.equal(col[e0:e1], rc), "rows %d..%d: columns differ" % (r0, r1)
+            del rc
+            rv = torch.from_numpy(ref.val).cuda()
+            ra = torch.from_numpy(ref.abs).cuda()
+            bound = 1e-12 * torch.maximum(rv.abs(), ra)
+            bad = int(((val[e0:e1] - rv).abs() > bound).sum().item())
+            assert bad == 0, "rows %d..%d: %d values differ" % (r0, r1, bad)
+            del rv, ra, bound
+        rows_done += r1 - r0
+        entries_done += e1 - e0
+        del ref
+        r0 = r1
+    return rows_done, entries_done
 
 
 def test_uniform_2_24_full_size():
@@ -104,9 +125,8 @@ def test_uniform_2_24_full_size():
     cnt = oracle.symbolic(A, A, threads=THREADS)
     assert int(cnt.sum()) == nnz
     assert np.array_equal(np.diff(rp_host), cnt)
-    rng = np.random.default_rng(1)
-    rows = np.concatenate(([0, 1, A.n_rows - 1], rng.choice(A.n_rows, 3000, replace=False)))
-    _sampled_rows(A, rp_host, col, val, rows)
+    rows, entries = _compare_all_rows(A, rp_host, col, val, 1 << 27, dense_oracle=False)
+    assert rows == A.n_rows and entries == nnz  # every entry of C compared
     _row_sum_check(dA, rp, val)
 
 
@@ -120,11 +140,8 @@ def test_rmat20_full_size():
     # Table 3: 9,940,402,266 nonzeros of A^2 at scale 20 (duplicates kept there)
     assert 0.5 * 9.94e9 < nnz < 1.5 * 9.94e9
     rp_host = rp.cpu().numpy()
-    counts = np.diff(rp_host)
-    assert np.all(counts <= np.minimum(P, A.n_cols)) and np.all((counts > 0) == (P > 0))
-    heavy = np.argsort(P)[-6:]
-    rng = np.random.default_rng(2)
-    nonempty = np.nonzero(P)[0]
-    rows = np.concatenate((heavy, rng.choice(nonempty, 400, replace=False), [0, 1, 2]))
-    _sampled_rows(A, rp_host, col, val, np.unique(rows))
+    # every row, heavy rows (millions of products, the coarse level) included,
+    # against the dense-accumulator oracle (bit-identical to the sort one)
+    rows, entries = _compare_all_rows(A, rp_host, col, val, 1 << 28, dense_oracle=True)
+    assert rows == A.n_rows and entries == nnz
     _row_sum_check(dA, rp, val)

@@ -56,6 +56,64 @@ def test_results_alone_and_in_the_mix(mem_budget):
         assert r.nnz == r2.nnz == ref.row_ptr[-1]
 
 
+def test_config_grid_sizes_alone_and_in_the_mix():
+    """Requests at the served workload's own grid sizes, k in {16..96}: the
+    smallest and the largest k (884,736 rows, 2.3e8 products) share batches
+    with sizes between them; every result equals the oracle's and the one
+    computed alone."""
+    from paper_2501_07056_gb300 import serve
+    ks = [16, 96, 33, 80, 16, 57, 96, 24, 70, 45]
+    rng = np.random.default_rng(3)
+    descs = [dict(req=i, k=k, b_id=3_000_000 + i, gap=float(g))
+             for i, (k, g) in enumerate(zip(ks, rng.exponential(1.0, len(ks))))]
+    # all arrive at once: the first batches take requests in order, so k = 16
+    # and k = 96 share the first two batches
+    reqs = serve.make_requests(descs, seed=0, rate=1e12)
+    mix = serve.Server(serve.StencilTimesRandom(), mode="batched", n_streams=3,
+                       max_requests=4, keep_results=True)
+    mix.run(reqs)
+    assert mix.n_batches < len(reqs)
+    by = {r.rid: r for r in reqs}
+    assert by[0].batch == by[1].batch and by[4].batch == by[6].batch
+    alone = serve.Server(serve.StencilTimesRandom(), mode="single", keep_results=True)
+    reqs2 = serve.make_requests(descs, seed=0, rate=1e12)
+    alone.run(reqs2)
+    for r, r2 in zip(sorted(reqs, key=lambda q: q.rid), sorted(reqs2, key=lambda q: q.rid)):
+        ref = _oracle(r)
+        _same(mix.results[r.rid], ref)
+        _same(alone.results[r2.rid], ref)
+
+
+def test_waits_when_free_memory_is_short():
+    """A memory figure that never admits a second batch: batches run one at
+    a time (each planned only after the previous one retired), and every
+    result still equals the oracle's."""
+    from paper_2501_07056_gb300 import serve
+    reqs = _requests(12, rate=1e12)
+    srv = serve.Server(serve.StencilTimesRandom(), mode="batched", n_streams=3,
+                       max_requests=3, mem_source=lambda: 0, keep_results=True)
+    srv.run(reqs)
+    assert srv.n_batches >= 4 and srv.plan_waits >= 1
+    spans = {}
+    for r in reqs:
+        s0, d0 = spans.get(r.batch, (r.start, r.done))
+        spans[r.batch] = (min(s0, r.start), max(d0, r.done))
+    order = [spans[b] for b in sorted(spans)]
+    for (s0, d0), (s1, d1) in zip(order, order[1:]):
+        assert s1 >= d0  # the next batch started after the previous retired
+    for r in reqs:
+        _same(srv.results[r.rid], _oracle(r))
+
+
+def test_free_memory_figure():
+    import torch
+    from paper_2501_07056_gb300 import magnus, serve
+    free, idle = magnus.magnus_device_memory()
+    assert 0 < free <= torch.cuda.get_device_properties(0).total_memory and idle >= 0
+    srv = serve.Server(serve.StencilTimesRandom(), mem_reserve=0)
+    assert srv.free_memory() >= free
+
+
 def test_latency_accounting():
     from paper_2501_07056_gb300 import serve
     reqs = _requests(30, rate=200.0, k_lo=3, k_hi=8)

@@ -227,3 +227,69 @@ def test_uniform4096_nnz_band():
     expect = 4096 * (1 - (1 - 1 / 4096) ** 64)
     assert abs(cnt.mean() - expect) < 0.05
     assert cnt.max() <= 64
+
+
+# ---- the dense-accumulator form (Algorithm 1), used by the full-size checks
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_dense_form_against_dense_matmul(seed):
+    rng = np.random.default_rng(100 + seed)
+    n, k, m = rng.integers(1, 17, size=3)
+    A = random_pattern_csr(rng, n, k, rng.uniform(0.05, 0.9))
+    B = random_pattern_csr(rng, k, m, rng.uniform(0.05, 0.9))
+    res = oracle.spgemm_dense(A, B)
+    got, pat = _dense_of(res, B.n_cols)
+    pa = (A.to_dense() != 0) | _pattern(A)
+    pb = _pattern(B)
+    assert np.array_equal(pat, (pa.astype(np.int64) @ pb.astype(np.int64)) > 0)
+    abs_dense = np.abs(A.to_dense()) @ np.abs(B.to_dense())
+    assert np.all(values_close(got, A.to_dense() @ B.to_dense(), abs_dense, rtol=1e-13))
+
+
+def _pattern(M):
+    p = np.zeros((M.n_rows, M.n_cols), dtype=bool)
+    p[np.repeat(np.arange(M.n_rows), np.diff(M.row_ptr)), M.col] = True
+    return p
+
+
+def test_dense_form_order_and_zeros():
+    A = inputs.CSR(1, 3, np.array([0, 3]), np.array([0, 1, 2], np.int32),
+                   np.array([1.0, 1e16, -1e16]))
+    B = inputs.CSR(3, 1, np.array([0, 1, 2, 3]), np.array([0, 0, 0], np.int32), np.ones(3))
+    res = oracle.spgemm_dense(A, B)
+    assert res.col.tolist() == [0] and res.val[0] == 0.0  # traversal order
+    A = inputs.CSR(1, 2, np.array([0, 2]), np.array([0, 1], np.int32), np.array([1.0, -1.0]))
+    B = inputs.CSR(2, 3, np.array([0, 1, 2]), np.array([2, 2], np.int32), np.array([1.0, 1.0]))
+    res = oracle.spgemm_dense(A, B)
+    assert res.col.tolist() == [2] and res.val.tolist() == [0.0]  # structural zero kept
+    I = inputs.identity(50)
+    M = inputs.ragged(50, 50, 0, 9, seed=4)
+    for X, Y in ((M, I), (I, M)):
+        r = oracle.spgemm_dense(X, Y)
+        assert np.array_equal(r.row_ptr, M.row_ptr) and np.array_equal(r.col, M.col)
+        assert np.array_equal(r.val, M.val)
+
+
+@pytest.mark.parametrize("kind", ["rmat", "ragged", "uniform", "empty_rows"])
+def test_dense_form_bit_identical_to_sort_form(kind):
+    if kind == "rmat":
+        A = inputs.rmat(11, 16, seed=3)
+        B = A
+    elif kind == "ragged":
+        A = inputs.ragged(700, 900, 0, 30, seed=5, matrix_id=1)
+        B = inputs.ragged(900, 5000, 0, 30, seed=5, matrix_id=2)
+    elif kind == "uniform":
+        A = inputs.uniform(2000, 2000, 8, seed=6)
+        B = A
+    else:
+        A = inputs.ragged(300, 400, 0, 2, seed=7, matrix_id=1)
+        B = inputs.ragged(400, 300, 0, 3, seed=7, matrix_id=2)
+    rows = np.arange(A.n_rows, dtype=np.int64)[::3]
+    for rr in (None, rows):
+        r1 = oracle.spgemm(A, B, rows=rr, threads=3)
+        r2 = oracle.spgemm_dense(A, B, rows=rr, threads=3)
+        assert np.array_equal(r1.row_ptr, r2.row_ptr)
+        assert np.array_equal(r1.col, r2.col)
+        assert np.array_equal(r1.val.view(np.int64), r2.val.view(np.int64))
+        assert np.array_equal(r1.abs, r2.abs)

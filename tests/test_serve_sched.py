@@ -41,6 +41,32 @@ def test_memory_admission():
     assert s.mem_in_use == 0
 
 
+def test_admission_by_free_memory_waits_when_short():
+    free = {"bytes": 100}
+    s = Scheduler(max_products=10, max_requests=1, mem_source=lambda: free["bytes"])
+    assert s.fits(10 ** 12)        # nothing in flight: always admitted
+    assert s.reserve(80)           # the first batch (its memory is then allocated)
+    free["bytes"] = 20
+    assert not s.fits(50) and not s.reserve(50)   # short of memory: waits
+    assert s.reserve(20)           # fits what is left
+    free["bytes"] = 0
+    assert not s.reserve(1)
+    s.release(80)
+    free["bytes"] = 80             # the retired batch's memory is free again
+    assert s.reserve(50)
+    s.release(20)
+    s.release(50)
+    assert s.in_flight == 0 and s.fits(10 ** 12)
+
+
+def test_peek_matches_next_batch():
+    s = Scheduler(max_products=100, max_requests=3, mem_budget=1)
+    s.admit(_reqs([40, 40, 40, 10]))
+    peek = [r.rid for r in s.peek_batch()]
+    assert peek == [r.rid for r in s.next_batch()] == [0, 1]
+    assert [r.rid for r in s.peek_batch()] == [2, 3]
+
+
 def test_stencil_products_closed_form():
     # with every B row of length L, products = L * nnz(stencil) = L (3k-2)^3
     for k in (1, 2, 5):
