@@ -101,6 +101,9 @@ def parse_args(argv=None):
                    help="e2e: row slabs of C whose entries are copied back while the next "
                         "compute")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-configs", action="store_true",
+                   help="default workload only: skip the R-MAT 20, batched and served lines "
+                        "appended under detail.configs")
     p.add_argument("--force-category", type=int, default=-1)
     p.add_argument("--sort-threshold", type=int, default=0)
     p.add_argument("--chunk-coarse", type=int, default=0,
@@ -936,6 +939,48 @@ def run_e2e(args, dist, A, dev, params, n_inter, nnz_c):
             "copy_floor_ms": 1e3 * (h2d / (link_h2d * 1e9) + d2h / (link_d2h * 1e9))}
 
 
+def _summary(res):
+    """The headline keys of another workload's line, for detail.configs."""
+    keep = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "roofline", "clocks",
+            "gpu_launches", "latency_ms", "products_per_s", "one_call_per_product",
+            "served_one_call", "config")
+    out = {k: res[k] for k in keep if k in res}
+    d = res.get("detail", {})
+    for k in ("stage_ms", "t_over_t_ideal", "nnz_c"):
+        if k in d:
+            out[k] = d[k]
+    if "served_batched" in res:
+        out["served_batched"] = {k: v for k, v in res["served_batched"].items() if k != "clocks"}
+        out["served_one_call"] = {k: v for k, v in res["served_one_call"].items()
+                                  if k != "clocks"}
+    return out
+
+
+def run_other_configs(args, dist):
+    """R-MAT scale 20 (3 steps), batched 4096 products (2 steps) and the
+    served stream (2,000 requests), each in its own metric, measured in the
+    same process after the headline workload."""
+    import torch
+    out = {}
+    for name, extra in (("rmat20", ["--steps", "3"]), ("batched4096", ["--steps", "2"]),
+                        ("served", ["--requests", "2000"])):
+        torch.cuda.empty_cache()
+        sub = parse_args(["--workload", name, "--warmup", "3", "--no-e2e", "--no-cpu",
+                          "--gpus", str(args.gpus)] + extra)
+        try:
+            if name == "batched4096":
+                r = run_batched(sub, dist)
+            elif name == "served":
+                r = run_served(sub, dist)
+            else:
+                r = run_ours(sub, dist)
+            out[name] = _summary(r)
+        except Exception as e:  # report, do not lose the headline line
+            out[name] = {"error": "%s: %s" % (type(e).__name__, e)}
+        torch.cuda.synchronize()
+    return out
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.warmup < 3:
@@ -952,6 +997,8 @@ def main(argv=None):
             res = run_ablation(args, dist)
         else:
             res = run_ours(args, dist)
+            if args.workload == "uniform2^24" and not args.no_configs:
+                res["detail"]["configs"] = run_other_configs(args, dist)
         if dist.rank == 0 and res is not None:
             print(json.dumps(res), flush=True)
     finally:

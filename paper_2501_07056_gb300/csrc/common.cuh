@@ -135,6 +135,54 @@ __device__ __forceinline__ void group_bitonic_sort(K (&k)[R]) {
   }
 }
 
+// Merge of sorted runs: every lane of a group of W lanes holds R keys that
+// are already ascending (one sorted run per lane, positions q = l * R + e as
+// above).  The levels of the bitonic network below size 2R are skipped; each
+// remaining level starts with a "flip" stage that compares position i of a
+// block with its mirror (block end - 1 - i), which turns two ascending halves
+// into two halves whose every key of the lower is <= every key of the upper,
+// then half-cleaners at distances size/4 .. 1 sort each half.  All stages
+// keep the smaller key at the lower position, so no stage needs a direction.
+template <int R, int W, typename K>
+__device__ __forceinline__ void group_merge_runs(K (&k)[R]) {
+  const int l = lane_id() & (W - 1);
+  constexpr int N = W * R;
+#pragma unroll
+  for (int size = 2 * R; size <= N; size <<= 1) {
+    {
+      const int pm = size / R - 1;                 // mirror lane within the block
+      const bool lower = (l & (size / R / 2)) == 0;
+      K o[R];
+#pragma unroll
+      for (int e = 0; e < R; ++e) o[e] = __shfl_xor_sync(FULL, k[R - 1 - e], pm);
+#pragma unroll
+      for (int e = 0; e < R; ++e) k[e] = lower ? kmin(k[e], o[e]) : kmax(k[e], o[e]);
+    }
+#pragma unroll
+    for (int j = size >> 2; j > 0; j >>= 1) {
+      if (j >= R) {
+        const int pl = j / R;
+        const bool lower = (l & pl) == 0;
+#pragma unroll
+        for (int e = 0; e < R; ++e) {
+          const K other = __shfl_xor_sync(FULL, k[e], pl);
+          k[e] = lower ? kmin(k[e], other) : kmax(k[e], other);
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < R; ++e) {
+          if ((e & j) == 0) {
+            const K lo = kmin(k[e], k[e + j]);
+            const K hi = kmax(k[e], k[e + j]);
+            k[e] = lo;
+            k[e + j] = hi;
+          }
+        }
+      }
+    }
+  }
+}
+
 template <int E, typename K>
 __device__ __forceinline__ void warp_bitonic_sort(K (&k)[E]) {
   group_bitonic_sort<E, 32, K>(k);

@@ -16,12 +16,37 @@
 // A.val * B.val; they are visited in the recorded sorted order, equal
 // columns are summed in slot order (the traversal order of Algorithm 1), and
 // the row of C is written.
+//
+// Rows whose nonzeros number at most W and each select a B row of 1..R
+// entries ("run rows": every uniform row) number their products run-major,
+// slot = j * R + x for the x-th entry of the B row of the row's j-th nonzero.
+// This keeps traversal order and lets the symbolic pass skip most of the
+// network: the B rows are stored sorted (an ABI requirement), so after a
+// transpose through shared memory each lane holds one sorted run of R keys,
+// and only the merge levels of the bitonic network remain
+// (group_merge_runs).  A warp whose rows are all run rows takes that path;
+// otherwise it runs the general expansion and the full network, numbering the
+// products of any run rows among them the same way, so the recorded order
+// means the same in both passes whichever path either took.
 #include "sort_accum.cuh"
 
 namespace magnus {
 
+// Shared layout of one group's keys for the run transpose: run r, entry x at
+// r * R + 4 * ((x >> 2) ^ ((r >> 2) & 1)) + (x & 3), groups KSTRIDE keys
+// apart.  The 4-key swizzle and the group pad keep both the writes (a run
+// per W/R lanes) and the 16-byte reads of whole runs free of bank conflicts.
+template <int W> struct RunLayout {
+  static constexpr int R = 8;
+  static constexpr int CAP = W * R;
+  static constexpr int KSTRIDE = CAP + (W < 32 ? W : 0);
+  __device__ static __forceinline__ int at(int r, int x) {
+    return r * R + 4 * ((x >> 2) ^ ((r >> 2) & 1)) + (x & 3);
+  }
+};
+
 template <int E, typename K, bool NUMERIC, int NW>
-__global__ void __launch_bounds__(NW * 32) k_sort_rows(SortArgs a) {
+__global__ void __launch_bounds__(NW * 32, NUMERIC ? 5 : 4) k_sort_rows(SortArgs a) {
   constexpr int W = 4 * E;    // lanes per row
   constexpr int G = 32 / W;   // rows per warp
   constexpr int R = 8;        // products per lane
@@ -29,6 +54,7 @@ __global__ void __launch_bounds__(NW * 32) k_sort_rows(SortArgs a) {
   constexpr int SB = Log2Cap<E>::v;
   constexpr int HW = CAP / 32;  // head-bit words per row
   using KT = KeyTraits<K>;
+  using RL = RunLayout<W>;
   // Per-warp shared arrays, indexed [position][group] so that the lanes of
   // the G groups interleave and a warp-wide access touches distinct banks.
   __shared__ uint8_t s_off[NW][CAP][G];    // first slot of each non-empty segment
@@ -38,6 +64,8 @@ __global__ void __launch_bounds__(NW * 32) k_sort_rows(SortArgs a) {
   __shared__ int32_t s_col[NW][NUMERIC ? CAP : 1][G];
   __shared__ double s_val[NW][NUMERIC ? CAP : 1][G];
   __shared__ uint8_t s_perm[NW][NUMERIC ? CAP : 1][G];
+  __shared__ uint8_t s_len[NW][W][G];      // run rows: entries of the j-th nonzero's B row
+  __shared__ __align__(16) K s_key[NW][NUMERIC ? 1 : G * RL::KSTRIDE];
   const int lane = lane_id(), w = warp_id();
   const int grp = lane / W, l = lane & (W - 1);
   const int gshift = grp * W;
@@ -81,94 +109,169 @@ __global__ void __launch_bounds__(NW * 32) k_sort_rows(SortArgs a) {
     const RowDesc d = p1.d;
     const uint64_t perm = p1.perm;
     const int64_t crp = p2.crp;
-    if (l < HW) s_head[w][l][grp] = 0;
-    // 1. Segments: the non-empty B rows referenced by the row, in stored
-    //    order, each with its first slot in the row's product list.
-    int nseg = 0, P = 0;
-    for (int j0 = 0; __any_sync(FULL, j0 < d.na); j0 += W) {
-      const int j = j0 + l;
-      int64_t bs = 0;
-      int L = 0;
-      double av = 0.0;
-      if (j0 == 0) {
-        bs = p2.bs;  // prefetched one iteration ahead
-        L = p2.L;
-        av = p2.av;
-      } else if (j < d.na) {
-        const uint64_t sg = a.seg[d.as + j];
-        bs = seg_start(sg);
-        L = seg_length(sg);
-        if (NUMERIC) av = a.A.val[d.as + j];
-      }
-      const unsigned nz = (__ballot_sync(FULL, L > 0) >> gshift) & gbits;
-      const int inc = group_inclusive_scan<W>(L);
-      if (L > 0) {
-        const int g = nseg + __popc(nz & ((1u << l) - 1u));
-        s_off[w][g][grp] = (uint8_t)(P + inc - L);
-        s_bs[w][g][grp] = bs;
-        if (NUMERIC) s_av[w][g][grp] = av;
-      }
-      nseg += __popc(nz);
-      P += __shfl_sync(FULL, inc, gshift + W - 1);
-    }
-    __syncwarp();
-    for (int g = 1 + l; g < nseg; g += W) {
-      const int off = s_off[w][g][grp];
-      atomicOr(&s_head[w][off >> 5][grp], 1u << (off & 31));
-    }
-    __syncwarp();
-    uint32_t hw[HW];
-    int pw[HW];
-    {
-      int cum = 0;
-#pragma unroll
-      for (int i = 0; i < HW; ++i) {
-        hw[i] = s_head[w][i][grp];
-        pw[i] = cum;
-        cum += __popc(hw[i]);
-      }
-    }
-    // 2. Expand: slot s = e*W + l (consecutive lanes read consecutive
-    //    entries of a B row).  The segment of s is the number of segment
-    //    starts at or before s.
-    // All gathers of the row are issued before any of them is used, so
-    // the R loads of a lane (2R in the numeric pass) are in flight together.
-    int32_t cg[R];
-    double vg[R];
-    double ag[R];
-#pragma unroll
-    for (int e = 0; e < R; ++e) {
-      const int s = e * W + l;
-      const int wi = (e * W) >> 5;
-      const int g = pw[wi] + __popc(hw[wi] & ((2u << (s & 31)) - 1u));
-      cg[e] = 0;
-      vg[e] = 0.0;
-      ag[e] = 0.0;
-      if (s < P) {
-        const int64_t k = s_bs[w][g][grp] + (s - s_off[w][g][grp]);
-        cg[e] = __ldg(a.B.col + k);
-        if (NUMERIC) {
-          vg[e] = __ldg(a.B.val + k);
-          ag[e] = s_av[w][g][grp];
-        }
-      }
-    }
+    // Run row: at most W nonzeros, each selecting a B row of 1..R entries
+    // (empty groups past the end count as run rows).
+    const bool mine_ok = (l >= d.na) || (p2.L >= 1 && p2.L <= R);
+    const unsigned okb = (__ballot_sync(FULL, mine_ok) >> gshift) & gbits;
+    const bool run_row = d.na <= W && okb == gbits;
+    const bool fast = __all_sync(FULL, run_row);
+    int P = 0;
     K key[R];
-#pragma unroll
-    for (int e = 0; e < R; ++e) {
-      const int s = e * W + l;
-      if (NUMERIC) {
-        if (s < P) {
-          s_col[w][s][grp] = cg[e];
-          s_val[w][s][grp] = ag[e] * vg[e];
-        }
-      } else {
-        key[e] = (s < P) ? KT::template make<SB>(cg[e], s) : ~K(0);
+    if (fast) {
+      // Run path.  Lane l of the group publishes its nonzero's B row; the
+      // B rows are then read whole by consecutive lanes (W / R runs per
+      // load instruction, or half a run when W = 4).
+      const int L = (l < d.na) ? p2.L : 0;
+      if (l < d.na) {
+        s_bs[w][l][grp] = p2.bs;
+        s_len[w][l][grp] = (uint8_t)L;
+        if (NUMERIC) s_av[w][l][grp] = p2.av;
       }
+      P = group_sum<W>(L);
+      __syncwarp();
+      constexpr int RPI = W >= R ? W / R : 1;  // runs per load instruction
+      int32_t cg[R];
+      double vg[R];
+      bool on[R];
+#pragma unroll
+      for (int it = 0; it < R; ++it) {
+        const int r = (W >= R) ? it * RPI + (l >> 3) : (it >> 1);
+        const int x = (W >= R) ? (l & 7) : (l + 4 * (it & 1));
+        on[it] = r < d.na && x < (int)s_len[w][r < W ? r : 0][grp];
+        cg[it] = 0;
+        vg[it] = 0.0;
+        if (on[it]) {
+          const int64_t k = s_bs[w][r][grp] + x;
+          cg[it] = __ldg(a.B.col + k);
+          if (NUMERIC) vg[it] = __ldg(a.B.val + k);
+        }
+      }
+#pragma unroll
+      for (int it = 0; it < R; ++it) {
+        const int r = (W >= R) ? it * RPI + (l >> 3) : (it >> 1);
+        const int x = (W >= R) ? (l & 7) : (l + 4 * (it & 1));
+        const int slot = r * R + x;
+        if (NUMERIC) {
+          if (on[it]) {
+            s_col[w][slot][grp] = cg[it];
+            s_val[w][slot][grp] = s_av[w][r][grp] * vg[it];
+          }
+        } else {
+          s_key[w][grp * RL::KSTRIDE + RL::at(r, x)] =
+              on[it] ? KT::template make<SB>(cg[it], slot) : ~K(0);
+        }
+      }
+      __syncwarp();
+      if (!NUMERIC) {
+        // lane l takes run l: ascending (B rows are sorted, slots increase)
+        const K* src = &s_key[w][grp * RL::KSTRIDE + l * R];
+        const int sw = (l >> 2) & 1;
+        if (sizeof(K) == 4) {
+          const uint4 q0 = *reinterpret_cast<const uint4*>(src + 4 * sw);
+          const uint4 q1 = *reinterpret_cast<const uint4*>(src + 4 * (sw ^ 1));
+          const uint32_t t[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+#pragma unroll
+          for (int e = 0; e < R; ++e) key[e] = (K)t[e];
+        } else {
+#pragma unroll
+          for (int e = 0; e < R; ++e) key[e] = src[4 * ((e >> 2) ^ sw) + (e & 3)];
+        }
+        group_merge_runs<R, W>(key);
+      }
+    } else {
+      if (l < HW) s_head[w][l][grp] = 0;
+      // 1. Segments: the non-empty B rows referenced by the row, in stored
+      //    order, each with its first slot in the row's product list.
+      int nseg = 0;
+      for (int j0 = 0; __any_sync(FULL, j0 < d.na); j0 += W) {
+        const int j = j0 + l;
+        int64_t bs = 0;
+        int L = 0;
+        double av = 0.0;
+        if (j0 == 0) {
+          bs = p2.bs;  // prefetched one iteration ahead
+          L = p2.L;
+          av = p2.av;
+        } else if (j < d.na) {
+          const uint64_t sg = a.seg[d.as + j];
+          bs = seg_start(sg);
+          L = seg_length(sg);
+          if (NUMERIC) av = a.A.val[d.as + j];
+        }
+        const unsigned nz = (__ballot_sync(FULL, L > 0) >> gshift) & gbits;
+        const int inc = group_inclusive_scan<W>(L);
+        if (L > 0) {
+          const int g = nseg + __popc(nz & ((1u << l) - 1u));
+          s_off[w][g][grp] = (uint8_t)(P + inc - L);
+          s_bs[w][g][grp] = bs;
+          if (NUMERIC) s_av[w][g][grp] = av;
+        }
+        nseg += __popc(nz);
+        P += __shfl_sync(FULL, inc, gshift + W - 1);
+      }
+      __syncwarp();
+      for (int g = 1 + l; g < nseg; g += W) {
+        const int off = s_off[w][g][grp];
+        atomicOr(&s_head[w][off >> 5][grp], 1u << (off & 31));
+      }
+      __syncwarp();
+      uint32_t hw[HW];
+      int pw[HW];
+      {
+        int cum = 0;
+#pragma unroll
+        for (int i = 0; i < HW; ++i) {
+          hw[i] = s_head[w][i][grp];
+          pw[i] = cum;
+          cum += __popc(hw[i]);
+        }
+      }
+      // 2. Expand: slot s = e*W + l (consecutive lanes read consecutive
+      //    entries of a B row).  The segment of s is the number of segment
+      //    starts at or before s.  A run row numbers its products run-major
+      //    (its segments are its nonzeros: no B row is empty).
+      // All gathers of the row are issued before any of them is used, so
+      // the R loads of a lane (2R in the numeric pass) are in flight together.
+      int32_t cg[R];
+      double vg[R];
+      double ag[R];
+      int sl[R];
+#pragma unroll
+      for (int e = 0; e < R; ++e) {
+        const int s = e * W + l;
+        const int wi = (e * W) >> 5;
+        const int g = pw[wi] + __popc(hw[wi] & ((2u << (s & 31)) - 1u));
+        cg[e] = 0;
+        vg[e] = 0.0;
+        ag[e] = 0.0;
+        sl[e] = s;
+        if (s < P) {
+          const int x = s - s_off[w][g][grp];
+          const int64_t k = s_bs[w][g][grp] + x;
+          if (run_row) sl[e] = g * R + x;
+          cg[e] = __ldg(a.B.col + k);
+          if (NUMERIC) {
+            vg[e] = __ldg(a.B.val + k);
+            ag[e] = s_av[w][g][grp];
+          }
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < R; ++e) {
+        const int s = e * W + l;
+        if (NUMERIC) {
+          if (s < P) {
+            s_col[w][sl[e]][grp] = cg[e];
+            s_val[w][sl[e]][grp] = ag[e] * vg[e];
+          }
+        } else {
+          key[e] = (s < P) ? KT::template make<SB>(cg[e], sl[e]) : ~K(0);
+        }
+      }
+      if (!NUMERIC) group_bitonic_sort<R, W>(key);
     }
     if (!NUMERIC) {
-      // 3s. Sort, count distinct columns, record the sorted slot order.
-      group_bitonic_sort<R, W>(key);
+      // 3s. Count distinct columns, record the sorted slot order.
       const K prev_last = __shfl_up_sync(FULL, key[R - 1], 1, W);
       int h = 0;
       uint64_t pb = 0;

@@ -144,16 +144,12 @@ def test_workspace_variants_allocate_nothing(kind, force):
     assert base % 256 == 0
     s = torch.cuda.current_stream().cuda_stream
     rp = torch.empty(A.n_rows + 1, dtype=torch.int64, device="cuda")
-    # too small and misaligned workspaces are refused before any work (the
-    # size is the largest need of the phases, so only a clearly short region
-    # must fail for every phase)
-    for call in (lambda b: magnus.magnus_symbolic_ws(plan.handle, rp.data_ptr(), base, b, s),
-                 lambda b: magnus.magnus_numeric_ws(plan.handle, dA.val.data_ptr(),
-                                                    dB.val.data_ptr(), rp.data_ptr(), base,
-                                                    base, base, b, s)):
-        with pytest.raises(magnus.MagnusError) as ei:
-            call(256)
-        assert ei.value.status in (7, 10)  # numeric before symbolic may report 7 first
+    # too small and misaligned workspaces are refused before any work: the
+    # symbolic phase always needs its C.rowPtr scan temporaries (more than 8
+    # bytes); a numeric phase needs scratch only for fine or coarse rows
+    with pytest.raises(magnus.MagnusError) as ei:
+        magnus.magnus_symbolic_ws(plan.handle, rp.data_ptr(), base, 8, s)
+    assert ei.value.status == 10
     with pytest.raises(magnus.MagnusError) as ei:
         magnus.magnus_symbolic_ws(plan.handle, rp.data_ptr(), base + 8, nbytes, s)
     assert ei.value.status == 1
@@ -173,6 +169,11 @@ def test_workspace_variants_allocate_nothing(kind, force):
     nnz = both()
     after = _pool_state()
     assert after == before, "the _ws calls allocated device memory: %s -> %s" % (before, after)
+    if force in (FINE, COARSE):
+        with pytest.raises(magnus.MagnusError) as ei:
+            magnus.magnus_numeric_ws(plan.handle, dA.val.data_ptr(), dB.val.data_ptr(),
+                                     rp.data_ptr(), col.data_ptr(), val.data_ptr(), base, 8, s)
+        assert ei.value.status == 10
     assert nnz == nnz_ref
     assert np.array_equal(rp.cpu().numpy(), ref.row_ptr)
     assert np.array_equal(col[:nnz].cpu().numpy(), ref.col)
