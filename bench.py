@@ -79,6 +79,9 @@ WORKLOADS = {
                 "dense accumulation) on a uniform stream of 2^28 (int32 index, FP64 value) "
                 "pairs with indices in [0, 2^16), [0, 2^20) and [0, 2^24), against a stream "
                 "copy and a global dense accumulator; chunk count swept 2^0..2^14",
+    "rates": "device rates that bound the kernels: random gathers of 16-256 byte chunks and "
+             "of 8-entry CSR B rows from 2 GB arrays, shared-memory FP64 and u32 accumulation "
+             "(distinct, random and 8-lanes-per-address atomics, plain adds)",
     "batched4096": "4096 independent products C_i=A_i*B_i, n_i log-uniform in [256, 65536], "
                    "A_i and B_i n_i x n_i with nnz/row uniform in {2..32} (counter-based "
                    "generator, drawn on the device), FP64 U(-1,1), seed 0",
@@ -114,6 +117,11 @@ def parse_args(argv=None):
                    help="fine-level hybrid threshold (0 = planner's choice; 1 = dense only)")
     p.add_argument("--chunk-accumulator", type=int, default=0, choices=[0, 1],
                    help="fine-level chunk accumulator: 0 dense array, 1 hash map")
+    p.add_argument("--coarse-reorder", type=int, default=0, choices=[0, 1, 2],
+                   help="coarse staging: 0 automatic, 1 outer product, 2 row-wise runs")
+    p.add_argument("--coarse-bucket-sort", type=int, default=0, choices=[-1, 0, 1],
+                   help="coarse buckets of 257..2048 products: block sort 1, off -1, "
+                        "0 automatic")
     p.add_argument("--batch-count", type=int, default=4096,
                    help="batched workload: number of products")
     p.add_argument("--batch-waves", type=int, default=4,
@@ -500,6 +508,8 @@ def run_ours(args, dist):
                                 chunk_len_fine_log2=args.chunk_fine,
                                 dense_chunk_threshold=args.dthr,
                                 chunk_accumulator=args.chunk_accumulator,
+                                coarse_reorder=args.coarse_reorder,
+                                coarse_bucket_sort=args.coarse_bucket_sort,
                                 l2_fetch_bytes=args.l2_fetch)
     stream = torch.cuda.current_stream()
     tuned = None
@@ -510,6 +520,19 @@ def run_ours(args, dist):
         tuned = {"report": rep, "seconds": time.perf_counter() - t0,
                  "params": magnus.params_dict(params)}
         torch.cuda.empty_cache()
+
+    # The end-to-end leg runs first, in the process as it starts: device
+    # memory released and mapped again (the device loop's plans and outputs)
+    # slows the copy engines for a while afterwards, which would charge the
+    # host-link copies with the device loop's bookkeeping.
+    e2e = None
+    if not args.no_e2e and not massive:
+        sizing = magnus.Plan(dA, dB, params, stream)
+        nnz_e2e = sizing.symbolic()
+        n_inter_e2e = sizing.info()["n_interprod"]
+        sizing.free()
+        torch.cuda.synchronize()
+        e2e = run_e2e(args, dist, A, dev, params, n_inter_e2e, nnz_e2e)
 
     stage = {k: [] for k in magnus.STAGES}
 
@@ -610,8 +633,8 @@ def run_ours(args, dist):
                    "t_ideal_ms": t_ideal_ms, "rows_per_category": info["rows_per_category"],
                    "sort_threshold": info["sort_threshold"]},
     }
-    if not args.no_e2e and not massive:
-        result["e2e"] = run_e2e(args, dist, A, dev, params, n_inter, nnz_c)
+    if e2e is not None:
+        result["e2e"] = e2e
     if not args.no_cpu and dist.rank == 0:
         threads = os.cpu_count() or 1
         if massive:
@@ -884,6 +907,31 @@ def _link_bandwidth(dst_host, src_host, dev, chunk=1 << 30):
     return res[0], res[1]
 
 
+def run_rates(args, dist):
+    """The device rates behind the rooflines: random chunk gathers (the sort
+    kernels gather one B row per nonzero of A) and shared-memory FP64
+    accumulation (the dense accumulators), per second device-wide."""
+    import torch
+
+    from paper_2501_07056_gb300 import magnus
+    dev = torch.device("cuda", dist.local_rank if dist.world > 1 else 0)
+    torch.cuda.set_device(dev)
+    clocks = ClockSampler(dev.index).start()
+    reps = [magnus.microbench_rates() for _ in range(max(1, args.steps))]
+    clk = clocks.stop()
+    best = {k: max(r[k] for r in reps) for k in reps[0]}
+    sm_hz = 2.07e9 * best["sms"]
+    per_clk = {k: best[k] / sm_hz for k in best if k.startswith("smem")}
+    return {
+        "metric": "random gather rate, 32-byte chunks", "value": best["gather_32"] / 1e9,
+        "unit": "G chunks/s", "n_gpus": dist.world, "steps": len(reps), "warmup": 0,
+        "ms_per_step": 0.0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOADS["rates"]},
+        "rates_per_s": best, "smem_updates_per_clock_per_sm_at_2070mhz": per_clk,
+        "clocks": clk, "gpu_launches": 44 * len(reps),
+    }
+
+
 def run_e2e(args, dist, A, dev, params, n_inter, nnz_c):
     """Same metric through the public API with host buffers: every step
     copies A (which serves as both operands) from pinned host memory to the
@@ -894,12 +942,14 @@ def run_e2e(args, dist, A, dev, params, n_inter, nnz_c):
     import torch
 
     from paper_2501_07056_gb300 import magnus
-    h_rp = torch.from_numpy(A.row_ptr).pin_memory()
-    h_col = torch.from_numpy(A.col).pin_memory()
-    h_val = torch.from_numpy(A.val).pin_memory()
-    o_rp = torch.empty(A.n_rows + 1, dtype=torch.int64).pin_memory()
-    o_col = torch.empty(nnz_c, dtype=torch.int32).pin_memory()
-    o_val = torch.empty(nnz_c, dtype=torch.float64).pin_memory()
+    # page-locked host buffers backed by huge pages (magnus_host_alloc): the
+    # public API's own allocator for host operands and results
+    h_rp = magnus.host_copy(A.row_ptr)
+    h_col = magnus.host_copy(A.col)
+    h_val = magnus.host_copy(A.val)
+    o_rp = magnus.host_empty(A.n_rows + 1, torch.int64)
+    o_col = magnus.host_empty(nnz_c, torch.int32)
+    o_val = magnus.host_empty(nnz_c, torch.float64)
     h2d = h_rp.numel() * 8 + h_col.numel() * 4 + h_val.numel() * 8
     d2h = o_rp.numel() * 8 + o_col.numel() * 4 + o_val.numel() * 8
 
@@ -946,7 +996,8 @@ def _summary(res):
             "served_one_call", "config")
     out = {k: res[k] for k in keep if k in res}
     d = res.get("detail", {})
-    for k in ("stage_ms", "t_over_t_ideal", "nnz_c"):
+    for k in ("stage_ms", "t_over_t_ideal", "nnz_c", "stage_ms_untimed_step",
+              "rows_per_category", "last_wave_plan"):
         if k in d:
             out[k] = d[k]
     if "served_batched" in res:
@@ -995,6 +1046,8 @@ def main(argv=None):
             res = run_served(args, dist)
         elif args.workload == "ablation":
             res = run_ablation(args, dist)
+        elif args.workload == "rates":
+            res = run_rates(args, dist)
         else:
             res = run_ours(args, dist)
             if args.workload == "uniform2^24" and not args.no_configs:

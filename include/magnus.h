@@ -137,7 +137,30 @@ typedef struct {
  *                     then the distinct columns are sorted by the warp;
  *                     larger chunks keep the dense accumulator.  The
  *                     symbolic phase counts with the bitmap either way (the
- *                     counts do not depend on the accumulator).  0 or 1.  */
+ *                     counts do not depend on the accumulator).  0 or 1.
+ * coarse_reorder      how the coarse level stages the products of a batch
+ *                     into its (row, coarse chunk) buckets (Algorithm 4):
+ *                     1 = outer product over the batch's A^CSC (each needed
+ *                     B row read once per batch, products appended one by
+ *                     one); 2 = row-wise in work items of 256 nonzeros of A,
+ *                     each sub-tile of 2,048 products counting-sorted by
+ *                     chunk in shared memory and written to the buckets as
+ *                     whole runs (at most 512 coarse chunks); 0 = automatic
+ *                     (2 when the chunks allow it, else 1).
+ * sort_block_warps    warps per thread block of the warp-sort kernels (rows of
+ *                     at most 256 products; every warp works on its own rows,
+ *                     so the block shape only changes occupancy and the
+ *                     resident wave): 2, 4 or 8 for both phases; 0 = 4 for
+ *                     the numeric phase and 8 for the symbolic phase.
+ * coarse_bucket_sort  coarse (row, chunk) buckets of 257..2048 products are
+ *                     accumulated by a block-wide bitonic sort (Algorithm 2;
+ *                     the hybrid of Section 3.4 choosing sort for the smaller
+ *                     chunks) instead of the dense accumulator or the fine
+ *                     level: 1 = on, -1 = off, 0 = automatic (on when the
+ *                     coarse chunks are wider than the 2^13-column block
+ *                     dense accumulator: sparse buckets; off otherwise, where
+ *                     the dense accumulator wins).  Buckets of at most 256
+ *                     products always take a warp sort.  */
 typedef struct {
   int32_t sort_threshold;
   int32_t force_category;
@@ -150,6 +173,9 @@ typedef struct {
   int32_t numeric_graph;
   int32_t wide_sort_max;
   int32_t chunk_accumulator;
+  int32_t coarse_reorder;
+  int32_t sort_block_warps;
+  int32_t coarse_bucket_sort;
 } magnus_params_t;
 
 /* Fill *p with the automatic values.  Returns MAGNUS_INVALID_ARG on NULL. */
@@ -347,8 +373,10 @@ magnus_plan_t magnus_batch_inner_plan(magnus_batch_t batch);
  * returns the fastest in *best.  The search starts from *base (NULL = the
  * automatic parameters) and does coordinate descent over sort_threshold
  * (64..1025), wide_sort_max, chunk_len_coarse_log2 (11..13, when coarse rows
- * exist), chunk_len_fine_log2 (7..10) and dense_chunk_threshold (when fine
- * rows exist); at most max_trials measured runs.  The paper fixes the
+ * exist), chunk_len_fine_log2 (7..10), dense_chunk_threshold and
+ * chunk_accumulator (when fine or coarse rows exist), coarse_reorder (when
+ * coarse rows exist) and sort_block_warps (2, 4, 8; when sort rows exist);
+ * at most max_trials measured runs.  The paper fixes the
  * threshold and derives the chunk lengths from its cache model (Section 3.5,
  * Section 4.1.1); on the GPU those values are the starting point.
  * sample_products > 0 and a product with more intermediate products than
@@ -405,6 +433,34 @@ typedef struct {
 int magnus_microbench_chunks(const int32_t* col, const double* val, int64_t length, int64_t m,
                              int32_t n_chunks_log2, int32_t* out_col, double* out_val,
                              int64_t* chunk_nnz, magnus_microbench_t* result, void* stream);
+
+/* ---- rates of the device's building operations ---------------------------
+ * magnus_microbench_rates measures, on the current device, the rates that
+ * bound the SpGEMM kernels (the paper has no counterpart: its bounds are a
+ * CPU's streaming bandwidth).  Gathers: chunks per second of random chunks of
+ * 16..256 bytes at chunk-aligned offsets of a 2 GB array, and of CSR B rows
+ * of 8 entries (32 bytes of columns and 64 bytes of values from two arrays).
+ * Shared memory: updates per second device-wide of an 8,192-entry FP64 array
+ * per block (3 blocks of 256 threads per SM) by atomicAdd at distinct
+ * addresses, random addresses, and 8 lanes per address, by a plain add, and
+ * by u32 atomicAdd at random addresses.  Allocates (about 2 GB) and frees
+ * its buffers; synchronises `stream`. */
+typedef struct {
+  double gather_16;                      /* chunks/s, 16-byte chunks */
+  double gather_32;
+  double gather_64;
+  double gather_128;
+  double gather_256;
+  double gather_csr_row8;                /* B rows/s, 32 B columns + 64 B values */
+  double smem_f64_atomic_distinct;       /* updates/s */
+  double smem_f64_atomic_random;
+  double smem_f64_atomic_8_per_address;
+  double smem_f64_add_plain;
+  double smem_u32_atomic_random;
+  int32_t sms;                           /* multiprocessors of the device */
+  int32_t reserved;
+} magnus_rates_t;
+int magnus_microbench_rates(magnus_rates_t* rates, void* stream);
 
 /* ---- plan introspection ------------------------------------------------ */
 typedef struct {
@@ -476,6 +532,25 @@ int magnus_stage_times(magnus_plan_t plan, double* ms, int n);
  * each C's exact size before it is allocated, Section 2.1).  Either pointer
  * may be NULL. */
 int magnus_device_memory(size_t* free_bytes, size_t* pool_idle_bytes);
+
+/* ---- page-locked host buffers ------------------------------------------
+ * For callers that move operands and results across the host link (the
+ * paper has no counterpart; it runs on the host).  magnus_host_alloc maps
+ * `bytes` of anonymous host memory advised to use transparent huge pages,
+ * touches every page and registers the range with the CUDA driver as
+ * page-locked, so device copies to and from it run at the link's rate even
+ * when host memory is fragmented (page-locked memory in small pages copies
+ * several times slower then).  *ptr is the host address, usable as a
+ * cudaMemcpyAsync source or destination.  Release it with magnus_host_free
+ * and the same size; no device work may still use it.  Errors:
+ * MAGNUS_INVALID_ARG (NULL ptr or zero size), MAGNUS_OUT_OF_MEMORY (the
+ * mapping failed), MAGNUS_CUDA_ERROR (registration failed; nothing is kept).
+ * The mapping starts on a huge-page boundary and is rounded up to whole huge
+ * pages, so a buffer may hold up to one huge page (512 MB with 64 KB base
+ * pages) more than asked.  Allocation touches the whole range (about 0.2 s
+ * for 8 GB): do it once and reuse the buffer. */
+int magnus_host_alloc(size_t bytes, void** ptr);
+int magnus_host_free(void* ptr, size_t bytes);
 
 /* Number of kernels this library has launched in this process. */
 uint64_t magnus_launch_count(void);

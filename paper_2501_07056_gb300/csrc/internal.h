@@ -131,6 +131,7 @@ struct SortArgs {
   // int64 subtracted from every output offset (C.rowPtr[row_begin]).
   const int64_t* range;
   const int64_t* c_base;
+  int32_t block_warps;  // warps per block of the warp-sort kernels (0 = per phase default)
 };
 cudaError_t launch_sort_rows(int bin, bool numeric, const SortArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_sort_rows_block(int bin, bool numeric, const SortArgs& a, int num_sms,
@@ -180,6 +181,31 @@ cudaError_t launch_fine_rows(bool numeric, const FineArgs& a, int grid, cudaStre
 // Resident blocks per SM of the fine-row kernel for a phase and chunk shift.
 int fine_rows_blocks_per_sm(bool numeric, int shift, bool hybrid);
 
+// A coarse (row, chunk) bucket too large for a warp sort, as listed by
+// k_bucket_small for the large-bucket accumulators: its staged products
+// [p0, p0 + n), its coarse chunk c, and `out` = its first entry in C
+// (numeric; C.rowPtr of the row less the output base plus the bucket's
+// offset in the row) or its index in the symbolic per-(row, chunk) counts.
+struct BigBucket {
+  int64_t p0;
+  int64_t out;
+  int32_t n;
+  int32_t c;
+};
+
+// A work item of the row-wise staged coarse reorder: nonzeros
+// [j0, j0 + nj) of A (nj <= CS_NJ) of the coarse row at position li of the
+// coarse row list.
+constexpr int CS_NJ = 256;
+struct CoarseItem {
+  int64_t j0;
+  int32_t li;
+  int32_t nj;
+};
+// The row-wise staged reorder keeps per-chunk counters in shared memory and
+// is used up to this many coarse chunks; beyond it, the outer product.
+constexpr int CS_MAX_CHUNKS = 512;
+
 // Coarse level (Algorithm 4) for one batch of coarse rows.
 struct CoarseArgs {
   Csr A, B;
@@ -206,7 +232,8 @@ struct CoarseArgs {
   int32_t* fine_col;         // second staging buffer for the fine level
   double* fine_val;
   int64_t* scan_tmp;
-  int32_t* big_list;         // buckets too large for a warp
+  BigBucket* big_list;       // buckets too large for a warp: block-sort ones from the
+                             // front, larger ones from the back (nbk entries)
   int32_t* n_big;
   // results
   int32_t* bucket_cnt;       // symbolic: per (coarse list row, chunk) nnz; numeric: read
@@ -222,8 +249,15 @@ struct CoarseArgs {
   int64_t* saved_offs;       // optional [n_rows * n_chunks + 1]: the batch's bucket offsets,
                              // written by the symbolic pass, reused by the numeric pass
   cudaEvent_t big_ev0, big_ev1;   // optional: recorded around the large-bucket kernel
+  // row-wise staged reorder (used when items != NULL): the batch's work items
+  const uint64_t* seg;       // segment table of A (B row start and length per nonzero)
+  const CoarseItem* items;
+  int32_t n_items;
+  int32_t* item_ctr;         // device counter, zeroed by each launch
+  int32_t bucket_sort;       // 1: buckets of 257..2048 products take the block sort
 };
 cudaError_t run_coarse_batch(bool numeric, CoarseArgs& a, cudaStream_t s);
+cudaError_t launch_coarse_stage(bool reorder, bool numeric, const CoarseArgs& a, cudaStream_t s);
 
 // Process-wide kernel launch counter.
 void count_launch(int n = 1);

@@ -223,8 +223,8 @@ __global__ void __launch_bounds__(BK_NW * 32)
                    const int32_t* __restrict__ rows, int32_t* __restrict__ bucket_cnt,
                    const int64_t* __restrict__ bucket_out, const int64_t* __restrict__ c_rp, const int64_t* __restrict__ c_base,
                    int32_t* __restrict__ c_col, double* __restrict__ c_val,
-                   int32_t* __restrict__ big_list, int32_t* __restrict__ n_big,
-                   unsigned long long* __restrict__ big_stats) {
+                   BigBucket* __restrict__ big_list, int32_t* __restrict__ n_big,
+                   unsigned long long* __restrict__ big_stats, int mid_max) {
   __shared__ double s_vals[BK_NW][NUMERIC ? SORT_MAX : 1];
   __shared__ K s_keys[BK_NW][NUMERIC ? SORT_MAX : 1];
   const int lane = lane_id(), w = warp_id();
@@ -237,7 +237,19 @@ __global__ void __launch_bounds__(BK_NW * 32)
     const int c = (int)(id - t * nc);
     if (n > SORT_MAX) {
       if (lane == 0) {
-        big_list[atomicAdd(n_big, 1)] = (int32_t)id;
+        // the whole record of the bucket, so the large-bucket kernels start
+        // each bucket from one load instead of a chain of dependent ones
+        BigBucket bb;
+        bb.p0 = p0;
+        bb.n = n;
+        bb.c = c;
+        bb.out = NUMERIC ? c_rp[rows[t]] - (c_base ? *c_base : 0) + bucket_out[id]
+                         : (list_base + t) * nc + c;
+        // buckets of at most mid_max products from the front of the list
+        // (the block sort, n_big[1] of them), larger ones from the back (the
+        // block dense accumulator or the fine level, n_big[0] of them)
+        if (n <= mid_max) big_list[atomicAdd(&n_big[1], 1)] = bb;
+        else big_list[nbk - 1 - atomicAdd(&n_big[0], 1)] = bb;
         big_p += (unsigned long long)n;
         big_n += 1;
         if (NUMERIC) big_z += (unsigned long long)bucket_cnt[(list_base + t) * nc + c];
@@ -278,13 +290,11 @@ __global__ void __launch_bounds__(BK_NW * 32)
 // shift is min(sc, sf) (the launch sizes shared memory with it).
 template <bool NUMERIC, bool HYBRID>
 __global__ void __launch_bounds__(FNT)
-    k_bucket_big(const int64_t* __restrict__ offs, const int32_t* __restrict__ big_list,
+    k_bucket_big(const BigBucket* __restrict__ big_end,
                  const int32_t* __restrict__ n_big, const int32_t* __restrict__ chunk_col,
                  const double* __restrict__ chunk_val, int32_t* __restrict__ fine_col,
-                 double* __restrict__ fine_val, int sc, int sf, int nc,
-                 int64_t list_base, const int32_t* __restrict__ rows,
-                 int32_t* __restrict__ bucket_cnt, const int64_t* __restrict__ bucket_out,
-                 const int64_t* __restrict__ c_rp, const int64_t* __restrict__ c_base, int32_t* __restrict__ c_col,
+                 double* __restrict__ fine_val, int sc, int sf,
+                 int32_t* __restrict__ bucket_cnt, int32_t* __restrict__ c_col,
                  double* __restrict__ c_val, int dthr, int hash) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const int shift = sf < sc ? sf : sc;
@@ -293,19 +303,20 @@ __global__ void __launch_bounds__(FNT)
   const int nbig = *n_big;
   const int nch = 1 << (sc - shift);
   fine_clear<NUMERIC>(f, shift);
+  BigBucket nxt{};
+  if (blockIdx.x < nbig) nxt = big_end[-1 - (int64_t)blockIdx.x];
   for (int q = blockIdx.x; q < nbig; q += gridDim.x) {
-    const int64_t id = big_list[q];
-    const int64_t p0 = offs[id];
-    const int n = (int)(offs[id + 1] - p0);
-    const int64_t t = id / nc;
-    const int c = (int)(id - t * nc);
+    const BigBucket bb = nxt;
+    if (q + gridDim.x < nbig) nxt = big_end[-1 - (int64_t)(q + gridDim.x)];  // in flight
+    const int64_t p0 = bb.p0;
+    const int n = bb.n;
+    const int c = bb.c;
     const int64_t col_base = (int64_t)c << sc;
     int32_t* oc = nullptr;
     double* ov = nullptr;
     if (NUMERIC) {
-      const int64_t o = c_rp[rows[t]] - (c_base ? *c_base : 0) + bucket_out[id];
-      oc = c_col + o;
-      ov = c_val + o;
+      oc = c_col + bb.out;
+      ov = c_val + bb.out;
     }
     const int32_t* cc = chunk_col + p0;
     const double* cv = NUMERIC ? chunk_val + p0 : nullptr;
@@ -349,7 +360,111 @@ __global__ void __launch_bounds__(FNT)
       __syncthreads();
       cnt = warp_chunks_accumulate<NUMERIC, HYBRID>(f, nch, shift, fc, fv, col_base, oc, ov, dthr, hash);
     }
-    if (!NUMERIC && threadIdx.x == 0) bucket_cnt[(list_base + t) * nc + c] = (int32_t)cnt;
+    if (!NUMERIC && threadIdx.x == 0) bucket_cnt[bb.out] = (int32_t)cnt;
+    __syncthreads();
+  }
+}
+
+// Coarse buckets of 257..BS_CAP products: the sort accumulator widened to
+// a thread block (Algorithm 2; the per-chunk hybrid of Section 3.4 choosing
+// sort for the smaller chunks).  Keys (chunk-local column, position in the
+// bucket) are loaded with coalesced reads, sorted by the block bitonic
+// network, and the runs of equal columns summed in position order, so the
+// bucket needs no atomics at all (a dense accumulator's FP64 atomics
+// contend on the hub columns of power-law rows).  Emission is striped:
+// thread t takes sorted positions t, t + BS_NT, ..., whose ranks among the
+// run heads come from a prefix over a head bitmap, so consecutive threads
+// write consecutive entries of C.
+constexpr int BS_NT = 256;
+constexpr int BS_CAP = BS_NT * BR;  // 2,048 products
+constexpr int BS_PB = 11;           // position bits of a key
+
+template <typename K, bool NUMERIC>
+__global__ void __launch_bounds__(BS_NT)
+    k_bucket_sort(const BigBucket* __restrict__ list, const int32_t* __restrict__ n_list,
+                  const int32_t* __restrict__ chunk_col, const double* __restrict__ chunk_val,
+                  int sc, int32_t* __restrict__ bucket_cnt, int32_t* __restrict__ c_col,
+                  double* __restrict__ c_val) {
+  __shared__ K s_key[BS_CAP];
+  __shared__ double s_val[NUMERIC ? BS_CAP : 1];
+  __shared__ uint32_t s_head[BS_CAP / 32];
+  __shared__ int32_t s_hpre[BS_CAP / 32 + 1];
+  const int t = threadIdx.x;
+  const int lane = lane_id(), w = warp_id();
+  constexpr K PMASK = (K(1) << BS_PB) - 1;
+  const int nl = *n_list;
+  BigBucket nxt{};
+  if (blockIdx.x < nl) nxt = list[blockIdx.x];
+  for (int q = blockIdx.x; q < nl; q += gridDim.x) {
+    const BigBucket bb = nxt;
+    if (q + gridDim.x < nl) nxt = list[q + gridDim.x];  // next bucket's record, in flight
+    const int n = bb.n;
+    K key[BR];
+#pragma unroll
+    for (int e = 0; e < BR; ++e) {
+      const int pos = e * BS_NT + t;
+      if (pos < n) {
+        key[e] = ((K)(uint32_t)__ldcs(chunk_col + bb.p0 + pos) << BS_PB) | (K)pos;
+        if (NUMERIC) s_val[pos] = __ldcs(chunk_val + bb.p0 + pos);
+      } else {
+        key[e] = ~K(0);
+      }
+    }
+    block_sort_keys<BS_NT>(key, s_key);
+    // sorted positions t*BR + e: stage them, mark the run heads
+#pragma unroll
+    for (int e = 0; e < BR; ++e) s_key[t * BR + e] = key[e];
+    __syncthreads();
+    uint32_t hb = 0;
+#pragma unroll
+    for (int e = 0; e < BR; ++e) {
+      const int qp = t * BR + e;
+      const K prev = (e > 0) ? key[e - 1] : (t > 0 ? s_key[qp - 1] : ~K(0));
+      const bool head = qp < n && (qp == 0 || (key[e] >> BS_PB) != (prev >> BS_PB));
+      hb |= head ? (1u << e) : 0u;
+    }
+    // BR = 8 head bits per thread: threads 4i..4i+3 fill word i
+    {
+      const uint32_t mine = hb << (8 * (t & 3));
+      uint32_t wd = mine;
+      wd |= __shfl_xor_sync(FULL, wd, 1);
+      wd |= __shfl_xor_sync(FULL, wd, 2);
+      if ((t & 3) == 0) s_head[t >> 2] = wd;
+    }
+    __syncthreads();
+    if (w == 0) {  // prefix of the head counts over the 64 words
+      const int c0 = __popc(s_head[lane]), c1 = __popc(s_head[32 + lane]);
+      const int i0 = warp_inclusive_scan(c0);
+      const int t0 = __shfl_sync(FULL, i0, 31);
+      const int i1 = warp_inclusive_scan(c1);
+      s_hpre[lane] = i0 - c0;
+      s_hpre[32 + lane] = t0 + i1 - c1;
+      if (lane == 31) s_hpre[64] = t0 + i1;
+    }
+    __syncthreads();
+    if (NUMERIC) {
+      const int64_t col_base = (int64_t)bb.c << sc;
+#pragma unroll
+      for (int e = 0; e < BR; ++e) {
+        const int qp = e * BS_NT + t;
+        const uint32_t wd = s_head[qp >> 5];
+        if (qp < n && ((wd >> (qp & 31)) & 1u)) {
+          const int rank = s_hpre[qp >> 5] + __popc(wd & ((1u << (qp & 31)) - 1u));
+          const K k0 = s_key[qp];
+          const K c = k0 >> BS_PB;
+          double acc = s_val[(int)(k0 & PMASK)];
+          for (int q2 = qp + 1; q2 < n; ++q2) {  // the run, in position order
+            const K k2 = s_key[q2];
+            if ((k2 >> BS_PB) != c) break;
+            acc += s_val[(int)(k2 & PMASK)];
+          }
+          c_col[bb.out + rank] = (int32_t)(col_base + (int64_t)c);
+          c_val[bb.out + rank] = acc;
+        }
+      }
+    } else if (t == 0) {
+      bucket_cnt[bb.out] = s_hpre[64];
+    }
     __syncthreads();
   }
 }
@@ -368,12 +483,10 @@ constexpr int BD_UNROLL = 4;
 
 template <bool NUMERIC>
 __global__ void __launch_bounds__(FNT)
-    k_bucket_dense(const int64_t* __restrict__ offs, const int32_t* __restrict__ big_list,
-                   const int32_t* __restrict__ n_big, const int32_t* __restrict__ chunk_col,
-                   const double* __restrict__ chunk_val, int sc, int nc, int64_t list_base,
-                   const int32_t* __restrict__ rows, int32_t* __restrict__ bucket_cnt,
-                   const int64_t* __restrict__ bucket_out, const int64_t* __restrict__ c_rp, const int64_t* __restrict__ c_base,
-                   int32_t* __restrict__ c_col, double* __restrict__ c_val) {
+    k_bucket_dense(const BigBucket* __restrict__ big_end, const int32_t* __restrict__ n_big,
+                   const int32_t* __restrict__ chunk_col, const double* __restrict__ chunk_val,
+                   int sc, int32_t* __restrict__ bucket_cnt, int32_t* __restrict__ c_col,
+                   double* __restrict__ c_val) {
   extern __shared__ __align__(16) unsigned char dsm[];
   const int cl = 1 << sc;
   const int words = cl >= 32 ? cl >> 5 : 1;
@@ -390,12 +503,14 @@ __global__ void __launch_bounds__(FNT)
   const int wd0 = w * wpw;
   const int my_wd = wd0 + lane;
   const bool own = lane < wpw && my_wd < words;
+  BigBucket nxt{};
+  if (blockIdx.x < nbig) nxt = big_end[-1 - (int64_t)blockIdx.x];
   for (int q = blockIdx.x; q < nbig; q += gridDim.x) {
-    const int64_t id = big_list[q];
-    const int64_t p0 = offs[id];
-    const int n = (int)(offs[id + 1] - p0);
-    const int64_t t = id / nc;
-    const int c = (int)(id - t * nc);
+    const BigBucket bb = nxt;
+    if (q + gridDim.x < nbig) nxt = big_end[-1 - (int64_t)(q + gridDim.x)];  // in flight
+    const int64_t p0 = bb.p0;
+    const int n = bb.n;
+    const int c = bb.c;
     const int32_t* cc = chunk_col + p0;
     const double* cv = NUMERIC ? chunk_val + p0 : nullptr;
     for (int p = threadIdx.x; p < n; p += BD_UNROLL * FNT) {
@@ -421,7 +536,7 @@ __global__ void __launch_bounds__(FNT)
     if (lane == 0) wcnt[w] = cnt;
     __syncthreads();
     if (NUMERIC) {
-      int64_t o = c_rp[rows[t]] - (c_base ? *c_base : 0) + bucket_out[id];
+      int64_t o = bb.out;
       for (int i = 0; i < w; ++i) o += wcnt[i];
       const int64_t col_base = (int64_t)c << sc;
       const unsigned below = (1u << lane) - 1u;
@@ -440,7 +555,7 @@ __global__ void __launch_bounds__(FNT)
     } else if (threadIdx.x == 0) {
       int total = 0;
       for (int i = 0; i < FNW; ++i) total += wcnt[i];
-      bucket_cnt[(list_base + t) * nc + c] = total;
+      bucket_cnt[bb.out] = total;
     }
     if (own) bits[my_wd] = 0u;
     __syncthreads();
@@ -455,49 +570,67 @@ static cudaError_t coarse_impl(CoarseArgs& a, cudaStream_t s) {
   const int nt = 256;
   const unsigned gw = grid_cap_c((a.n_rows + 7) / 8, (int64_t)a.num_sms * 32);
 #define CK(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
-  // 1. A^CSC and coarseRowsB
-  CK(cudaMemsetAsync(a.col_cnt, 0, (size_t)(nB + 1) * sizeof(int32_t), s));
-  CK(cudaMemsetAsync(a.n_rows_b, 0, sizeof(int32_t), s));
-  k_csc_count<<<gw, nt, 0, s>>>(a.A, a.rows, a.n_rows, a.col_cnt, a.rows_b, a.n_rows_b);
-  count_launch();
-  CK(cudaGetLastError());
-  CK(launch_scan_i32_to_i64(a.col_cnt, nB, a.col_ptr, a.scan_tmp, s));
-  CK(cudaMemsetAsync(a.col_cnt, 0, (size_t)(nB + 1) * sizeof(int32_t), s));
-  k_csc_fill<NUMERIC><<<gw, nt, 0, s>>>(a.A, a.rows, a.n_rows, a.col_ptr, a.col_cnt, a.csc_row,
-                                        a.csc_val);
-  count_launch();
-  CK(cudaGetLastError());
-  // 2. histogram over balanced work items of the outer product
-  k_outer_items<<<grid_cap_c((nB + 255) / 256, (int64_t)a.num_sms * 32), nt, 0, s>>>(
-      a.B.rp, a.col_ptr, nB, a.item_off);
-  count_launch();
-  CK(cudaGetLastError());
-  CK(launch_exclusive_scan_i64(a.item_off, nB, a.scan_tmp, s));
   const unsigned go = (unsigned)a.num_sms * 16;
-  if (NUMERIC && a.saved_offs) {
-    // the symbolic pass over the same batch kept the bucket offsets
-    CK(cudaMemcpyAsync(a.counts, a.saved_offs, (size_t)(nbk + 1) * sizeof(int64_t),
-                       cudaMemcpyDeviceToDevice, s));
+  if (a.items) {
+    // row-wise staged reorder: histogram (unless the symbolic pass kept the
+    // bucket offsets), row-chained prefix sum, then the reorder in runs
+    if (NUMERIC && a.saved_offs) {
+      CK(cudaMemcpyAsync(a.counts, a.saved_offs, (size_t)(nbk + 1) * sizeof(int64_t),
+                         cudaMemcpyDeviceToDevice, s));
+    } else {
+      CK(cudaMemsetAsync(a.counts, 0, (size_t)(nbk + 1) * sizeof(int64_t), s));
+      CK(launch_coarse_stage(false, false, a, s));
+      CK(launch_exclusive_scan_i64(a.counts, nbk, a.scan_tmp, s));
+      if (a.saved_offs)
+        CK(cudaMemcpyAsync(a.saved_offs, a.counts, (size_t)(nbk + 1) * sizeof(int64_t),
+                           cudaMemcpyDeviceToDevice, s));
+    }
+    CK(cudaMemcpyAsync(a.cursor, a.counts, (size_t)nbk * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    CK(launch_coarse_stage(true, NUMERIC, a, s));
   } else {
-    CK(cudaMemsetAsync(a.counts, 0, (size_t)(nbk + 1) * sizeof(int64_t), s));
-    k_coarse_outer<false, false><<<go, nt, 0, s>>>(a.B, a.item_off, nB, a.col_ptr, a.csc_row,
-                                                   a.csc_val, a.shift_coarse, a.n_chunks,
-                                                   a.counts, a.cursor, a.chunk_col, a.chunk_val);
+    // 1. A^CSC and coarseRowsB
+    CK(cudaMemsetAsync(a.col_cnt, 0, (size_t)(nB + 1) * sizeof(int32_t), s));
+    CK(cudaMemsetAsync(a.n_rows_b, 0, sizeof(int32_t), s));
+    k_csc_count<<<gw, nt, 0, s>>>(a.A, a.rows, a.n_rows, a.col_cnt, a.rows_b, a.n_rows_b);
     count_launch();
     CK(cudaGetLastError());
-    // 3. row-chained prefix sum
-    CK(launch_exclusive_scan_i64(a.counts, nbk, a.scan_tmp, s));
-    if (a.saved_offs)
-      CK(cudaMemcpyAsync(a.saved_offs, a.counts, (size_t)(nbk + 1) * sizeof(int64_t),
+    CK(launch_scan_i32_to_i64(a.col_cnt, nB, a.col_ptr, a.scan_tmp, s));
+    CK(cudaMemsetAsync(a.col_cnt, 0, (size_t)(nB + 1) * sizeof(int32_t), s));
+    k_csc_fill<NUMERIC><<<gw, nt, 0, s>>>(a.A, a.rows, a.n_rows, a.col_ptr, a.col_cnt, a.csc_row,
+                                          a.csc_val);
+    count_launch();
+    CK(cudaGetLastError());
+    // 2. histogram over balanced work items of the outer product
+    k_outer_items<<<grid_cap_c((nB + 255) / 256, (int64_t)a.num_sms * 32), nt, 0, s>>>(
+        a.B.rp, a.col_ptr, nB, a.item_off);
+    count_launch();
+    CK(cudaGetLastError());
+    CK(launch_exclusive_scan_i64(a.item_off, nB, a.scan_tmp, s));
+    if (NUMERIC && a.saved_offs) {
+      // the symbolic pass over the same batch kept the bucket offsets
+      CK(cudaMemcpyAsync(a.counts, a.saved_offs, (size_t)(nbk + 1) * sizeof(int64_t),
                          cudaMemcpyDeviceToDevice, s));
+    } else {
+      CK(cudaMemsetAsync(a.counts, 0, (size_t)(nbk + 1) * sizeof(int64_t), s));
+      k_coarse_outer<false, false><<<go, nt, 0, s>>>(a.B, a.item_off, nB, a.col_ptr, a.csc_row,
+                                                     a.csc_val, a.shift_coarse, a.n_chunks,
+                                                     a.counts, a.cursor, a.chunk_col, a.chunk_val);
+      count_launch();
+      CK(cudaGetLastError());
+      // 3. row-chained prefix sum
+      CK(launch_exclusive_scan_i64(a.counts, nbk, a.scan_tmp, s));
+      if (a.saved_offs)
+        CK(cudaMemcpyAsync(a.saved_offs, a.counts, (size_t)(nbk + 1) * sizeof(int64_t),
+                           cudaMemcpyDeviceToDevice, s));
+    }
+    // 4. reorder
+    CK(cudaMemcpyAsync(a.cursor, a.counts, (size_t)nbk * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    k_coarse_outer<true, NUMERIC><<<go, nt, 0, s>>>(a.B, a.item_off, nB, a.col_ptr, a.csc_row,
+                                                    a.csc_val, a.shift_coarse, a.n_chunks, a.counts,
+                                                    a.cursor, a.chunk_col, a.chunk_val);
+    count_launch();
+    CK(cudaGetLastError());
   }
-  // 4. reorder
-  CK(cudaMemcpyAsync(a.cursor, a.counts, (size_t)nbk * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-  k_coarse_outer<true, NUMERIC><<<go, nt, 0, s>>>(a.B, a.item_off, nB, a.col_ptr, a.csc_row,
-                                                  a.csc_val, a.shift_coarse, a.n_chunks, a.counts,
-                                                  a.cursor, a.chunk_col, a.chunk_val);
-  count_launch();
-  CK(cudaGetLastError());
   // 5. fine level per (row, coarse chunk)
   if (NUMERIC) {
     k_bucket_offsets<<<gw, nt, 0, s>>>(a.bucket_cnt, a.n_rows, a.n_chunks, a.list_base,
@@ -505,20 +638,38 @@ static cudaError_t coarse_impl(CoarseArgs& a, cudaStream_t s) {
     count_launch();
     CK(cudaGetLastError());
   }
-  CK(cudaMemsetAsync(a.n_big, 0, sizeof(int32_t), s));
+  CK(cudaMemsetAsync(a.n_big, 0, 2 * sizeof(int32_t), s));
   const bool k32 = a.shift_coarse + 8 <= 32;
   const unsigned gb = grid_cap_c((nbk + BK_NW - 1) / BK_NW, (int64_t)a.num_sms * 64);
+  // buckets of 257..BS_CAP products go to the block sort when enabled
+  const int mid_max = a.bucket_sort ? BS_CAP : 0;
   if (k32)
     k_bucket_small<uint32_t, NUMERIC><<<gb, BK_NW * 32, 0, s>>>(
         a.counts, nbk, a.chunk_col, a.chunk_val, a.shift_coarse, a.n_chunks, a.list_base, a.rows,
-        a.bucket_cnt, a.bucket_out, a.c_rp, a.c_base, a.c_col, a.c_val, a.big_list, a.n_big, a.big_stats);
+        a.bucket_cnt, a.bucket_out, a.c_rp, a.c_base, a.c_col, a.c_val, a.big_list, a.n_big,
+        a.big_stats, mid_max);
   else
     k_bucket_small<uint64_t, NUMERIC><<<gb, BK_NW * 32, 0, s>>>(
         a.counts, nbk, a.chunk_col, a.chunk_val, a.shift_coarse, a.n_chunks, a.list_base, a.rows,
-        a.bucket_cnt, a.bucket_out, a.c_rp, a.c_base, a.c_col, a.c_val, a.big_list, a.n_big, a.big_stats);
+        a.bucket_cnt, a.bucket_out, a.c_rp, a.c_base, a.c_col, a.c_val, a.big_list, a.n_big,
+        a.big_stats, mid_max);
   count_launch();
   CK(cudaGetLastError());
   if (a.big_ev0) CK(cudaEventRecord(a.big_ev0, s));
+  if (mid_max > 0) {
+    // the grid is one resident wave; blocks beyond the list's length exit
+    auto kern = (a.shift_coarse + BS_PB <= 32) ? k_bucket_sort<uint32_t, NUMERIC>
+                                               : k_bucket_sort<uint64_t, NUMERIC>;
+    int per_sm = 1;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BS_NT, 0));
+    if (per_sm < 1) per_sm = 1;
+    kern<<<(unsigned)(a.num_sms * per_sm), BS_NT, 0, s>>>(a.big_list, a.n_big + 1, a.chunk_col,
+                                                        a.chunk_val, a.shift_coarse,
+                                                        a.bucket_cnt, a.c_col, a.c_val);
+    count_launch();
+    CK(cudaGetLastError());
+  }
+  const BigBucket* big_end = a.big_list + nbk;
   if (a.shift_coarse <= BUCKET_DENSE_LOG2) {
     const size_t cl = (size_t)1 << a.shift_coarse;
     const size_t smem = (NUMERIC ? cl * 8 : 0) + (cl >= 32 ? cl / 8 : 4);
@@ -528,8 +679,8 @@ static cudaError_t coarse_impl(CoarseArgs& a, cudaStream_t s) {
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bucket_dense<NUMERIC>, FNT, smem));
     if (per_sm < 1) per_sm = 1;
     k_bucket_dense<NUMERIC><<<(unsigned)(a.num_sms * per_sm), FNT, smem, s>>>(
-        a.counts, a.big_list, a.n_big, a.chunk_col, a.chunk_val, a.shift_coarse, a.n_chunks,
-        a.list_base, a.rows, a.bucket_cnt, a.bucket_out, a.c_rp, a.c_base, a.c_col, a.c_val);
+        big_end, a.n_big, a.chunk_col, a.chunk_val, a.shift_coarse, a.bucket_cnt, a.c_col,
+        a.c_val);
   } else {
     // the sort and hash accumulators share the per-warp staging
     const bool hybrid = a.dense_chunk_threshold > 1 || (NUMERIC && a.hash);
@@ -538,9 +689,9 @@ static cudaError_t coarse_impl(CoarseArgs& a, cudaStream_t s) {
     auto kern = hybrid ? k_bucket_big<NUMERIC, true> : k_bucket_big<NUMERIC, false>;
     CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<(unsigned)a.num_sms * 2, FNT, smem, s>>>(
-        a.counts, a.big_list, a.n_big, a.chunk_col, a.chunk_val, a.fine_col, a.fine_val,
-        a.shift_coarse, a.shift_fine, a.n_chunks, a.list_base, a.rows,
-        a.bucket_cnt, a.bucket_out, a.c_rp, a.c_base, a.c_col, a.c_val, a.dense_chunk_threshold, a.hash);
+        big_end, a.n_big, a.chunk_col, a.chunk_val, a.fine_col, a.fine_val,
+        a.shift_coarse, a.shift_fine, a.bucket_cnt, a.c_col, a.c_val, a.dense_chunk_threshold,
+        a.hash);
   }
   count_launch();
   CK(cudaGetLastError());

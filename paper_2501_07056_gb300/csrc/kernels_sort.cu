@@ -368,9 +368,8 @@ __global__ void __launch_bounds__(NW * 32, NUMERIC ? 5 : 4) k_sort_rows(SortArgs
   }
 }
 
-template <int E, typename K, bool NUMERIC>
-static cudaError_t launch_one(const SortArgs& a, int num_sms, cudaStream_t s) {
-  constexpr int NW = NUMERIC ? 4 : 8;
+template <int E, typename K, bool NUMERIC, int NW>
+static cudaError_t launch_nw(const SortArgs& a, int num_sms, cudaStream_t s) {
   constexpr int G = 8 / E;
   auto kern = k_sort_rows<E, K, NUMERIC, NW>;
   int per_sm = 0;
@@ -383,6 +382,17 @@ static cudaError_t launch_one(const SortArgs& a, int num_sms, cudaStream_t s) {
   kern<<<(unsigned)blocks, NW * 32, 0, s>>>(a);
   count_launch();
   return cudaGetLastError();
+}
+
+// Warps per block: the requested shape, else 4 (numeric) / 8 (symbolic).
+template <int E, typename K, bool NUMERIC>
+static cudaError_t launch_one(const SortArgs& a, int num_sms, cudaStream_t s) {
+  switch (a.block_warps) {
+    case 2: return launch_nw<E, K, NUMERIC, 2>(a, num_sms, s);
+    case 4: return launch_nw<E, K, NUMERIC, 4>(a, num_sms, s);
+    case 8: return launch_nw<E, K, NUMERIC, 8>(a, num_sms, s);
+    default: return launch_nw<E, K, NUMERIC, NUMERIC ? 4 : 8>(a, num_sms, s);
+  }
 }
 
 template <typename K, bool NUMERIC>

@@ -24,60 +24,6 @@ namespace magnus {
 
 namespace {
 
-constexpr int BR = 8;  // keys per thread
-
-// Bitonic sort of NT * BR keys; thread t holds positions t * BR + e.  The
-// direction of a compare-exchange depends on bit k of the position and its
-// side on bit j; for k or j >= BR those bits come from t alone, so they are
-// computed once per stage (BR is a power of two).
-template <int NT, typename K>
-__device__ __forceinline__ void block_sort_keys(K (&key)[BR], K* s_key) {
-  constexpr int CAP = NT * BR;
-  const int t = threadIdx.x;
-  const int tb = t * BR;
-#pragma unroll
-  for (int k = 2; k <= CAP; k <<= 1) {
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      if (j < BR) {
-        const bool up_t = (tb & k) == 0;  // used when k >= BR
-#pragma unroll
-        for (int e = 0; e < BR; ++e) {
-          if ((e & j) == 0) {
-            const bool up = (k < BR) ? ((e & k) == 0) : up_t;
-            K& x = key[e];
-            K& y = key[e | j];
-            const K lo = x < y ? x : y;
-            const K hi = x < y ? y : x;
-            x = up ? lo : hi;
-            y = up ? hi : lo;
-          }
-        }
-      } else {
-        const bool take_min = (((tb & k) == 0) == ((tb & j) == 0));
-        if (j < 32 * BR) {
-          const int lm = j / BR;  // partner lane distance
-#pragma unroll
-          for (int e = 0; e < BR; ++e) {
-            const K o = __shfl_xor_sync(FULL, key[e], lm);
-            key[e] = take_min ? (o < key[e] ? o : key[e]) : (o > key[e] ? o : key[e]);
-          }
-        } else {
-#pragma unroll
-          for (int e = 0; e < BR; ++e) s_key[tb + e] = key[e];
-          __syncthreads();
-#pragma unroll
-          for (int e = 0; e < BR; ++e) {
-            const K o = s_key[(tb + e) ^ j];
-            key[e] = take_min ? (o < key[e] ? o : key[e]) : (o > key[e] ? o : key[e]);
-          }
-          __syncthreads();
-        }
-      }
-    }
-  }
-}
-
 template <int CAPLOG, typename K, bool NUMERIC>
 __global__ void __launch_bounds__((1 << CAPLOG) / BR) k_sort_rows_block(SortArgs a) {
   constexpr int CAP = 1 << CAPLOG;

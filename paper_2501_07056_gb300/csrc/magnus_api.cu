@@ -165,6 +165,9 @@ struct magnus_plan_s {
   unsigned long long* big_stats = nullptr;  // [3] of the last numeric call (coarse large buckets)
   int64_t* coarse_offs = nullptr;  // bucket offsets of every coarse batch (symbolic -> numeric)
   std::vector<int64_t> coarse_offs_at;  // start of each batch's offsets in coarse_offs
+  bool coarse_rowwise = false;          // row-wise staged reorder (else the outer product)
+  CoarseItem* coarse_items_d = nullptr;  // its work items, in coarse list order
+  std::vector<int64_t> coarse_item_first;  // first item of each coarse list row (+ total)
   // sorted slot order of the sort rows (symbolic -> numeric)
   uint8_t* perm = nullptr;
   int64_t perm_off[NUM_BINS + 1] = {0};
@@ -379,6 +382,11 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
   if (P.sort_threshold < 0 || P.sort_threshold > SORT_BLOCK_MAX + 1) return MAGNUS_INVALID_ARG;
   if (P.wide_sort_max < -1 || P.wide_sort_max > SORT_BLOCK_MAX) return MAGNUS_INVALID_ARG;
   if (P.chunk_accumulator != 0 && P.chunk_accumulator != 1) return MAGNUS_INVALID_ARG;
+  if (P.coarse_reorder < 0 || P.coarse_reorder > 2) return MAGNUS_INVALID_ARG;
+  if (P.sort_block_warps != 0 && P.sort_block_warps != 2 && P.sort_block_warps != 4 &&
+      P.sort_block_warps != 8)
+    return MAGNUS_INVALID_ARG;
+  if (P.coarse_bucket_sort < -1 || P.coarse_bucket_sort > 1) return MAGNUS_INVALID_ARG;
   pl->sort_T = P.sort_threshold > 0 ? P.sort_threshold : 256;
   const int64_t m_c = B->n_cols > 0 ? B->n_cols : 1;
   pl->col_bits = ceil_log2_i64(m_c);
@@ -629,6 +637,32 @@ static int plan_impl(magnus_plan_t pl, const magnus_csr_t* A, const magnus_csr_t
     CUDA_TRY(cudaStreamSynchronize(s));
     pl->coarse_nnz.resize(nc);
     for (size_t i = 0; i < nc; ++i) pl->coarse_nnz[i] = rp[pl->coarse_rows[i] + 1] - rp[pl->coarse_rows[i]];
+    // work items of the row-wise staged reorder: runs of CS_NJ nonzeros of A
+    // automatic: row-wise when B rows are barely shared (the coarse rows'
+    // nonzeros of A reference each B row about once, so the outer product's
+    // one read per batch saves nothing); the outer product otherwise
+    int64_t coarse_nnz_total = 0;
+    for (int64_t z : pl->coarse_nnz) coarse_nnz_total += z;
+    const bool low_reuse = coarse_nnz_total <= 2 * pl->B.n_rows;
+    pl->coarse_rowwise = P.coarse_reorder == 2 ||
+                         (P.coarse_reorder == 0 && low_reuse &&
+                          pl->n_chunks_coarse <= CS_MAX_CHUNKS);
+    if (pl->coarse_rowwise && pl->n_chunks_coarse > CS_MAX_CHUNKS) return MAGNUS_INVALID_ARG;
+    if (pl->coarse_rowwise) {
+      std::vector<CoarseItem> items;
+      pl->coarse_item_first.assign(nc + 1, 0);
+      for (size_t i = 0; i < nc; ++i) {
+        pl->coarse_item_first[i] = (int64_t)items.size();
+        const int64_t a0 = rp[pl->coarse_rows[i]], a1 = rp[pl->coarse_rows[i] + 1];
+        for (int64_t j0 = a0; j0 < a1; j0 += CS_NJ)
+          items.push_back(CoarseItem{j0, (int32_t)i, (int32_t)std::min<int64_t>(CS_NJ, a1 - j0)});
+      }
+      pl->coarse_item_first[nc] = (int64_t)items.size();
+      MAG_TRY(plan_alloc(pl, &pl->coarse_items_d, items.size(), s));
+      // pageable source: the copy has left the vector when the call returns
+      CUDA_TRY(cudaMemcpyAsync(pl->coarse_items_d, items.data(), items.size() * sizeof(CoarseItem),
+                               cudaMemcpyHostToDevice, s));
+    }
     MAG_TRY(plan_alloc(pl, &pl->bucket_cnt, nc * (size_t)pl->n_chunks_coarse, s));
     MAG_TRY(plan_alloc(pl, &pl->big_stats, 3, s));
     // the bucket offsets of each batch, kept from the symbolic pass for the
@@ -769,12 +803,14 @@ void carve_phase(magnus_plan_t pl, bool numeric, bool rows_mode, Arena& ar, Phas
     const int64_t nB = pl->B.n_rows;
     const int64_t nbk = z.maxRows * pl->n_chunks_coarse;
     CoarseArgs& a = ps.co;
-    a.col_cnt = ar.get<int32_t>((size_t)nB + 1);
-    a.col_ptr = ar.get<int64_t>((size_t)nB + 1);
-    a.csc_row = ar.get<int32_t>((size_t)z.maxNnz);
-    if (numeric) a.csc_val = ar.get<double>((size_t)z.maxNnz);
-    a.rows_b = ar.get<int32_t>((size_t)nB + 1);
-    a.item_off = ar.get<int64_t>((size_t)nB + 1);
+    if (!pl->coarse_rowwise) {  // the outer product's A^CSC and work offsets
+      a.col_cnt = ar.get<int32_t>((size_t)nB + 1);
+      a.col_ptr = ar.get<int64_t>((size_t)nB + 1);
+      a.csc_row = ar.get<int32_t>((size_t)z.maxNnz);
+      if (numeric) a.csc_val = ar.get<double>((size_t)z.maxNnz);
+      a.rows_b = ar.get<int32_t>((size_t)nB + 1);
+      a.item_off = ar.get<int64_t>((size_t)nB + 1);
+    }
     a.n_rows_b = ar.get<int32_t>(2);
     a.counts = ar.get<int64_t>((size_t)nbk + 1);
     a.cursor = ar.get<unsigned long long>((size_t)nbk);
@@ -787,7 +823,7 @@ void carve_phase(magnus_plan_t pl, bool numeric, bool rows_mode, Arena& ar, Phas
       a.bucket_out = ar.get<int64_t>((size_t)nbk);
     }
     a.scan_tmp = ar.get<int64_t>((size_t)scan_tmp_elems(std::max<int64_t>(nB, nbk)) + 2);
-    a.big_list = ar.get<int32_t>((size_t)nbk);
+    a.big_list = ar.get<BigBucket>((size_t)nbk);
     a.n_big = ar.get<int32_t>(2);
   }
   // the symbolic pass's C.rowPtr scan (after every category)
@@ -875,6 +911,7 @@ static int run_phase(magnus_plan_t pl, bool numeric, const RowRange& rr, int64_t
       a.c_val = c_val;
       a.range = rr.on ? ps.bounds + 2 * b : nullptr;
       a.c_base = c_base;
+      a.block_warps = pl->params.sort_block_warps;
       if (b <= BIN_SORT256) CUDA_TRY(launch_sort_rows(b, numeric, a, pl->num_sms, s));
       else CUDA_TRY(launch_sort_rows_block(b, numeric, a, pl->num_sms, s));
     }
@@ -1018,6 +1055,18 @@ static int run_phase(magnus_plan_t pl, bool numeric, const RowRange& rr, int64_t
           if (numeric) staged += pl->coarse_P[i];
         }
         a.nnz_batch = nz;
+        a.seg = pl->seg;
+        // automatic: the block sort for buckets of chunks wider than the block
+        // dense accumulator (sparse buckets, e.g. the massive nonsquare
+        // workload); the dense accumulator for narrower, denser chunks (its
+        // bitmap is cheap there, and the sort would pad small buckets)
+        a.bucket_sort = pl->params.coarse_bucket_sort > 0 ||
+                        (pl->params.coarse_bucket_sort == 0 && pl->shift_coarse > 13);
+        if (pl->coarse_rowwise) {
+          a.items = pl->coarse_items_d + pl->coarse_item_first[r0];
+          a.n_items = (int32_t)(pl->coarse_item_first[r1] - pl->coarse_item_first[r0]);
+          a.item_ctr = a.n_rows_b;
+        }
         // the bucket offsets kept by the symbolic pass cover whole batches
         const bool whole = r0 == b0 && r1 == b1;
         a.saved_offs = (pl->coarse_offs && whole) ? pl->coarse_offs + pl->coarse_offs_at[bi] : nullptr;
@@ -1206,6 +1255,7 @@ int magnus_numeric_noalloc(magnus_plan_t pl, const double* a_val, const double* 
     a.c_rp = c_row_ptr;
     a.c_col = c_col;
     a.c_val = c_val;
+    a.block_warps = pl->params.sort_block_warps;
     if (b <= BIN_SORT256) CUDA_TRY(launch_sort_rows(b, true, a, pl->num_sms, s));
     else CUDA_TRY(launch_sort_rows_block(b, true, a, pl->num_sms, s));
   }

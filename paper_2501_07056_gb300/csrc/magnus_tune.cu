@@ -6,8 +6,10 @@
 // model values are starting points: the search is coordinate descent from the
 // automatic parameters over the sort threshold, the wide-row sort limit, the
 // coarse and fine chunk lengths and the fine-level hybrid threshold, each
-// dimension tried only when the rows it governs exist; last, the fine
-// level's chunk accumulator (dense array or hash map).  Every candidate
+// dimension tried only when the rows it governs exist; then the fine
+// level's chunk accumulator (dense array or hash map), the coarse level's
+// staging form (outer product or row-wise runs) and the block shape of the
+// warp-sort kernels (2, 4 or 8 warps per block).  Every candidate
 // computes the same C (parameters never change results beyond FP64 summation
 // order), so C is allocated once.  Results are cached per operand shape and
 // base parameters.
@@ -215,6 +217,10 @@ int magnus_autotune(const magnus_csr_t* A, const magnus_csr_t* B, const magnus_p
       {&magnus_params_t::chunk_len_fine_log2, {7, 8, 9, 10}, has_fine || has_coarse},
       {&magnus_params_t::dense_chunk_threshold, {1, 32, 128, 257}, has_fine || has_coarse},
       {&magnus_params_t::chunk_accumulator, {0, 1}, has_fine || has_coarse},
+      {&magnus_params_t::coarse_reorder, {1, 2}, has_coarse},
+      {&magnus_params_t::coarse_bucket_sort, {-1, 1}, has_coarse},
+      {&magnus_params_t::sort_block_warps, {2, 4, 8},
+       info.rows_per_category[MAGNUS_CAT_SORT] > 0},
   };
   for (const Dim& d : dims) {
     if (st != MAGNUS_OK || !d.active) continue;

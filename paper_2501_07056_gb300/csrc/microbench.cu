@@ -17,6 +17,7 @@
 //
 // The accumulate step needs 2^shift <= 2^13 (one block's accumulator).
 #include <algorithm>
+#include <cstring>
 
 #include "common.cuh"
 #include "internal.h"
@@ -200,6 +201,100 @@ __global__ void k_mb_global(const int32_t* __restrict__ col, const double* __res
     atomicAdd(&gacc[col[i]], val[i]);
 }
 
+// ---------------------------------------------------------------------------
+// Rates of the GB300 operations the SpGEMM kernels are built from (no
+// counterpart in the paper; these bound the kernels' rooflines):
+//  * random gathers of chunks of 16..256 bytes at chunk-aligned offsets of a
+//    large array (a B row is such a chunk; the sort kernels gather one per
+//    nonzero of A), one chunk per chunk/16 lanes with 16-byte loads, and the
+//    CSR form of a B row of 8 entries: 32 bytes of columns and 64 bytes of
+//    values from two arrays;
+//  * shared-memory accumulation: FP64 atomicAdd at distinct and at random
+//    addresses and with 8 lanes per address, a plain FP64 add, and u32
+//    atomicAdd, each thread updating an 8,192-entry block-private array.
+
+__device__ __forceinline__ uint64_t mb_mix(uint64_t z) {
+  z += 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+template <int LP>  // lanes per chunk (chunk bytes / 16)
+__global__ void k_mb_gather(const uint4* __restrict__ a, uint64_t nchunks, uint64_t work,
+                            uint4* __restrict__ out) {
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
+  uint4 acc = make_uint4(0, 0, 0, 0);
+  for (uint64_t t = tid; t < work * LP; t += nthr) {
+    const uint64_t c = mb_mix(t / LP) % nchunks;
+    const uint4 v = __ldg(a + c * LP + (t % LP));
+    acc.x ^= v.x;
+    acc.y ^= v.y;
+    acc.z ^= v.z;
+    acc.w ^= v.w;
+  }
+  if ((acc.x ^ acc.y ^ acc.z ^ acc.w) == 0x9e3779b9u) out[tid & 1023] = acc;
+}
+
+// rows of 8 entries: 32 B of columns (2 lanes) and 64 B of values (4 lanes)
+__global__ void k_mb_gather_csr(const uint4* __restrict__ cols, const uint4* __restrict__ vals,
+                                uint64_t nrows, uint64_t work, uint4* __restrict__ out) {
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
+  uint4 acc = make_uint4(0, 0, 0, 0);
+  for (uint64_t t = tid; t < work * 4; t += nthr) {
+    const uint64_t r = mb_mix(t / 4) % nrows;
+    const int q = (int)(t % 4);
+    uint4 v = __ldg(vals + r * 4 + q);
+    if (q < 2) {
+      const uint4 w = __ldg(cols + r * 2 + q);
+      v.x ^= w.x;
+      v.y ^= w.y;
+    }
+    acc.x ^= v.x;
+    acc.y ^= v.y;
+    acc.z ^= v.z;
+    acc.w ^= v.w;
+  }
+  if ((acc.x ^ acc.y ^ acc.z ^ acc.w) == 0x9e3779b9u) out[tid & 1023] = acc;
+}
+
+constexpr int MB_ACC_N = 8192;
+
+__device__ __forceinline__ uint32_t mb_hash(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352dU;
+  x ^= x >> 15;
+  x *= 0x846ca68bU;
+  x ^= x >> 16;
+  return x;
+}
+
+// MODE 0 f64 atomic distinct, 1 f64 atomic random, 2 f64 atomic 8 lanes per
+// address, 3 plain f64 add (distinct), 4 u32 atomic random
+template <int MODE>
+__global__ void __launch_bounds__(MB_NT) k_mb_atomics(int iters, double* __restrict__ out) {
+  extern __shared__ double acc_s[];
+  for (int i = threadIdx.x; i < MB_ACC_N; i += blockDim.x) acc_s[i] = 0.0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const double v = 1.0 + threadIdx.x * 1e-3;
+  for (int it = 0; it < iters; ++it) {
+    int idx;
+    if (MODE == 0 || MODE == 3) idx = (w * 1024 + it * 32 + lane) & (MB_ACC_N - 1);
+    else if (MODE == 2) idx = (int)(mb_hash(it * 64 + w * 4 + (lane >> 3)) & (MB_ACC_N - 1));
+    else idx = (int)(mb_hash(it * 256 + threadIdx.x + blockIdx.x * 7919) & (MB_ACC_N - 1));
+    if (MODE <= 2) atomicAdd(&acc_s[idx], v);
+    else if (MODE == 3) acc_s[idx] += v;
+    else atomicAdd(reinterpret_cast<unsigned*>(acc_s) + 2 * idx, 1u);
+  }
+  __syncthreads();
+  double t = 0.0;
+  for (int i = threadIdx.x; i < MB_ACC_N; i += blockDim.x) t += acc_s[i];
+  if (t == -1.0) out[blockIdx.x] = t;
+}
+
 }  // namespace
 
 extern "C" {
@@ -305,6 +400,81 @@ int magnus_microbench_chunks(const int32_t* col, const double* val, int64_t leng
     if (p) cudaFreeAsync(p, s);
   for (auto& x : ev) cudaEventDestroy(x);
   return st;
+}
+
+/* magnus_microbench_rates: see magnus.h. */
+int magnus_microbench_rates(magnus_rates_t* r, void* stream) {
+  if (!r) return MAGNUS_INVALID_ARG;
+  memset(r, 0, sizeof(*r));
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return api_cuda_fail(cudaGetLastError(), "cudaDeviceGetAttribute");
+  const size_t bytes = (size_t)2 << 30;
+  uint4* a = nullptr;
+  uint4* o = nullptr;
+  double* od = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&a), bytes, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&o), 1024 * sizeof(uint4), s);
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&od), 4096 * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a, 1, bytes, s);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const uint64_t work = (uint64_t)64 << 20;  // chunks per gather launch
+  const unsigned gb = (unsigned)sms * 8;
+  auto timed = [&](auto launch, float* out_ms) {
+    if (e != cudaSuccess) return;
+    launch();
+    e = cudaEventRecord(e0, s);
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    *out_ms = ms / 3.f;
+    count_launch(4);
+  };
+  const double gch = (double)work;
+  float ms = 0.f;
+  timed([&] { k_mb_gather<1><<<gb, MB_NT, 0, s>>>(a, bytes / 16, work, o); }, &ms);
+  r->gather_16 = gch / (ms * 1e-3);
+  timed([&] { k_mb_gather<2><<<gb, MB_NT, 0, s>>>(a, bytes / 32, work, o); }, &ms);
+  r->gather_32 = gch / (ms * 1e-3);
+  timed([&] { k_mb_gather<4><<<gb, MB_NT, 0, s>>>(a, bytes / 64, work, o); }, &ms);
+  r->gather_64 = gch / (ms * 1e-3);
+  timed([&] { k_mb_gather<8><<<gb, MB_NT, 0, s>>>(a, bytes / 128, work, o); }, &ms);
+  r->gather_128 = gch / (ms * 1e-3);
+  timed([&] { k_mb_gather<16><<<gb, MB_NT, 0, s>>>(a, bytes / 256, work, o); }, &ms);
+  r->gather_256 = gch / (ms * 1e-3);
+  {
+    const uint64_t nrows = (bytes / 3) / 32;  // 32 B of columns + 64 B of values each
+    timed([&] { k_mb_gather_csr<<<gb, MB_NT, 0, s>>>(a, a + nrows * 2, nrows, work, o); }, &ms);
+    r->gather_csr_row8 = gch / (ms * 1e-3);
+  }
+  // shared-memory accumulation: 3 blocks of 64 KB per SM
+  const unsigned ga = (unsigned)sms * 3;
+  const size_t smem = MB_ACC_N * sizeof(double);
+  auto atom = [&](auto kern, int iters, double* out_rate) {
+    if (e != cudaSuccess) return;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    timed([&] { kern<<<ga, MB_NT, smem, s>>>(iters, od); }, &ms);
+    *out_rate = (double)ga * MB_NT * iters / (ms * 1e-3);
+  };
+  atom(k_mb_atomics<0>, 2048, &r->smem_f64_atomic_distinct);
+  atom(k_mb_atomics<1>, 2048, &r->smem_f64_atomic_random);
+  atom(k_mb_atomics<2>, 512, &r->smem_f64_atomic_8_per_address);
+  atom(k_mb_atomics<3>, 2048, &r->smem_f64_add_plain);
+  atom(k_mb_atomics<4>, 2048, &r->smem_u32_atomic_random);
+  r->sms = sms;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFreeAsync(a, s);
+  cudaFreeAsync(o, s);
+  cudaFreeAsync(od, s);
+  const cudaError_t fin = e == cudaSuccess ? cudaStreamSynchronize(s) : e;
+  return fin == cudaSuccess ? MAGNUS_OK : api_cuda_fail(fin, "magnus_microbench_rates");
 }
 
 }  // extern "C"

@@ -37,7 +37,8 @@ class Params(ctypes.Structure):
                 ("chunk_len_fine_log2", c_i32), ("chunk_len_coarse_log2", c_i32),
                 ("dense_chunk_threshold", c_i32), ("validate", c_i32),
                 ("max_scratch_bytes", c_i64), ("l2_fetch_bytes", c_i32), ("numeric_graph", c_i32), ("wide_sort_max", c_i32),
-                ("chunk_accumulator", c_i32)]
+                ("chunk_accumulator", c_i32), ("coarse_reorder", c_i32),
+                ("sort_block_warps", c_i32), ("coarse_bucket_sort", c_i32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -73,6 +74,17 @@ class MicrobenchResult(ctypes.Structure):
                 ("accumulate_ms", ctypes.c_float), ("global_accumulate_ms", ctypes.c_float),
                 ("n_chunks", c_i32), ("chunk_len_log2", c_i32),
                 ("reorder_staged_ms", ctypes.c_float), ("reserved", c_i32)]
+
+
+class Rates(ctypes.Structure):
+    _fields_ = [("gather_16", ctypes.c_double), ("gather_32", ctypes.c_double),
+                ("gather_64", ctypes.c_double), ("gather_128", ctypes.c_double),
+                ("gather_256", ctypes.c_double), ("gather_csr_row8", ctypes.c_double),
+                ("smem_f64_atomic_distinct", ctypes.c_double),
+                ("smem_f64_atomic_random", ctypes.c_double),
+                ("smem_f64_atomic_8_per_address", ctypes.c_double),
+                ("smem_f64_add_plain", ctypes.c_double),
+                ("smem_u32_atomic_random", ctypes.c_double), ("sms", c_i32), ("reserved", c_i32)]
 
 
 class ChunkModel(ctypes.Structure):
@@ -115,6 +127,8 @@ SIGNATURES = {
     "magnus_launch_count": (c_u64, []),
     "magnus_device_memory": (c_i32, [ctypes.POINTER(ctypes.c_size_t),
                                      ctypes.POINTER(ctypes.c_size_t)]),
+    "magnus_host_alloc": (c_i32, [ctypes.c_size_t, ctypes.POINTER(c_p)]),
+    "magnus_host_free": (c_i32, [c_p, ctypes.c_size_t]),
     "magnus_plan_batched": (c_i32, [ctypes.POINTER(c_p), c_i32, ctypes.POINTER(CsrDesc),
                                     ctypes.POINTER(CsrDesc), ctypes.POINTER(Params), c_p]),
     "magnus_batch_layout": (c_i32, [c_p, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
@@ -129,6 +143,7 @@ SIGNATURES = {
                                 ctypes.POINTER(Params), c_i64, c_i32, ctypes.POINTER(Params),
                                 ctypes.POINTER(TuneReport), c_p]),
     "magnus_chunk_model": (c_i32, [c_i64, c_i64, c_i64, c_i32, ctypes.POINTER(ChunkModel)]),
+    "magnus_microbench_rates": (c_i32, [ctypes.POINTER(Rates), c_p]),
 }
 
 
@@ -261,6 +276,45 @@ def magnus_chunk_model(m_c: int, smem_bytes: int, l2_bytes: int, resident_blocks
     return {name: getattr(out, name) for name, _ in out._fields_}
 
 
+class _HostRegion:
+    """A magnus_host_alloc region exposed to numpy through the array
+    interface; released when the last array (or tensor) using it is gone."""
+
+    def __init__(self, nbytes: int):
+        p = c_p()
+        _check(_lib().magnus_host_alloc(nbytes, ctypes.byref(p)), "magnus_host_alloc")
+        self.ptr, self.nbytes = p.value, nbytes
+        self.__array_interface__ = {"shape": (nbytes,), "typestr": "|u1",
+                                    "data": (self.ptr, False), "version": 3}
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            _lib().magnus_host_free(c_p(self.ptr), self.nbytes)
+            self.ptr = None
+
+
+def host_empty(count: int, dtype):
+    """A page-locked host tensor of ``count`` elements in huge-page-backed
+    memory (magnus_host_alloc): copies to and from the device run at the
+    host link's rate even when host memory is fragmented."""
+    import numpy as np
+    import torch
+    npdt = {torch.int32: np.int32, torch.int64: np.int64, torch.float64: np.float64,
+            torch.uint8: np.uint8}[dtype]
+    nbytes = max(int(count), 1) * np.dtype(npdt).itemsize
+    raw = np.asarray(_HostRegion(nbytes))  # keeps the region alive as its base
+    return torch.from_numpy(raw.view(npdt)[:max(int(count), 1)])[:int(count)]
+
+
+def host_copy(x):
+    """A huge-page-backed page-locked copy of the numpy array ``x``."""
+    import torch
+    dt = {"int32": torch.int32, "int64": torch.int64, "float64": torch.float64}[str(x.dtype)]
+    t = host_empty(x.size, dt)
+    t.numpy()[:] = x.reshape(-1)
+    return t
+
+
 # ---------------------------------------------------------------------------
 # PyTorch-facing convenience layer.
 
@@ -294,7 +348,8 @@ class DeviceCSR:
 def make_params(sort_threshold=0, force_category=CAT_AUTO, chunk_len_fine_log2=0,
                 chunk_len_coarse_log2=0, dense_chunk_threshold=0, validate=0,
                 max_scratch_bytes=0, l2_fetch_bytes=0, numeric_graph=0,
-                wide_sort_max=0, chunk_accumulator=0) -> Params:
+                wide_sort_max=0, chunk_accumulator=0, coarse_reorder=0,
+                sort_block_warps=0, coarse_bucket_sort=0) -> Params:
     p = magnus_params_default()
     p.sort_threshold = sort_threshold
     p.force_category = force_category
@@ -307,6 +362,9 @@ def make_params(sort_threshold=0, force_category=CAT_AUTO, chunk_len_fine_log2=0
     p.numeric_graph = numeric_graph
     p.wide_sort_max = wide_sort_max
     p.chunk_accumulator = chunk_accumulator
+    p.coarse_reorder = coarse_reorder
+    p.sort_block_warps = sort_block_warps
+    p.coarse_bucket_sort = coarse_bucket_sort
     return p
 
 
@@ -415,6 +473,17 @@ def microbench_chunks(col, val, m: int, n_chunks_log2: int, stream=None):
                                            ctypes.byref(res), c_p(s.cuda_stream)),
            "magnus_microbench_chunks")
     return ({name: getattr(res, name) for name, _ in res._fields_}, out_col, out_val, chunk_nnz)
+
+
+def microbench_rates(stream=None) -> dict:
+    """magnus_microbench_rates: random-gather and shared-memory accumulation
+    rates of the current device (per second, device-wide)."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    r = Rates()
+    _check(_lib().magnus_microbench_rates(ctypes.byref(r), c_p(s.cuda_stream)),
+           "magnus_microbench_rates")
+    return {name: getattr(r, name) for name, _ in r._fields_ if name != "reserved"}
 
 
 def params_dict(p: Params) -> dict:
@@ -531,9 +600,10 @@ def spgemm_host(A, B, params: Params | None = None, blocks: int = 4, device="cud
     magnus_numeric_rows into one of two device slab buffers and copied back
     to host memory while the next slab computes, so the device holds two
     slabs of C, not all of it.
-    ``pinned``: optional (A, B) pinned host copies (torch tensors
-    (row_ptr, col, val)) to copy from; ``out``: optional pinned host tensors
-    (row_ptr, col, val) large enough for C (else allocated).  ``timing``:
+    ``pinned``: optional (A, B) page-locked host copies (torch tensors
+    (row_ptr, col, val)) to copy from, else made with ``host_copy``;
+    ``out``: optional page-locked host tensors (row_ptr, col, val) large
+    enough for C, else allocated with ``host_empty``.  ``timing``:
     optional dict that receives the device time of each part (ms, CUDA
     events): h2d, plan_symbolic, rowptr_d2h, numeric (sum over slabs), d2h
     (first slab copy start to last copy end), total.  Returns (row_ptr,
@@ -542,9 +612,8 @@ def spgemm_host(A, B, params: Params | None = None, blocks: int = 4, device="cud
     import torch
     dev = torch.device(device)
     if pinned is None:
-        pa = tuple(torch.from_numpy(x).pin_memory() for x in (A.row_ptr, A.col, A.val))
-        pinned = (pa, pa if B is A else
-                  tuple(torch.from_numpy(x).pin_memory() for x in (B.row_ptr, B.col, B.val)))
+        pa = tuple(host_copy(x) for x in (A.row_ptr, A.col, A.val))
+        pinned = (pa, pa if B is A else tuple(host_copy(x) for x in (B.row_ptr, B.col, B.val)))
     main = torch.cuda.current_stream(dev)
     cs = _copy_stream(dev)
     ev = (lambda: torch.cuda.Event(enable_timing=True)) if timing is not None else \
@@ -567,9 +636,8 @@ def spgemm_host(A, B, params: Params | None = None, blocks: int = 4, device="cud
         t_sym = ev()
         t_sym.record(main)
         if out is None:
-            out = (torch.empty(A.n_rows + 1, dtype=torch.int64).pin_memory(),
-                   torch.empty(max(nnz, 1), dtype=torch.int32).pin_memory(),
-                   torch.empty(max(nnz, 1), dtype=torch.float64).pin_memory())
+            out = (host_empty(A.n_rows + 1, torch.int64), host_empty(max(nnz, 1), torch.int32),
+                   host_empty(max(nnz, 1), torch.float64))
         o_rp, o_col, o_val = out
         o_rp[:A.n_rows + 1].copy_(plan.c_row_ptr)
         t_rp = ev()

@@ -150,6 +150,7 @@ def _header_structs():
     ("magnus_csr_t", "CsrDesc"), ("magnus_params_t", "Params"),
     ("magnus_plan_info_t", "PlanInfo"), ("magnus_tune_report_t", "TuneReport"),
     ("magnus_microbench_t", "MicrobenchResult"), ("magnus_chunk_model_t", "ChunkModel"),
+    ("magnus_rates_t", "Rates"),
 ])
 def test_binding_structs_match_header(cname, pyname):
     # The ctypes mirrors of the ABI structs carry the header's fields in the

@@ -50,3 +50,17 @@ def test_chunk_accumulation(n, m, lg):
         s0 = starts[c]
         assert np.array_equal(oc[s0:s0 + u.size], u)
         assert values_close(ov[s0:s0 + u.size], sums, abss).all()
+
+
+def test_device_rates_are_consistent():
+    """magnus_microbench_rates: every rate is positive; byte rates grow with
+    the chunk size while chunk rates do not (a random gather costs at least
+    one DRAM transaction); an 8-lanes-per-address FP64 atomic is slower than
+    one at distinct addresses."""
+    from paper_2501_07056_gb300 import magnus
+    r = magnus.microbench_rates()
+    assert r["sms"] > 0
+    assert all(v > 0 for k, v in r.items() if k != "sms")
+    assert r["gather_256"] * 256 > r["gather_32"] * 32
+    assert r["gather_256"] <= r["gather_32"] * 1.1
+    assert r["smem_f64_atomic_8_per_address"] < r["smem_f64_atomic_distinct"]

@@ -329,3 +329,42 @@ def test_hash_chunk_accumulator(inp, force, dthr):
     p = P(force_category=force, dense_chunk_threshold=dthr, chunk_accumulator=1, **extra)
     got = run_gpu(A, B, p, same=A is B)
     assert_parity(got, A, B)
+
+
+@pytest.mark.parametrize("reorder,bsort", [(1, 1), (2, 1), (1, -1), (2, -1)])
+@pytest.mark.parametrize("case", ["rmat", "rmat_forced_small_budget", "ragged_coarse",
+                                  "wide_chunks", "hub_rows"])
+def test_coarse_reorder_forms(case, reorder, bsort):
+    """Both stagings of Algorithm 4's reorder (outer product over A^CSC, and
+    row-wise with sub-tiles counting-sorted by chunk and written as runs)
+    give the oracle's C: R-MAT with its automatic coarse rows; every row
+    forced coarse under an 8 MB staging budget (several batches); ragged rows
+    with 2^10-column chunks; chunks wider than the block accumulator (fine
+    level inside); rows of A with more than 256 nonzeros over long B rows
+    (several work items per row, B rows longer than a sub-tile).  Each with
+    buckets of 257..2048 products block-sorted (bsort 1) or accumulated by
+    the dense accumulator / fine level (bsort -1)."""
+    if case == "rmat":
+        A = B = inputs.rmat(14, 16, seed=1)
+        params = P(coarse_reorder=reorder, coarse_bucket_sort=bsort)
+    elif case == "rmat_forced_small_budget":
+        A = B = inputs.rmat(13, 16, seed=2)
+        params = P(coarse_reorder=reorder, coarse_bucket_sort=bsort, force_category=COARSE,
+                   max_scratch_bytes=8 << 20)
+    elif case == "ragged_coarse":
+        A = inputs.ragged(2000, 5000, 0, 40, seed=3, matrix_id=1)
+        B = inputs.ragged(5000, 60000, 0, 40, seed=3, matrix_id=2)
+        params = P(coarse_reorder=reorder, coarse_bucket_sort=bsort, force_category=COARSE,
+                   chunk_len_coarse_log2=10)
+    elif case == "wide_chunks":
+        A = inputs.ragged(1500, 5000, 5, 60, seed=4, matrix_id=1)
+        B = inputs.ragged(5000, 1 << 20, 5, 60, seed=4, matrix_id=2)
+        params = P(coarse_reorder=reorder, coarse_bucket_sort=bsort, force_category=COARSE,
+                   chunk_len_coarse_log2=15)
+    else:
+        A = inputs.ragged(40, 3000, 300, 700, seed=5, matrix_id=1)
+        B = inputs.ragged(3000, 200000, 500, 3000, seed=5, matrix_id=2)
+        params = P(coarse_reorder=reorder, coarse_bucket_sort=bsort, force_category=COARSE)
+    got = run_gpu(A, B, params, same=A is B)
+    assert got["info"]["rows_per_category"][COARSE] > 0
+    assert_parity(got, A, B)

@@ -192,3 +192,25 @@ def test_workspace_variants_allocate_nothing(kind, force):
     assert after == before
     _check_slab(ref.row_ptr, ref, r0, r1, sc[:m].cpu().numpy(), sv[:m].cpu().numpy())
     plan.free()
+
+
+def test_host_buffers_round_trip():
+    """magnus_host_alloc buffers are page-locked host memory: asynchronous
+    copies to and from the device return the data unchanged, and the region
+    is released with the last tensor using it."""
+    import torch
+    from paper_2501_07056_gb300 import magnus
+    x = np.arange(1 << 20, dtype=np.float64) * 0.5
+    h = magnus.host_copy(x)
+    assert h.is_pinned() and h.dtype == torch.float64 and np.array_equal(h.numpy(), x)
+    d = h.to("cuda", non_blocking=True)
+    out = magnus.host_empty(x.size, torch.float64)
+    assert out.is_pinned()
+    out.copy_(d * 2, non_blocking=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.numpy(), 2 * x)
+    e = magnus.host_empty(0, torch.int32)
+    assert e.numel() == 0
+    del h, out, e
+    with pytest.raises(magnus.MagnusError):
+        magnus._HostRegion(0)
