@@ -130,6 +130,8 @@ def parse_args(argv=None):
                    help="served workload: number of requests")
     p.add_argument("--rho", type=float, default=0.8,
                    help="served workload: offered load as a fraction of the one-call capacity")
+    p.add_argument("--rho-high", type=float, default=1.1,
+                   help="served workload: a second, overloading offered load (0 = skip)")
     p.add_argument("--autotune", type=int, default=0,
                    help="1 = run magnus_autotune (row sample of about 2^27 products, at most "
                         "16 runs) before the warm-up and time its choice")
@@ -811,6 +813,19 @@ def run_served(args, dist):
                          batches=srv.n_batches, gpu_launches=magnus.magnus_launch_count() - n0,
                          clocks=clk)
     b, o = out["batched"], out["single"]
+    high = None
+    if args.rho_high > 0:
+        # an offered load above the one-call capacity: the one-call queue
+        # grows for the whole run, continuous batching may still keep up
+        rate_h = args.rho_high * cap / mean_p
+        high = {"rho": args.rho_high, "arrival_rate_per_s": rate_h}
+        for mode in ("single", "batched"):
+            reqs = reqs_at(rate_h)
+            srv = serve.Server(work, params, mode=mode, n_streams=3, max_requests=64,
+                               max_products=1 << 30, device=dev)
+            srv.run(reqs)
+            high[mode] = dict(serve.latency_stats(reqs), requests_per_s=len(reqs) / srv.makespan,
+                              makespan_s=srv.makespan, batches=srv.n_batches)
     return {
         "metric": "served products/s", "value": b["requests_per_s"], "unit": "products/s",
         "n_gpus": dist.world, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * b["makespan_s"],
@@ -823,7 +838,7 @@ def run_served(args, dist):
                    "mean_products_per_request": float(mean_p),
                    "parallelism": "replicas" if dist.world > 1 else "single"},
         "latency_ms": {"p50": b["p50_ms"], "p99": b["p99_ms"]},
-        "served_batched": b, "served_one_call": o,
+        "served_batched": b, "served_one_call": o, "overload": high,
         "clocks": b["clocks"], "gpu_launches": b["gpu_launches"],
     }
 
@@ -993,7 +1008,7 @@ def _summary(res):
     """The headline keys of another workload's line, for detail.configs."""
     keep = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "roofline", "clocks",
             "gpu_launches", "latency_ms", "products_per_s", "one_call_per_product",
-            "served_one_call", "config")
+            "served_one_call", "overload", "config")
     out = {k: res[k] for k in keep if k in res}
     d = res.get("detail", {})
     for k in ("stage_ms", "t_over_t_ideal", "nnz_c", "stage_ms_untimed_step",

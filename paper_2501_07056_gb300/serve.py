@@ -112,7 +112,8 @@ class Scheduler:
 
 
 class _Flight:
-    __slots__ = ("reqs", "plan", "event", "outputs", "operands", "nbytes", "stream", "batch")
+    __slots__ = ("reqs", "plan", "event", "outputs", "operands", "nbytes", "stream", "batch",
+                 "single")
 
 
 class Server:
@@ -167,7 +168,10 @@ class Server:
         with torch.cuda.stream(stream):
             ops = [self.executor.operands(r, stream) for r in reqs]
             f.operands = ops
-            if self.mode == "single":
+            # a batch of one request takes the single-product path (packing
+            # its operands would only add work)
+            f.single = self.mode == "single" or len(reqs) == 1
+            if f.single:
                 A, B = ops[0]
                 plan = magnus.Plan(A, B, self.params, stream)
                 nnz = plan.symbolic()
@@ -198,7 +202,7 @@ class Server:
             r.done = now
         if self.keep_results:
             for i, r in enumerate(f.reqs):
-                if self.mode == "single":
+                if f.single:
                     self.results[r.rid] = _host_csr(f.plan.A.n_rows, f.plan.B.n_cols,
                                                     f.plan.c_row_ptr, f.outputs[0], f.outputs[1])
                 else:
