@@ -96,45 +96,6 @@ __device__ __forceinline__ uint32_t kmax(uint32_t a, uint32_t b) { return max(a,
 __device__ __forceinline__ uint64_t kmin(uint64_t a, uint64_t b) { return a < b ? a : b; }
 __device__ __forceinline__ uint64_t kmax(uint64_t a, uint64_t b) { return a < b ? b : a; }
 
-// Bitonic sort over aligned groups of W lanes holding R keys each (W * R
-// keys per group, W a power of two <= 32).  Logical position of (lane l in
-// its group, e) is q = l * R + e; partners at distance j >= R are in lane
-// l ^ (j / R) of the same group.
-template <int R, int W, typename K>
-__device__ __forceinline__ void group_bitonic_sort(K (&k)[R]) {
-  const int l = lane_id() & (W - 1);
-  constexpr int N = W * R;
-#pragma unroll
-  for (int size = 2; size <= N; size <<= 1) {
-#pragma unroll
-    for (int j = size >> 1; j > 0; j >>= 1) {
-      if (j >= R) {
-        const int pl = j / R;
-        // this lane keeps the max iff (descending block) xor (higher partner)
-        const bool desc = ((l * R) & size) != 0;
-        const bool take_max = desc != ((l & pl) != 0);
-#pragma unroll
-        for (int e = 0; e < R; ++e) {
-          const K other = __shfl_xor_sync(FULL, k[e], pl);
-          k[e] = take_max ? kmax(k[e], other) : kmin(k[e], other);
-        }
-      } else {
-        const bool lane_desc = (size >= R) && (((l * R) & size) != 0);
-#pragma unroll
-        for (int e = 0; e < R; ++e) {
-          if ((e & j) == 0) {
-            const bool desc = (size >= R) ? lane_desc : ((e & size) != 0);
-            const K lo = kmin(k[e], k[e + j]);
-            const K hi = kmax(k[e], k[e + j]);
-            k[e] = desc ? hi : lo;
-            k[e + j] = desc ? lo : hi;
-          }
-        }
-      }
-    }
-  }
-}
-
 // Merge of sorted runs: every lane of a group of W lanes holds R keys that
 // are already ascending (one sorted run per lane, positions q = l * R + e as
 // above).  The levels of the bitonic network below size 2R are skipped; each
@@ -181,6 +142,44 @@ __device__ __forceinline__ void group_merge_runs(K (&k)[R]) {
       }
     }
   }
+}
+
+// Bitonic sort over aligned groups of W lanes holding R keys each (W * R
+// keys per group, W a power of two <= 32).  Logical position of (lane l in
+// its group, e) is q = l * R + e.  Every level starts with a flip stage and
+// continues with ascending half-cleaners (as in group_merge_runs), so no
+// compare-exchange needs a direction: the levels below 2R run inside a
+// lane's registers and leave each lane with one ascending run, the levels
+// above merge the runs.
+template <int R, int W, typename K>
+__device__ __forceinline__ void group_bitonic_sort(K (&k)[R]) {
+#pragma unroll
+  for (int size = 2; size <= R; size <<= 1) {
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+      const int b = e & ~(size - 1);
+      const int m = b + size - 1 - (e - b);  // mirror of e in its block
+      if (e < m) {
+        const K lo = kmin(k[e], k[m]);
+        const K hi = kmax(k[e], k[m]);
+        k[e] = lo;
+        k[m] = hi;
+      }
+    }
+#pragma unroll
+    for (int j = size >> 2; j > 0; j >>= 1) {
+#pragma unroll
+      for (int e = 0; e < R; ++e) {
+        if ((e & j) == 0) {
+          const K lo = kmin(k[e], k[e + j]);
+          const K hi = kmax(k[e], k[e + j]);
+          k[e] = lo;
+          k[e + j] = hi;
+        }
+      }
+    }
+  }
+  if (W > 1) group_merge_runs<R, W>(k);
 }
 
 template <int E, typename K>

@@ -46,7 +46,7 @@ template <int W> struct RunLayout {
 };
 
 template <int E, typename K, bool NUMERIC, int NW>
-__global__ void __launch_bounds__(NW * 32, NUMERIC ? 5 : 4) k_sort_rows(SortArgs a) {
+__global__ void __launch_bounds__(NW * 32, (NUMERIC ? 20 : 32) / NW) k_sort_rows(SortArgs a) {
   constexpr int W = 4 * E;    // lanes per row
   constexpr int G = 32 / W;   // rows per warp
   constexpr int R = 8;        // products per lane

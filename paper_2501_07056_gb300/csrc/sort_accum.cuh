@@ -93,41 +93,76 @@ __device__ __forceinline__ int warp_merge_emit(const K (&k)[E], int n, const dou
 // products (kernels_sort_block.cu, kernels_coarse.cu).
 constexpr int BR = 8;  // keys per thread
 
-// Bitonic sort of NT * BR keys; thread t holds positions t * BR + e.  The
-// direction of a compare-exchange depends on bit k of the position and its
-// side on bit j; for k or j >= BR those bits come from t alone, so they are
-// computed once per stage (BR is a power of two).
+// Bitonic sort of NT * BR keys; thread t holds positions t * BR + e.  As in
+// group_bitonic_sort, every level starts with a flip stage (position q
+// against the mirror position of its block) and continues with ascending
+// half-cleaners, so no compare-exchange needs a direction.  Partners in the
+// same thread are swapped in registers, partners in the same warp exchanged
+// by shuffles, partners in other warps through s_key (NT * BR keys).
 template <int NT, typename K>
 __device__ __forceinline__ void block_sort_keys(K (&key)[BR], K* s_key) {
   constexpr int CAP = NT * BR;
   const int t = threadIdx.x;
   const int tb = t * BR;
+  // levels inside a thread: each thread's BR keys become one ascending run
 #pragma unroll
-  for (int k = 2; k <= CAP; k <<= 1) {
+  for (int size = 2; size <= BR; size <<= 1) {
 #pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      if (j < BR) {
-        const bool up_t = (tb & k) == 0;  // used when k >= BR
+    for (int e = 0; e < BR; ++e) {
+      const int b = e & ~(size - 1);
+      const int m = b + size - 1 - (e - b);
+      if (e < m) {
+        const K lo = key[e] < key[m] ? key[e] : key[m];
+        const K hi = key[e] < key[m] ? key[m] : key[e];
+        key[e] = lo;
+        key[m] = hi;
+      }
+    }
 #pragma unroll
-        for (int e = 0; e < BR; ++e) {
-          if ((e & j) == 0) {
-            const bool up = (k < BR) ? ((e & k) == 0) : up_t;
-            K& x = key[e];
-            K& y = key[e | j];
-            const K lo = x < y ? x : y;
-            const K hi = x < y ? y : x;
-            x = up ? lo : hi;
-            y = up ? hi : lo;
-          }
+    for (int j = size >> 2; j > 0; j >>= 1) {
+#pragma unroll
+      for (int e = 0; e < BR; ++e) {
+        if ((e & j) == 0) {
+          const K lo = key[e] < key[e + j] ? key[e] : key[e + j];
+          const K hi = key[e] < key[e + j] ? key[e + j] : key[e];
+          key[e] = lo;
+          key[e + j] = hi;
         }
+      }
+    }
+  }
+  // levels across threads: merge the runs
+#pragma unroll
+  for (int size = 2 * BR; size <= CAP; size <<= 1) {
+    {
+      const int pm = size / BR - 1;  // mirror thread within the block of `size`
+      const bool lower = (t & (size / BR / 2)) == 0;
+      K o[BR];
+      if (pm < 32) {
+#pragma unroll
+        for (int e = 0; e < BR; ++e) o[e] = __shfl_xor_sync(FULL, key[BR - 1 - e], pm);
       } else {
-        const bool take_min = (((tb & k) == 0) == ((tb & j) == 0));
-        if (j < 32 * BR) {
-          const int lm = j / BR;  // partner lane distance
+#pragma unroll
+        for (int e = 0; e < BR; ++e) s_key[tb + e] = key[e];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < BR; ++e) o[e] = s_key[(t ^ pm) * BR + (BR - 1 - e)];
+        __syncthreads();
+      }
+#pragma unroll
+      for (int e = 0; e < BR; ++e)
+        key[e] = lower ? (o[e] < key[e] ? o[e] : key[e]) : (o[e] > key[e] ? o[e] : key[e]);
+    }
+#pragma unroll
+    for (int j = size >> 2; j > 0; j >>= 1) {
+      if (j >= BR) {
+        const int pl = j / BR;  // partner thread distance
+        const bool lower = (t & pl) == 0;
+        if (pl < 32) {
 #pragma unroll
           for (int e = 0; e < BR; ++e) {
-            const K o = __shfl_xor_sync(FULL, key[e], lm);
-            key[e] = take_min ? (o < key[e] ? o : key[e]) : (o > key[e] ? o : key[e]);
+            const K o = __shfl_xor_sync(FULL, key[e], pl);
+            key[e] = lower ? (o < key[e] ? o : key[e]) : (o > key[e] ? o : key[e]);
           }
         } else {
 #pragma unroll
@@ -136,14 +171,23 @@ __device__ __forceinline__ void block_sort_keys(K (&key)[BR], K* s_key) {
 #pragma unroll
           for (int e = 0; e < BR; ++e) {
             const K o = s_key[(tb + e) ^ j];
-            key[e] = take_min ? (o < key[e] ? o : key[e]) : (o > key[e] ? o : key[e]);
+            key[e] = lower ? (o < key[e] ? o : key[e]) : (o > key[e] ? o : key[e]);
           }
           __syncthreads();
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < BR; ++e) {
+          if ((e & j) == 0) {
+            const K lo = key[e] < key[e + j] ? key[e] : key[e + j];
+            const K hi = key[e] < key[e + j] ? key[e + j] : key[e];
+            key[e] = lo;
+            key[e + j] = hi;
+          }
         }
       }
     }
   }
 }
-
 
 }  // namespace magnus
