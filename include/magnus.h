@@ -86,8 +86,9 @@ typedef struct {
  * sort_threshold      rows with P_i < sort_threshold use the sort accumulator
  *                     (Section 3.1, category 1).  Range 1..1025; 0 = 256
  *                     (the threshold of Section 4.1.1).  Rows of up to 256
- *                     products sort in one warp, rows of 257..1024 in one
- *                     thread block.
+ *                     products sort in a group of lanes, rows of 257..1024 in
+ *                     one warp (symbolic, and numeric up to 512 products) or
+ *                     one thread block (numeric, 513..1024 products).
  * force_category      -1 = automatic; otherwise every non-empty row is put in
  *                     that category (used to exercise each stage).
  * chunk_len_fine_log2 log2 of the fine chunk length (columns) for the numeric
@@ -122,12 +123,16 @@ typedef struct {
  *                     stream (NULL), else the launches run uncaptured; stage
  *                     timing (magnus_enable_timing) also runs uncaptured.
  *                     0 = no graph.
- * wide_sort_max       automatic categorisation only: a row whose column range
- *                     is too wide for the dense accumulator and that has at
- *                     most this many products uses the sort accumulator
- *                     instead of the fine/coarse levels (GPU rule; the paper
- *                     sends such rows to the reorder levels).  Range 1..1024;
- *                     0 = 1024; -1 = off.
+ * wide_sort_max       automatic categorisation only: a row with at least
+ *                     sort_threshold and at most wide_sort_max products uses
+ *                     the sort accumulator when its column range is too wide
+ *                     for the dense accumulator (instead of the fine/coarse
+ *                     levels, where the paper sends such rows) or more than
+ *                     twice its product count (a sparse row, which the block
+ *                     dense accumulator would spend its time zeroing and
+ *                     scanning).  GPU rules.  Range 1..1024; 0 = 1024;
+ *                     -1 = off (such rows take the dense accumulator when
+ *                     their range fits it, else the reorder levels).
  * chunk_accumulator   accumulator of the fine level's non-sort chunks:
  *                     0 = dense array and bitmap (Algorithm 1); 1 = hash map
  *                     (the extension of Algorithm 1 named in Section 2.1,

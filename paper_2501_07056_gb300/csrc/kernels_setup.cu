@@ -134,7 +134,10 @@ __global__ void k_rowinfo(Csr A, Csr B, CatParams cp, int64_t* __restrict__ P,
                            p < ((int64_t)1 << 31);
       if (cp.force == MAGNUS_CAT_COARSE) b = BIN_COARSE;
       else if (cp.force == MAGNUS_CAT_FINE) b = fine_ok ? BIN_FINE : BIN_COARSE;
-      else if (dense_ok) b = BIN_DENSE;
+      // automatic: a row of at most wide_sort_max products that fills less
+      // than half of its column range sorts instead (the dense
+      // accumulator's work follows the range, the sort's the products)
+      else if (dense_ok && (cp.force >= 0 || p > cp.wide_sort_max || range <= 2 * p)) b = BIN_DENSE;
       else if (cp.force < 0 && p <= cp.wide_sort_max) b = sort_bin(p);
       else b = (cp.prefer_fine && fine_ok) ? BIN_FINE : BIN_COARSE;
     }

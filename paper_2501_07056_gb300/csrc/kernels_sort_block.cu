@@ -1,59 +1,73 @@
 // Sort-category rows of 257..1024 products (Section 3.1, category 1, with the
-// sort accumulator of Algorithm 2 widened to a thread block).
+// sort accumulator of Algorithm 2 widened past one lane group).
 //
-// A row of bin SORT512 / SORT1024 is handled by one block of CAP/8 threads
-// (64 or 128), eight products per thread.
-//
-// Symbolic: the products' (column, slot) keys are generated from A and B and
-// sorted by a bitonic network (partners within a thread are swapped in
-// registers, partners within a warp exchanged by shuffles, partners in other
-// warps through shared memory); the runs of equal columns are counted
-// (precise prediction, Section 2.1) and the sorted slot order is stored, two
-// bytes per product.
+// Symbolic (bins SORT512 and SORT1024): one warp per row.  The products'
+// (column, slot) keys are generated from A and B, CAP/32 per lane, and
+// sorted by the warp's register network; the runs of equal columns are
+// counted (precise prediction, Section 2.1) and the sorted slot order is
+// stored, two bytes per product.
 //
 // Numeric: the products are generated again with their values, parked in
 // shared memory by slot, and visited in the recorded order: equal columns
 // are adjacent with their slots ascending, so a run is summed in the
-// traversal order of Algorithm 1.  Consecutive threads take consecutive
-// sorted positions and write consecutive entries of the row of C.
+// traversal order of Algorithm 1.  Rows of at most 512 products take one
+// warp each; rows of 513..1024 one block of 128 threads (eight slots per
+// thread), which keeps the row's values in shared memory instead of
+// registers.  Consecutive threads take consecutive sorted positions and
+// write consecutive entries of the row of C.
 //
-// Blocks are persistent: each takes rows idx = blockIdx.x, + gridDim.x, ...
+// Warps and blocks are persistent: each takes rows idx, idx + its stride, ...
 #include "sort_accum.cuh"
 
 namespace magnus {
 
 namespace {
 
-template <int CAPLOG, typename K, bool NUMERIC>
-__global__ void __launch_bounds__((1 << CAPLOG) / BR) k_sort_rows_block(SortArgs a) {
+// Numeric pass of the SORT1024 bin: one block of CAP/8 threads per row,
+// eight slots per thread (slot s = e*NT + t).  The steps of the warp kernel
+// below, with the segment table, the slots and the bitmaps shared by the
+// block's warps: segments by a block scan, the segment of a slot by the
+// bitmap's prefix popcount, the slots parked over the segment table once
+// every gather has returned, run heads by comparing each position's column
+// with the previous position's (a shuffle, or shared memory across warps).
+template <int CAPLOG>
+__global__ void __launch_bounds__((1 << CAPLOG) / BR) k_sort_block_numeric(SortArgs a) {
   constexpr int CAP = 1 << CAPLOG;
   constexpr int NT = CAP / BR;
   constexpr int NWB = NT / 32;
-  constexpr int SB = CAPLOG;  // slot bits of a key
   constexpr int HW = CAP / 32;
-  using KT = KeyTraits<K>;
-  __shared__ K s_key[NUMERIC ? 1 : CAP];
-  __shared__ int32_t s_start[CAP + 1];  // first slot of each non-empty segment
-  __shared__ int64_t s_bs[CAP];         // B.rowPtr of the segment's B row
-  __shared__ double s_av[NUMERIC ? CAP : 1];
-  __shared__ double s_val[NUMERIC ? CAP : 1];    // product value by slot
-  __shared__ int32_t s_col[NUMERIC ? CAP : 1];   // product column by slot
-  __shared__ uint16_t s_perm[NUMERIC ? CAP : 1]; // slot at each sorted position
-  __shared__ uint32_t s_head[HW];
-  __shared__ int32_t s_pw[HW];
+  struct SegT {
+    int64_t base[CAP];  // B.rowPtr of the segment's B row minus its first slot
+    double av[CAP];     // the A value that scales the segment
+  };
+  struct SlotT {
+    double val[CAP];    // product value by slot
+    int32_t col[CAP];   // product column by slot
+  };
+  union Area {
+    SegT seg;
+    SlotT slot;
+  };
+  __shared__ Area ar;
+  __shared__ uint16_t s_perm[CAP];  // slot at each sorted position
+  __shared__ uint32_t s_head[HW];   // bit s: a segment other than the first starts at s
+  __shared__ int32_t s_pw[HW];      // segments starting in earlier words
+  __shared__ uint32_t s_qh[HW];     // bit q: a run of equal columns starts at q
+  __shared__ int32_t s_qw[HW];      // runs starting in earlier words
   __shared__ int32_t s_ws[NWB + 1];
   __shared__ int32_t s_ws2[NWB + 1];
   const int t = threadIdx.x, lane = lane_id(), w = warp_id();
   // rows [first, n) of the bin's list: all of them, or a row range's
-  const int64_t first = (NUMERIC && a.range) ? a.range[0] : 0;
-  const int64_t n = (NUMERIC && a.range) ? a.range[1] : a.n_rows;
-  const int64_t cbase = (NUMERIC && a.c_base) ? *a.c_base : 0;
+  const int64_t first = a.range ? a.range[0] : 0;
+  const int64_t n = a.range ? a.range[1] : a.n_rows;
+  const int64_t cbase = a.c_base ? *a.c_base : 0;
 
   for (int64_t idx = first + blockIdx.x; idx < n; idx += gridDim.x) {
     const RowDesc d = a.desc[idx];
     const int64_t poff = a.perm2_off[idx];
-    // 1. segments: the non-empty B rows referenced by the row, in stored
-    //    order, with their first slots (block scan of the lengths)
+    if (t < HW) s_head[t] = 0u;
+    __syncthreads();
+    // 1. segments: the non-empty B rows in stored order, their first slots
     int nseg = 0, P = 0;
     for (int j0 = 0; j0 < d.na; j0 += NT) {
       const int j = j0 + t;
@@ -64,7 +78,7 @@ __global__ void __launch_bounds__((1 << CAPLOG) / BR) k_sort_rows_block(SortArgs
         const uint64_t sg = a.seg[d.as + j];
         L = seg_length(sg);
         bs = seg_start(sg);
-        if (NUMERIC) av = a.A.val[d.as + j];
+        av = a.A.val[d.as + j];
       }
       const int nz = L > 0 ? 1 : 0;
       const int incL = warp_inclusive_scan(L);
@@ -84,149 +98,120 @@ __global__ void __launch_bounds__((1 << CAPLOG) / BR) k_sort_rows_block(SortArgs
       }
       if (L > 0) {
         const int g = nseg + offZ + incZ - 1;
-        s_start[g] = P + offL + incL - L;
-        s_bs[g] = bs;
-        if (NUMERIC) s_av[g] = av;
+        const int off = P + offL + incL - L;
+        ar.seg.base[g] = bs - off;
+        ar.seg.av[g] = av;
+        if (g > 0) atomicOr(&s_head[off >> 5], 1u << (off & 31));
       }
       nseg += totZ;
       P += totL;
       __syncthreads();
     }
-    // 2. expand: slot s = e * NT + t (consecutive threads read consecutive
-    //    entries of a B row); all gathers are issued before any is used
-    int64_t kk[BR];
-    int gg[BR];
+    if (w == 0) {
+      const uint32_t hw = lane < HW ? s_head[lane] : 0u;
+      const int c = __popc(hw);
+      const int inc = warp_inclusive_scan(c);
+      if (lane < HW) s_pw[lane] = inc - c;
+    }
+    __syncthreads();
+    // 2. gather slot s = e*NT + t (consecutive threads read consecutive
+    //    entries of a B row); all loads issued before any is used
+    int32_t cg[BR];
+    double vg[BR];
+    uint32_t pg[BR];
 #pragma unroll
     for (int e = 0; e < BR; ++e) {
       const int s = e * NT + t;
-      kk[e] = -1;
-      gg[e] = 0;
+      cg[e] = 0;
+      vg[e] = 0.0;
+      pg[e] = 0u;
       if (s < P) {
-        const int g = upper_bound_i32(s_start, nseg, s) - 1;
-        gg[e] = g;
-        kk[e] = s_bs[g] + (s - s_start[g]);
+        const int g = s_pw[s >> 5] + __popc(s_head[s >> 5] & ((2u << lane) - 1u));
+        const int64_t kk = ar.seg.base[g] + s;
+        cg[e] = __ldg(a.B.col + kk);
+        vg[e] = ar.seg.av[g] * __ldg(a.B.val + kk);
+        pg[e] = a.perm2[poff + s];
       }
     }
-    int32_t cg[BR];
-    double vg[BR];
-    uint16_t pg[BR];
+    __syncthreads();  // the segment table is consumed; its space takes the slots
 #pragma unroll
     for (int e = 0; e < BR; ++e) {
-      cg[e] = kk[e] >= 0 ? __ldg(a.B.col + kk[e]) : 0;
-      if (NUMERIC) {
-        vg[e] = kk[e] >= 0 ? __ldg(a.B.val + kk[e]) : 0.0;
-        const int q = e * NT + t;
-        pg[e] = q < P ? a.perm2[poff + q] : (uint16_t)0;
+      const int s = e * NT + t;
+      if (s < P) {
+        ar.slot.col[s] = cg[e];
+        ar.slot.val[s] = vg[e];
+        s_perm[s] = (uint16_t)pg[e];
       }
     }
-    if (!NUMERIC) {
-      K key[BR];
+    __syncthreads();
+    // 3. run heads in position order (position q = e*NT + t holds slot pg[e])
+    int32_t cq[BR];
+    uint32_t qh[BR];
 #pragma unroll
-      for (int e = 0; e < BR; ++e) {
-        const int s = e * NT + t;
-        key[e] = (s < P) ? KT::template make<SB>(cg[e], s) : ~K(0);
-      }
-      // 3s. sort, store the order, count the runs of equal columns
-      block_sort_keys<NT>(key, s_key);
+    for (int e = 0; e < BR; ++e) {
+      const int q = e * NT + t;
+      const bool in = q < P;
+      cq[e] = in ? ar.slot.col[pg[e]] : 0;
+      int32_t up = __shfl_up_sync(FULL, cq[e], 1);
+      if (lane == 0) up = (in && q > 0) ? ar.slot.col[s_perm[q - 1]] : -1;
+      qh[e] = __ballot_sync(FULL, in && cq[e] != up);
+      if (lane == 0) s_qh[q >> 5] = qh[e];
+    }
+    __syncthreads();
+    if (w == 0) {
+      const uint32_t hw = lane < HW ? s_qh[lane] : 0u;
+      const int c = __popc(hw);
+      const int inc = warp_inclusive_scan(c);
+      if (lane < HW) s_qw[lane] = inc - c;
+    }
+    __syncthreads();
+    // 4. one output per run, written at C.rowPtr + the run's rank
+    const int64_t crp = a.c_rp[d.row] - cbase;
 #pragma unroll
-      for (int e = 0; e < BR; ++e) {
-        const int q = t * BR + e;
-        s_key[q] = key[e];
-        if (q < P) a.perm2[poff + q] = (uint16_t)KT::template slot<SB>(key[e]);
-      }
-      __syncthreads();
-      uint32_t hb = 0;
-#pragma unroll
-      for (int e = 0; e < BR; ++e) {
-        const int q = t * BR + e;
-        const int32_t c = KT::template col<SB>(key[e]);
-        const int32_t pc = q == 0 ? -1 : KT::template col<SB>(s_key[q - 1]);
-        if (q < P && (q == 0 || c != pc)) hb |= 1u << e;
-      }
-      int c = __popc(hb);
-      c = warp_sum(c);
-      if (lane == 0) s_ws[w] = c;
-      __syncthreads();
-      if (t == 0) {
-        int tot = 0;
-        for (int i = 0; i < NWB; ++i) tot += s_ws[i];
-        a.out_cnt[d.row] = tot;
-      }
-    } else {
-      // 3n. replay the recorded order
-#pragma unroll
-      for (int e = 0; e < BR; ++e) {
-        const int s = e * NT + t;
-        if (s < P) {
-          s_col[s] = cg[e];
-          s_val[s] = s_av[gg[e]] * vg[e];
-          s_perm[s] = pg[e];  // position s of the sorted order holds slot pg[e]
+    for (int e = 0; e < BR; ++e) {
+      const int q = e * NT + t;
+      const uint32_t h = qh[e];
+      if ((h >> lane) & 1u) {
+        const int o = s_qw[q >> 5] + __popc(h & ((1u << lane) - 1u));
+        double acc = ar.slot.val[pg[e]];
+        const uint32_t next_head =
+            lane < 31 ? (h >> (lane + 1)) & 1u : (q + 1 < P ? s_qh[(q + 1) >> 5] & 1u : 1u);
+        if (!next_head) {
+          for (int q2 = q + 1; q2 < P && !((s_qh[q2 >> 5] >> (q2 & 31)) & 1u); ++q2)
+            acc += ar.slot.val[s_perm[q2]];
         }
-      }
-      __syncthreads();
-      // run heads in position-major order: word m of the head bitmap covers
-      // positions 32m..32m+31, one warp's lanes for one e
-      int32_t cq[BR];
-#pragma unroll
-      for (int e = 0; e < BR; ++e) {
-        const int q = e * NT + t;
-        cq[e] = q < P ? s_col[pg[e]] : 0;
-        const int32_t pc = (q == 0 || q >= P) ? -1 : s_col[s_perm[q - 1]];
-        const unsigned hb = __ballot_sync(FULL, q < P && cq[e] != pc);
-        if (lane == 0) s_head[(e * NT + w * 32) >> 5] = hb;
-      }
-      __syncthreads();
-      if (w == 0) {
-        const int c = lane < HW ? __popc(s_head[lane]) : 0;
-        const int inc = warp_inclusive_scan(c);
-        if (lane < HW) s_pw[lane] = inc - c;
-      }
-      __syncthreads();
-      const int64_t crp = a.c_rp[d.row] - cbase;
-#pragma unroll
-      for (int e = 0; e < BR; ++e) {
-        const int q = e * NT + t;
-        const uint32_t hw = q < P ? s_head[q >> 5] : 0u;
-        if ((hw >> (q & 31)) & 1u) {
-          const int o = s_pw[q >> 5] + __popc(hw & ((1u << (q & 31)) - 1u));
-          const int32_t c = cq[e];
-          double acc = s_val[pg[e]];
-          for (int q2 = q + 1; q2 < P; ++q2) {
-            const int s2 = s_perm[q2];
-            if (s_col[s2] != c) break;
-            acc += s_val[s2];
-          }
-          a.c_col[crp + o] = c;
-          a.c_val[crp + o] = acc;
-        }
+        a.c_col[crp + o] = cq[e];
+        a.c_val[crp + o] = acc;
       }
     }
     __syncthreads();
   }
 }
 
-// Symbolic pass of the SORT512 bin with one warp per row: sixteen keys per
-// lane, sorted by the warp's register network (group_bitonic_sort over 32
-// lanes: swaps in registers below distance 16, shuffles above), so neither
-// shared-memory exchanges nor block barriers are needed.  Segments are found
-// as in the lane-group kernel (head bits at segment starts, prefix popcounts);
-// the distinct columns are counted and the sorted slot order is stored, two
-// bytes per product, for the block numeric replay.
-constexpr int S5_NW = 4;
+// Symbolic pass of the SORT512 and SORT1024 bins with one warp per row:
+// CAP/32 keys per lane, sorted by the warp's register network
+// (group_bitonic_sort over 32 lanes: swaps in registers below distance CAP/32,
+// shuffles above), so neither shared-memory exchanges nor block barriers are
+// needed.  Segments are found as in the lane-group kernel (head bits at
+// segment starts, prefix popcounts); the distinct columns are counted and
+// the sorted slot order is stored, two bytes per product, for the replay.
+constexpr int SW_NW = 4;
 
-template <typename K>
-__global__ void __launch_bounds__(S5_NW * 32) k_sort512_symbolic(SortArgs a) {
-  constexpr int CAP = 512, R = 16, SB = 9, HW = CAP / 32;
+template <int CAPLOG, typename K>
+__global__ void __launch_bounds__(SW_NW * 32) k_sortw_symbolic(SortArgs a) {
+  constexpr int CAP = 1 << CAPLOG, R = CAP / 32, SB = CAPLOG, HW = CAP / 32;
   using KT = KeyTraits<K>;
-  __shared__ uint16_t s_off[S5_NW][CAP];  // first slot of each non-empty segment
-  __shared__ int64_t s_bs[S5_NW][CAP];    // B.rowPtr of the segment's B row
-  __shared__ uint32_t s_head[S5_NW][HW];  // bit s: a segment other than the first starts at s
+  __shared__ uint16_t s_off[SW_NW][CAP];  // first slot of each non-empty segment
+  __shared__ int64_t s_bs[SW_NW][CAP];    // B.rowPtr of the segment's B row
+  __shared__ uint32_t s_head[SW_NW][HW];  // bit s: a segment other than the first starts at s
+  __shared__ int32_t s_pw[SW_NW][HW];     // segments starting in earlier words
   const int lane = lane_id(), w = warp_id();
-  const int64_t nwarps = (int64_t)gridDim.x * S5_NW;
-  for (int64_t idx = (int64_t)blockIdx.x * S5_NW + w; idx < a.n_rows; idx += nwarps) {
+  const int64_t nwarps = (int64_t)gridDim.x * SW_NW;
+  for (int64_t idx = (int64_t)blockIdx.x * SW_NW + w; idx < a.n_rows; idx += nwarps) {
     const RowDesc d = a.desc[idx];
     const int64_t poff = a.perm2_off[idx];
     if (lane < HW) s_head[w][lane] = 0u;
+    __syncwarp();
     int nseg = 0, P = 0;
     for (int j0 = 0; j0 < d.na; j0 += 32) {
       const int j = j0 + lane;
@@ -241,36 +226,32 @@ __global__ void __launch_bounds__(S5_NW * 32) k_sort512_symbolic(SortArgs a) {
       const int inc = warp_inclusive_scan(L);
       if (L > 0) {
         const int g = nseg + __popc(nz & ((1u << lane) - 1u));
-        s_off[w][g] = (uint16_t)(P + inc - L);
+        const int off = P + inc - L;
+        s_off[w][g] = (uint16_t)off;
         s_bs[w][g] = bs;
+        if (g > 0) atomicOr(&s_head[w][off >> 5], 1u << (off & 31));
       }
       nseg += __popc(nz);
       P += __shfl_sync(FULL, inc, 31);
     }
     __syncwarp();
-    for (int g = 1 + lane; g < nseg; g += 32) {
-      const int off = s_off[w][g];
-      atomicOr(&s_head[w][off >> 5], 1u << (off & 31));
+    {
+      const uint32_t hw = lane < HW ? s_head[w][lane] : 0u;
+      const int c = __popc(hw);
+      const int inc = warp_inclusive_scan(c);
+      if (lane < HW) s_pw[w][lane] = inc - c;
     }
     __syncwarp();
-    uint32_t hw[HW];
-    int pw[HW];
-    {
-      int cum = 0;
-#pragma unroll
-      for (int i = 0; i < HW; ++i) {
-        hw[i] = s_head[w][i];
-        pw[i] = cum;
-        cum += __popc(hw[i]);
-      }
-    }
     // slot s = e*32 + lane; all gathers issued before any is used
     int32_t cg[R];
 #pragma unroll
     for (int e = 0; e < R; ++e) {
       const int s = e * 32 + lane;
-      const int g = pw[e] + __popc(hw[e] & ((2u << lane) - 1u));
-      cg[e] = s < P ? __ldg(a.B.col + s_bs[w][g] + (s - s_off[w][g])) : 0;
+      cg[e] = 0;
+      if (s < P) {
+        const int g = s_pw[w][e] + __popc(s_head[w][e] & ((2u << lane) - 1u));
+        cg[e] = __ldg(a.B.col + s_bs[w][g] + (s - s_off[w][g]));
+      }
     }
     K key[R];
 #pragma unroll
@@ -297,25 +278,190 @@ __global__ void __launch_bounds__(S5_NW * 32) k_sort512_symbolic(SortArgs a) {
   }
 }
 
-template <typename K>
-cudaError_t launch_sort512_symbolic(const SortArgs& a, int num_sms, cudaStream_t s) {
+// Numeric pass of the SORT512 bin with one warp per row.  The segment of
+// slot s = e*32 + lane is found from the segment-start bitmap (a population
+// count, no search); its B entry is gathered, scaled by the row's A value
+// and parked in shared memory by slot, over the segment table, which is no
+// longer needed once every gather has returned.  Position q = e*32 + lane of
+// the recorded order then reads slot perm2[q]; a position starts a run of
+// equal columns when its column differs from the previous position's (one
+// shuffle).  A run head whose next position is also a head (the common
+// case) writes its product at once; a longer run is summed in position
+// order, which is slot order within the run (Algorithm 1's traversal order).
+// No block barriers: the warps of a block are independent.
+constexpr int S5N_NW = 4;
+
+__global__ void __launch_bounds__(S5N_NW * 32, 4) k_sort512_numeric(SortArgs a) {
+  constexpr int CAP = 512, R = CAP / 32, HW = CAP / 32;
+  struct SegT {
+    int64_t base[CAP];  // B.rowPtr of the segment's B row minus its first slot
+    double av[CAP];     // the A value that scales the segment
+  };
+  struct SlotT {
+    double val[CAP];    // product value by slot
+    int32_t col[CAP];   // product column by slot
+  };
+  union Area {
+    SegT seg;
+    SlotT slot;
+  };
+  __shared__ Area s_area[S5N_NW];
+  __shared__ uint16_t s_perm[S5N_NW][CAP];  // slot at each sorted position
+  __shared__ uint32_t s_head[S5N_NW][HW];   // bit s: a segment other than the first starts at s
+  __shared__ int32_t s_pw[S5N_NW][HW];      // segments starting in earlier words
+  __shared__ uint32_t s_qh[S5N_NW][HW];     // bit q: a run of equal columns starts at q
+  const int lane = lane_id(), w = warp_id();
+  const int64_t first = a.range ? a.range[0] : 0;
+  const int64_t n = a.range ? a.range[1] : a.n_rows;
+  const int64_t cbase = a.c_base ? *a.c_base : 0;
+  const int64_t nwarps = (int64_t)gridDim.x * S5N_NW;
+  Area& ar = s_area[w];
+  for (int64_t idx = first + (int64_t)blockIdx.x * S5N_NW + w; idx < n; idx += nwarps) {
+    const RowDesc d = a.desc[idx];
+    const int64_t poff = a.perm2_off[idx];
+    if (lane < HW) s_head[w][lane] = 0u;
+    __syncwarp();
+    // 1. segments: the non-empty B rows in stored order, their first slots
+    int nseg = 0, P = 0;
+    for (int j0 = 0; j0 < d.na; j0 += 32) {
+      const int j = j0 + lane;
+      int L = 0;
+      int64_t bs = 0;
+      double av = 0.0;
+      if (j < d.na) {
+        const uint64_t sg = a.seg[d.as + j];
+        L = seg_length(sg);
+        bs = seg_start(sg);
+        av = a.A.val[d.as + j];
+      }
+      const unsigned nz = __ballot_sync(FULL, L > 0);
+      const int inc = warp_inclusive_scan(L);
+      if (L > 0) {
+        const int g = nseg + __popc(nz & ((1u << lane) - 1u));
+        const int off = P + inc - L;
+        ar.seg.base[g] = bs - off;
+        ar.seg.av[g] = av;
+        if (g > 0) atomicOr(&s_head[w][off >> 5], 1u << (off & 31));
+      }
+      nseg += __popc(nz);
+      P += __shfl_sync(FULL, inc, 31);
+    }
+    __syncwarp();
+    {
+      const uint32_t hw = lane < HW ? s_head[w][lane] : 0u;
+      const int c = __popc(hw);
+      const int inc = warp_inclusive_scan(c);
+      if (lane < HW) s_pw[w][lane] = inc - c;
+    }
+    __syncwarp();
+    // 2. gather slot s = e*32 + lane; all loads issued before any is used
+    int32_t cg[R];
+    double vg[R];
+    uint32_t pg[R];
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+      const int s = e * 32 + lane;
+      cg[e] = 0;
+      vg[e] = 0.0;
+      pg[e] = 0u;
+      if (s < P) {
+        const int g = s_pw[w][e] + __popc(s_head[w][e] & ((2u << lane) - 1u));
+        const int64_t kk = ar.seg.base[g] + s;
+        cg[e] = __ldg(a.B.col + kk);
+        vg[e] = ar.seg.av[g] * __ldg(a.B.val + kk);
+        pg[e] = a.perm2[poff + s];
+      }
+    }
+    __syncwarp();  // the segment table is consumed; its space takes the slots
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+      const int s = e * 32 + lane;
+      if (s < P) {
+        ar.slot.col[s] = cg[e];
+        ar.slot.val[s] = vg[e];
+        s_perm[w][s] = (uint16_t)pg[e];
+      }
+    }
+    __syncwarp();
+    // 3. run heads in position order
+    int32_t cq[R];
+    uint32_t qh[R];
+    int32_t tail = -1;  // column at the position before e*32
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+      const int q = e * 32 + lane;
+      const bool in = q < P;
+      cq[e] = in ? ar.slot.col[pg[e]] : 0;
+      int32_t up = __shfl_up_sync(FULL, cq[e], 1);
+      if (lane == 0) up = tail;
+      qh[e] = __ballot_sync(FULL, in && cq[e] != up);
+      tail = __shfl_sync(FULL, cq[e], 31);
+    }
+    if (lane < HW) {
+      uint32_t h = 0u;
+#pragma unroll
+      for (int e = 0; e < R; ++e) h = lane == e ? qh[e] : h;
+      s_qh[w][lane] = h;
+    }
+    __syncwarp();
+    // 4. one output per run, written at C.rowPtr + the run's rank
+    const int64_t crp = a.c_rp[d.row] - cbase;
+    int base_o = 0;
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+      const int q = e * 32 + lane;
+      const uint32_t h = qh[e];
+      if ((h >> lane) & 1u) {
+        const int o = base_o + __popc(h & ((1u << lane) - 1u));
+        double acc = ar.slot.val[pg[e]];
+        const uint32_t next_head =
+            lane < 31 ? (h >> (lane + 1)) & 1u : (e + 1 < R ? qh[e + 1 < R ? e + 1 : e] & 1u : 1u);
+        if (!next_head) {
+          for (int q2 = q + 1; q2 < P && !((s_qh[w][q2 >> 5] >> (q2 & 31)) & 1u); ++q2)
+            acc += ar.slot.val[s_perm[w][q2]];
+        }
+        a.c_col[crp + o] = cq[e];
+        a.c_val[crp + o] = acc;
+      }
+      base_o += __popc(h);
+    }
+    __syncwarp();
+  }
+}
+
+cudaError_t launch_sort512_numeric(const SortArgs& a, int num_sms, cudaStream_t s) {
   int per_sm = 0;
-  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort512_symbolic<K>,
-                                                                  S5_NW * 32, 0);
+  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort512_numeric,
+                                                                  S5N_NW * 32, 0);
   if (err != cudaSuccess) return err;
   if (per_sm < 1) per_sm = 1;
-  int64_t blocks = (a.n_rows + S5_NW - 1) / S5_NW;
+  int64_t blocks = (a.n_rows + S5N_NW - 1) / S5N_NW;
   const int64_t cap = (int64_t)num_sms * per_sm;
   if (blocks > cap) blocks = cap;
-  k_sort512_symbolic<K><<<(unsigned)blocks, S5_NW * 32, 0, s>>>(a);
+  k_sort512_numeric<<<(unsigned)blocks, S5N_NW * 32, 0, s>>>(a);
   count_launch();
   return cudaGetLastError();
 }
 
-template <int CAPLOG, typename K, bool NUMERIC>
-cudaError_t launch_block(const SortArgs& a, int num_sms, cudaStream_t s) {
+template <int CAPLOG, typename K>
+cudaError_t launch_sortw_symbolic(const SortArgs& a, int num_sms, cudaStream_t s) {
+  auto kern = k_sortw_symbolic<CAPLOG, K>;
+  int per_sm = 0;
+  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SW_NW * 32, 0);
+  if (err != cudaSuccess) return err;
+  if (per_sm < 1) per_sm = 1;
+  int64_t blocks = (a.n_rows + SW_NW - 1) / SW_NW;
+  const int64_t cap = (int64_t)num_sms * per_sm;
+  if (blocks > cap) blocks = cap;
+  kern<<<(unsigned)blocks, SW_NW * 32, 0, s>>>(a);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int CAPLOG>
+cudaError_t launch_block_numeric(const SortArgs& a, int num_sms, cudaStream_t s) {
   constexpr int NT = (1 << CAPLOG) / BR;
-  auto kern = k_sort_rows_block<CAPLOG, K, NUMERIC>;
+  auto kern = k_sort_block_numeric<CAPLOG>;
   int per_sm = 0;
   cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, 0);
   if (err != cudaSuccess) return err;
@@ -335,17 +481,12 @@ cudaError_t launch_sort_rows_block(int bin, bool numeric, const SortArgs& a, int
   if (a.n_rows == 0) return cudaSuccess;
   const bool big = bin == BIN_SORT1024;
   if (numeric)  // the replay holds no keys
-    return big ? launch_block<10, uint32_t, true>(a, num_sms, s)
-               : launch_block<9, uint32_t, true>(a, num_sms, s);
-  if (!big)  // rows of at most 512 products: one warp per row
-    return a.key32 ? launch_sort512_symbolic<uint32_t>(a, num_sms, s)
-                   : launch_sort512_symbolic<uint64_t>(a, num_sms, s);
-  if (a.key32) {
-    return big ? launch_block<10, uint32_t, false>(a, num_sms, s)
-               : launch_block<9, uint32_t, false>(a, num_sms, s);
-  }
-  return big ? launch_block<10, uint64_t, false>(a, num_sms, s)
-             : launch_block<9, uint64_t, false>(a, num_sms, s);
+    return big ? launch_block_numeric<10>(a, num_sms, s) : launch_sort512_numeric(a, num_sms, s);
+  if (a.key32)  // symbolic: one warp per row
+    return big ? launch_sortw_symbolic<10, uint32_t>(a, num_sms, s)
+               : launch_sortw_symbolic<9, uint32_t>(a, num_sms, s);
+  return big ? launch_sortw_symbolic<10, uint64_t>(a, num_sms, s)
+             : launch_sortw_symbolic<9, uint64_t>(a, num_sms, s);
 }
 
 }  // namespace magnus

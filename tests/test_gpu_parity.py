@@ -78,6 +78,41 @@ def test_block_sort_bins(T, wide):
     assert cats[SORT] == int(((Prow > 0) & (Prow <= limit)).sum())
 
 
+@pytest.mark.parametrize("b_cols", [700, 4000])
+@pytest.mark.parametrize("wide", [0, -1])
+def test_sparse_rows_sort_rule(b_cols, wide):
+    # rows of about 100-1600 products whose column range fits the dense
+    # accumulator: rows with at least sort_threshold products take the dense
+    # accumulator only when they fill half of their range (wide_sort_max on),
+    # else the sort bins; with the rule off every such row is dense
+    A = inputs.ragged(2000, 3000, 8, 40, seed=9, matrix_id=1)
+    B = inputs.ragged(3000, b_cols, 8, 40, seed=9, matrix_id=2)
+    got = run_gpu(A, B, P(wide_sort_max=wide, validate=1))
+    assert_parity(got, A, B)
+    info = got["info"]
+    Bl = np.diff(B.row_ptr)
+    first = np.where(Bl > 0, B.col[np.minimum(B.row_ptr[:-1], B.col.size - 1)], np.iinfo(np.int32).max)
+    last = np.where(Bl > 0, B.col[np.maximum(B.row_ptr[1:] - 1, 0)], -1)
+    n_sort = n_dense = 0
+    for i in range(A.n_rows):
+        js = A.col[A.row_ptr[i]:A.row_ptr[i + 1]]
+        p = int(Bl[js].sum())
+        if p == 0:
+            continue
+        rng = int(last[js].max()) - int(first[js].min()) + 1
+        lim = 1024 if wide == 0 else 0
+        if p < info["sort_threshold"]:
+            n_sort += 1
+        elif rng <= info["dense_cols"] and (p > lim or rng <= 2 * p):
+            n_dense += 1
+        elif p <= lim:
+            n_sort += 1
+    cats = info["rows_per_category"]
+    assert cats[SORT] == n_sort and cats[DENSE] == n_dense
+    if wide == 0:
+        assert cats[SORT] > 0 and (b_cols > 1000 or cats[DENSE] > 0)
+
+
 def test_block_sort_64bit_keys():
     # 2^27 columns: column + 10 slot bits exceed 32 bits
     A = inputs.ragged(1500, 3000, 10, 40, seed=6, matrix_id=1)
