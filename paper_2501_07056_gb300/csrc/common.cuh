@@ -182,6 +182,54 @@ __device__ __forceinline__ void group_bitonic_sort(K (&k)[R]) {
   if (W > 1) group_merge_runs<R, W>(k);
 }
 
+// Batcher's odd-even merge sort (Batcher 1968) of N keys in one thread's
+// registers, ascending; N a power of two.  For N = 32 it takes 191
+// compare-exchanges where a bitonic network takes 240.  Stage p merges
+// sorted runs of length p; within it, comparators at distance q join keys
+// whose indices fall in the same block of 2p.  The comparator list is built
+// at compile time, so the unrolled loop indexes registers only.
+template <int N>
+struct OddEvenNet {
+  static constexpr int count() {
+    int c = 0;
+    for (int p = 1; p < N; p <<= 1)
+      for (int q = p; q >= 1; q >>= 1)
+        for (int j = q % p; j + q < N; j += 2 * q)
+          for (int i = 0; i < q && i + j + q < N; ++i)
+            if ((i + j) / (2 * p) == (i + j + q) / (2 * p)) ++c;
+    return c;
+  }
+  static constexpr int NC = count();
+  struct Table {
+    unsigned char lo[NC > 0 ? NC : 1], hi[NC > 0 ? NC : 1];
+  };
+  static constexpr Table table() {
+    Table t{};
+    int c = 0;
+    for (int p = 1; p < N; p <<= 1)
+      for (int q = p; q >= 1; q >>= 1)
+        for (int j = q % p; j + q < N; j += 2 * q)
+          for (int i = 0; i < q && i + j + q < N; ++i)
+            if ((i + j) / (2 * p) == (i + j + q) / (2 * p)) {
+              t.lo[c] = (unsigned char)(i + j);
+              t.hi[c] = (unsigned char)(i + j + q);
+              ++c;
+            }
+    return t;
+  }
+};
+
+template <int N, typename K>
+__device__ __forceinline__ void lane_oddeven_sort(K (&k)[N]) {
+  constexpr auto T = OddEvenNet<N>::table();
+#pragma unroll
+  for (int c = 0; c < OddEvenNet<N>::NC; ++c) {
+    const K x = k[T.lo[c]], y = k[T.hi[c]];
+    k[T.lo[c]] = kmin(x, y);
+    k[T.hi[c]] = kmax(x, y);
+  }
+}
+
 template <int E, typename K>
 __device__ __forceinline__ void warp_bitonic_sort(K (&k)[E]) {
   group_bitonic_sort<E, 32, K>(k);

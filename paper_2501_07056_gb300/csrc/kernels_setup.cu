@@ -73,6 +73,9 @@ __global__ void k_rowinfo(Csr A, Csr B, CatParams cp, int64_t* __restrict__ P,
     int64_t s = 0, e = 0;
     if (active) { s = A.rp[i]; e = A.rp[i + 1]; }
     int64_t p = 0;
+    // the B row bounds of a row that fits one step stay in registers for
+    // the column range below
+    int64_t r0 = 0, r1 = 0, r2 = 0, r3 = 0;
     // two entries per lane and step, their loads issued together
     for (int64_t j = s + sub; j < e; j += 2 * V) {
       const int64_t j2 = j + V;
@@ -84,6 +87,10 @@ __global__ void k_rowinfo(Csr A, Csr B, CatParams cp, int64_t* __restrict__ P,
       p += (b1 - b0) + (b3 - b2);
       seg[j] = seg_pack(b0, b1 - b0);
       if (two) seg[j2] = seg_pack(b2, b3 - b2);
+      r0 = b0;
+      r1 = b1;
+      r2 = b2;
+      r3 = b3;
     }
 #pragma unroll
     for (int d = V / 2; d > 0; d >>= 1) p += __shfl_xor_sync(gmask, p, d, V);
@@ -107,13 +114,25 @@ __global__ void k_rowinfo(Csr A, Csr B, CatParams cp, int64_t* __restrict__ P,
     int32_t lo = 0x7fffffff, hi = -1;
     // need_range is uniform within a group (p is the group-reduced sum)
     if (need_range) {
-      for (int64_t j = s + sub; j < e; j += V) {
-        const int32_t c = A.col[j];
-        const int64_t bs = B.rp[c], be = B.rp[c + 1];
-        if (be > bs) {
-          const int32_t c0 = B.col[bs], c1 = B.col[be - 1];
+      if (e - s <= 2 * V) {  // one step: the bounds are r0..r3 (empty pairs when unused)
+        if (r1 > r0) {
+          lo = B.col[r0];
+          hi = B.col[r1 - 1];
+        }
+        if (r3 > r2) {
+          const int32_t c0 = B.col[r2], c1 = B.col[r3 - 1];
           lo = c0 < lo ? c0 : lo;
           hi = c1 > hi ? c1 : hi;
+        }
+      } else {
+        for (int64_t j = s + sub; j < e; j += V) {
+          const int32_t c = A.col[j];
+          const int64_t bs = B.rp[c], be = B.rp[c + 1];
+          if (be > bs) {
+            const int32_t c0 = B.col[bs], c1 = B.col[be - 1];
+            lo = c0 < lo ? c0 : lo;
+            hi = c1 > hi ? c1 : hi;
+          }
         }
       }
     }

@@ -188,29 +188,56 @@ __global__ void __launch_bounds__((1 << CAPLOG) / BR) k_sort_block_numeric(SortA
   }
 }
 
-// Symbolic pass of the SORT512 and SORT1024 bins with one warp per row:
-// CAP/32 keys per lane, sorted by the warp's register network
-// (group_bitonic_sort over 32 lanes: swaps in registers below distance CAP/32,
-// shuffles above), so neither shared-memory exchanges nor block barriers are
-// needed.  Segments are found as in the lane-group kernel (head bits at
-// segment starts, prefix popcounts); the distinct columns are counted and
-// the sorted slot order is stored, two bytes per product, for the replay.
+// Symbolic pass of the SORT512 and SORT1024 bins with one warp per row.
+// The row's (column, slot) keys are split by column into NB = CAP/16
+// buckets of consecutive column ranges (a multiply-high of the column's
+// offset from the row's smallest column; counts by shared-memory atomics,
+// bucket starts by a warp scan), and every lane sorts its bucket(s) of at
+// most 32 keys in registers (odd-even merge sort): half the compare-exchanges
+// of one warp-wide network over all CAP keys and none of its shuffles, which
+// matters because the network keeps the integer pipe busy.  Buckets follow
+// column order, so their concatenation is the sorted order.  A row with a
+// bucket of more than 32 keys (a narrow or skewed column range) takes the
+// warp-wide bitonic network instead (group_bitonic_sort over 32 lanes: swaps
+// in registers below distance CAP/32, shuffles above).  The distinct columns
+// are counted (precise prediction, Section 2.1) and the sorted slot order
+// is stored, two bytes per product, for the numeric replay.
 constexpr int SW_NW = 4;
 
 template <int CAPLOG, typename K>
 __global__ void __launch_bounds__(SW_NW * 32) k_sortw_symbolic(SortArgs a) {
   constexpr int CAP = 1 << CAPLOG, R = CAP / 32, SB = CAPLOG, HW = CAP / 32;
+  constexpr int NBL = R / 16;   // buckets per lane
+  constexpr int NB = 32 * NBL;  // buckets per row: at most 16 keys each on average
+  constexpr int BC = 32;        // bucket capacity: the keys one lane sorts
   using KT = KeyTraits<K>;
-  __shared__ uint16_t s_off[SW_NW][CAP];  // first slot of each non-empty segment
-  __shared__ int64_t s_bs[SW_NW][CAP];    // B.rowPtr of the segment's B row
+  union Area {
+    int64_t bs[CAP];  // B.rowPtr of each segment's B row
+    K key[CAP];       // then the keys, bucket by bucket
+  };
+  __shared__ Area s_area[SW_NW];
+  __shared__ uint16_t s_off[SW_NW][CAP];  // first slot of each segment; then the sorted slots
   __shared__ uint32_t s_head[SW_NW][HW];  // bit s: a segment other than the first starts at s
   __shared__ int32_t s_pw[SW_NW][HW];     // segments starting in earlier words
+  __shared__ int32_t s_cnt[SW_NW][NB];    // keys per bucket
+  __shared__ int32_t s_bst[SW_NW][NB];    // first sorted position of each bucket
   const int lane = lane_id(), w = warp_id();
   const int64_t nwarps = (int64_t)gridDim.x * SW_NW;
-  for (int64_t idx = (int64_t)blockIdx.x * SW_NW + w; idx < a.n_rows; idx += nwarps) {
-    const RowDesc d = a.desc[idx];
-    const int64_t poff = a.perm2_off[idx];
+  Area& ar = s_area[w];
+  // the next row's descriptor and first 32 segment entries are loaded while
+  // the current row's gathers are in flight
+  int64_t idx = (int64_t)blockIdx.x * SW_NW + w;
+  RowDesc d{0, 0, 0};
+  int64_t poff = 0;
+  uint64_t sg_pf = 0;
+  if (idx < a.n_rows) {
+    d = a.desc[idx];
+    poff = a.perm2_off[idx];
+    if (lane < d.na) sg_pf = a.seg[d.as + lane];
+  }
+  for (; idx < a.n_rows; idx += nwarps) {
     if (lane < HW) s_head[w][lane] = 0u;
+    for (int i = lane; i < NB; i += 32) s_cnt[w][i] = 0;
     __syncwarp();
     int nseg = 0, P = 0;
     for (int j0 = 0; j0 < d.na; j0 += 32) {
@@ -218,7 +245,7 @@ __global__ void __launch_bounds__(SW_NW * 32) k_sortw_symbolic(SortArgs a) {
       int L = 0;
       int64_t bs = 0;
       if (j < d.na) {
-        const uint64_t sg = a.seg[d.as + j];
+        const uint64_t sg = j0 == 0 ? sg_pf : a.seg[d.as + j];
         L = seg_length(sg);
         bs = seg_start(sg);
       }
@@ -228,7 +255,7 @@ __global__ void __launch_bounds__(SW_NW * 32) k_sortw_symbolic(SortArgs a) {
         const int g = nseg + __popc(nz & ((1u << lane) - 1u));
         const int off = P + inc - L;
         s_off[w][g] = (uint16_t)off;
-        s_bs[w][g] = bs;
+        ar.bs[g] = bs;
         if (g > 0) atomicOr(&s_head[w][off >> 5], 1u << (off & 31));
       }
       nseg += __popc(nz);
@@ -250,30 +277,117 @@ __global__ void __launch_bounds__(SW_NW * 32) k_sortw_symbolic(SortArgs a) {
       cg[e] = 0;
       if (s < P) {
         const int g = s_pw[w][e] + __popc(s_head[w][e] & ((2u << lane) - 1u));
-        cg[e] = __ldg(a.B.col + s_bs[w][g] + (s - s_off[w][g]));
+        cg[e] = __ldg(a.B.col + ar.bs[g] + (s - s_off[w][g]));
       }
     }
-    K key[R];
+    RowDesc nd{0, 0, 0};
+    int64_t npoff = 0;
+    if (idx + nwarps < a.n_rows) {
+      nd = a.desc[idx + nwarps];
+      npoff = a.perm2_off[idx + nwarps];
+      if (lane < nd.na) sg_pf = a.seg[nd.as + lane];
+    }
+    // buckets: column c goes to floor((c - mn) * NB / range), computed as a
+    // multiply-high (monotone in c, clamped to the last bucket)
+    int32_t mn = 0x7fffffff, mx = -1;
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+      if (e * 32 + lane < P) {
+        mn = min(mn, cg[e]);
+        mx = max(mx, cg[e]);
+      }
+    }
+    mn = warp_min(mn);
+    mx = warp_max(mx);
+    const uint32_t range = (uint32_t)(mx - mn) + 1u;
+    const uint32_t mul =
+        range <= (uint32_t)NB
+            ? 0u
+            : (uint32_t)fminf((float)NB * 4294967296.0f / (float)range, 4294967040.0f);
+    uint32_t br[R];  // bucket << 16 | rank in the bucket
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+      br[e] = 0u;
+      if (e * 32 + lane < P) {
+        const uint32_t o = (uint32_t)(cg[e] - mn);
+        const uint32_t b = range <= (uint32_t)NB ? o : min(__umulhi(o, mul), (uint32_t)NB - 1u);
+        br[e] = (b << 16) | (uint32_t)atomicAdd(&s_cnt[w][b], 1);
+      }
+    }
+    __syncwarp();
+    // lane l owns buckets l*NBL .. l*NBL + NBL - 1
+    int cb[NBL];
+    int tot = 0;
+    bool over = false;
+#pragma unroll
+    for (int j = 0; j < NBL; ++j) {
+      cb[j] = s_cnt[w][lane * NBL + j];
+      tot += cb[j];
+      over = over || cb[j] > BC;
+    }
+    const int start = warp_inclusive_scan(tot) - tot;
+    {
+      int st = start;
+#pragma unroll
+      for (int j = 0; j < NBL; ++j) {
+        s_bst[w][lane * NBL + j] = st;
+        st += cb[j];
+      }
+    }
+    const bool fallback = __any_sync(FULL, over);
+    __syncwarp();  // the segment starts are consumed; their space takes the keys
 #pragma unroll
     for (int e = 0; e < R; ++e) {
       const int s = e * 32 + lane;
-      key[e] = s < P ? KT::template make<SB>(cg[e], s) : ~K(0);
+      if (s < P) ar.key[s_bst[w][br[e] >> 16] + (br[e] & 0xffffu)] = KT::template make<SB>(cg[e], s);
     }
-    group_bitonic_sort<R, 32>(key);
-    // sorted position q = lane*R + e
-    const K prev_last = __shfl_up_sync(FULL, key[R - 1], 1);
+    __syncwarp();
     int h = 0;
+    if (!fallback) {
+      int st = start;
 #pragma unroll
-    for (int e = 0; e < R; ++e) {
-      const int q = lane * R + e;
-      const int32_t c = KT::template col<SB>(key[e]);
-      const int32_t pc = (e == 0) ? ((lane == 0) ? -1 : KT::template col<SB>(prev_last))
-                                  : KT::template col<SB>(key[e - 1]);
-      h += ((q < P) && (q == 0 || c != pc)) ? 1 : 0;
-      if (q < P) a.perm2[poff + q] = (uint16_t)KT::template slot<SB>(key[e]);
+      for (int j = 0; j < NBL; ++j) {
+        K kk[BC];
+#pragma unroll
+        for (int i = 0; i < BC; ++i) kk[i] = i < cb[j] ? ar.key[st + i] : ~K(0);
+        lane_oddeven_sort<BC>(kk);
+#pragma unroll
+        for (int i = 0; i < BC; ++i) {
+          if (i < cb[j]) {
+            s_off[w][st + i] = (uint16_t)KT::template slot<SB>(kk[i]);
+            h += (i == 0 || KT::template col<SB>(kk[i]) != KT::template col<SB>(kk[i > 0 ? i - 1 : 0]))
+                     ? 1 : 0;
+          }
+        }
+        st += cb[j];
+      }
+      __syncwarp();
+      // the sorted slots, written coalesced
+      for (int q = lane; q < P; q += 32) a.perm2[poff + q] = s_off[w][q];
+    } else {
+      K key[R];
+#pragma unroll
+      for (int e = 0; e < R; ++e) {
+        const int s = e * 32 + lane;
+        key[e] = s < P ? ar.key[s] : ~K(0);
+      }
+      group_bitonic_sort<R, 32>(key);
+      // sorted position q = lane*R + e
+      const K prev_last = __shfl_up_sync(FULL, key[R - 1], 1);
+#pragma unroll
+      for (int e = 0; e < R; ++e) {
+        const int q = lane * R + e;
+        const int32_t c = KT::template col<SB>(key[e]);
+        const int32_t pc = (e == 0) ? ((lane == 0) ? -1 : KT::template col<SB>(prev_last))
+                                    : KT::template col<SB>(key[e > 0 ? e - 1 : 0]);
+        h += ((q < P) && (q == 0 || c != pc)) ? 1 : 0;
+        if (q < P) a.perm2[poff + q] = (uint16_t)KT::template slot<SB>(key[e]);
+      }
     }
     const int cnt = warp_sum(h);
     if (lane == 0) a.out_cnt[d.row] = cnt;
+    d = nd;
+    poff = npoff;
     __syncwarp();
   }
 }
@@ -316,9 +430,22 @@ __global__ void __launch_bounds__(S5N_NW * 32, 4) k_sort512_numeric(SortArgs a) 
   const int64_t cbase = a.c_base ? *a.c_base : 0;
   const int64_t nwarps = (int64_t)gridDim.x * S5N_NW;
   Area& ar = s_area[w];
-  for (int64_t idx = first + (int64_t)blockIdx.x * S5N_NW + w; idx < n; idx += nwarps) {
-    const RowDesc d = a.desc[idx];
-    const int64_t poff = a.perm2_off[idx];
+  // the next row's descriptor and first 32 segment entries are loaded while
+  // the current row's gathers are in flight
+  int64_t idx = first + (int64_t)blockIdx.x * S5N_NW + w;
+  RowDesc d{0, 0, 0};
+  int64_t poff = 0;
+  uint64_t sg_pf = 0;
+  double av_pf = 0.0;
+  if (idx < n) {
+    d = a.desc[idx];
+    poff = a.perm2_off[idx];
+    if (lane < d.na) {
+      sg_pf = a.seg[d.as + lane];
+      av_pf = a.A.val[d.as + lane];
+    }
+  }
+  for (; idx < n; idx += nwarps) {
     if (lane < HW) s_head[w][lane] = 0u;
     __syncwarp();
     // 1. segments: the non-empty B rows in stored order, their first slots
@@ -329,10 +456,10 @@ __global__ void __launch_bounds__(S5N_NW * 32, 4) k_sort512_numeric(SortArgs a) 
       int64_t bs = 0;
       double av = 0.0;
       if (j < d.na) {
-        const uint64_t sg = a.seg[d.as + j];
+        const uint64_t sg = j0 == 0 ? sg_pf : a.seg[d.as + j];
         L = seg_length(sg);
         bs = seg_start(sg);
-        av = a.A.val[d.as + j];
+        av = j0 == 0 ? av_pf : a.A.val[d.as + j];
       }
       const unsigned nz = __ballot_sync(FULL, L > 0);
       const int inc = warp_inclusive_scan(L);
@@ -372,6 +499,17 @@ __global__ void __launch_bounds__(S5N_NW * 32, 4) k_sort512_numeric(SortArgs a) 
         pg[e] = a.perm2[poff + s];
       }
     }
+    const int64_t crp = a.c_rp[d.row] - cbase;
+    RowDesc nd{0, 0, 0};
+    int64_t npoff = 0;
+    if (idx + nwarps < n) {
+      nd = a.desc[idx + nwarps];
+      npoff = a.perm2_off[idx + nwarps];
+      if (lane < nd.na) {
+        sg_pf = a.seg[nd.as + lane];
+        av_pf = a.A.val[nd.as + lane];
+      }
+    }
     __syncwarp();  // the segment table is consumed; its space takes the slots
 #pragma unroll
     for (int e = 0; e < R; ++e) {
@@ -405,7 +543,6 @@ __global__ void __launch_bounds__(S5N_NW * 32, 4) k_sort512_numeric(SortArgs a) 
     }
     __syncwarp();
     // 4. one output per run, written at C.rowPtr + the run's rank
-    const int64_t crp = a.c_rp[d.row] - cbase;
     int base_o = 0;
 #pragma unroll
     for (int e = 0; e < R; ++e) {
@@ -425,6 +562,8 @@ __global__ void __launch_bounds__(S5N_NW * 32, 4) k_sort512_numeric(SortArgs a) 
       }
       base_o += __popc(h);
     }
+    d = nd;
+    poff = npoff;
     __syncwarp();
   }
 }

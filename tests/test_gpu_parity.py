@@ -113,6 +113,28 @@ def test_sparse_rows_sort_rule(b_cols, wide):
         assert cats[SORT] > 0 and (b_cols > 1000 or cats[DENSE] > 0)
 
 
+@pytest.mark.parametrize("force", [-1, SORT])
+def test_block_sort_skewed_columns(force):
+    # four in five B rows hold column 0: rows of A with more than 32 such B
+    # rows put more than 32 keys in one column bucket and take the warp-wide
+    # network, the others the per-lane bucket sorts (both block-sort bins)
+    rng = np.random.default_rng(11)
+    b_rows = []
+    for r in range(2000):
+        others = rng.choice(np.arange(1, 60000), size=int(rng.integers(7, 16)), replace=False)
+        cols = np.sort(others)
+        if r % 5:
+            cols = np.concatenate(([0], cols))
+        b_rows.append(cols.tolist())
+    a_rows = [np.sort(rng.choice(2000, size=int(rng.integers(24, 61)), replace=False)).tolist()
+              for _ in range(700)]
+    A = _csr(700, 2000, a_rows)
+    B = _csr(2000, 60000, b_rows)
+    got = run_gpu(A, B, P(force_category=force, validate=1))
+    assert_parity(got, A, B)
+    assert got["info"]["rows_per_category"][SORT] > 0
+
+
 def test_block_sort_64bit_keys():
     # 2^27 columns: column + 10 slot bits exceed 32 bits
     A = inputs.ragged(1500, 3000, 10, 40, seed=6, matrix_id=1)
