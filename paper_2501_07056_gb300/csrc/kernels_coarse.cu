@@ -474,9 +474,10 @@ __global__ void __launch_bounds__(BS_NT)
 // second reorder.  FP64 values and the bitmap live in shared memory.  The
 // scatter loop issues BD_UNROLL loads per thread before its atomics.
 // Emission is warp-cooperative: warp w owns a contiguous range of bitmap
-// words; each non-zero word is expanded by a ballot so the warp writes its
-// set columns as one coalesced run, reading (and re-zeroing) the 32
-// accumulator slots of the word together.  The words are cleared after use,
+// words; each word is expanded by a ballot so the warp writes its set
+// columns as one coalesced run, reading (and re-zeroing) the 32 accumulator
+// slots of the word together, four words per step so that their reads
+// overlap.  The words are cleared after use,
 // so the accumulator is clean for the next chunk.
 constexpr int BUCKET_DENSE_LOG2 = 13;
 constexpr int BD_UNROLL = 4;
@@ -540,17 +541,35 @@ __global__ void __launch_bounds__(FNT)
       for (int i = 0; i < w; ++i) o += wcnt[i];
       const int64_t col_base = (int64_t)c << sc;
       const unsigned below = (1u << lane) - 1u;
-      for (int j = 0; j < wpw; ++j) {
-        const uint32_t m = __shfl_sync(FULL, mine, j);
-        if (m == 0u) continue;
-        const int idx = (wd0 + j) * 32 + lane;
-        if ((m >> lane) & 1u) {
-          const int64_t pos = o + __popc(m & below);
-          c_col[pos] = (int32_t)(col_base + idx);
-          c_val[pos] = acc[idx];
-          acc[idx] = 0.0;
+      // four words per step: their accumulator reads are independent
+      for (int j0 = 0; j0 < wpw; j0 += 4) {
+        uint32_t m[4];
+        int64_t ob[4];
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          m[u] = __shfl_sync(FULL, mine, (j0 + u) & 31);
+          if (j0 + u >= wpw) m[u] = 0u;
+          ob[u] = o;
+          o += __popc(m[u]);
         }
-        o += __popc(m);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          v[u] = 0.0;
+          if ((m[u] >> lane) & 1u) {
+            const int idx = (wd0 + j0 + u) * 32 + lane;
+            v[u] = acc[idx];
+            acc[idx] = 0.0;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if ((m[u] >> lane) & 1u) {
+            const int64_t pos = ob[u] + __popc(m[u] & below);
+            c_col[pos] = (int32_t)(col_base + (wd0 + j0 + u) * 32 + lane);
+            c_val[pos] = v[u];
+          }
+        }
       }
     } else if (threadIdx.x == 0) {
       int total = 0;
