@@ -379,8 +379,105 @@ constexpr int BS_NT = 256;
 constexpr int BS_CAP = BS_NT * BR;  // 2,048 products
 constexpr int BS_PB = 11;           // position bits of a key
 
+// Block sort of one bucket's keys (chunk-local column << PB | position) by
+// column sub-ranges: the bucket's column range is split into NT sub-ranges
+// (the high word of the column's offset from the smallest column times a
+// per-bucket multiplier, monotone in the column), the keys are counted and
+// scattered into their sub-ranges through shared memory, and every thread
+// sorts its own sub-range in registers (odd-even merge network of 16 keys,
+// or 32 when some sub-range holds more than 16).  That is about a third of
+// the compare-exchanges of the block bitonic network, with four barriers
+// instead of its shared-memory stages.  A sub-range of more than 32 keys (a
+// narrow or skewed bucket) sends the bucket to block_sort_keys.  On return
+// key[e] holds sorted position t*BR + e, as block_sort_keys leaves it.
+template <int NT, int PB, typename K>
+__device__ __forceinline__ void bucket_sort_keys(K (&key)[BR], int n, K* s_key, int32_t* s_cnt,
+                                                 int32_t* s_bst, uint32_t* s_red, int32_t* s_ws) {
+  constexpr int NWB = NT / 32;
+  const int t = threadIdx.x, lane = lane_id(), w = warp_id();
+  uint32_t mn = 0xffffffffu, mx = 0u;
+#pragma unroll
+  for (int e = 0; e < BR; ++e) {
+    if (e * NT + t < n) {
+      const uint32_t c = (uint32_t)(key[e] >> PB);
+      mn = min(mn, c);
+      mx = max(mx, c);
+    }
+  }
+  mn = warp_min(mn);
+  mx = warp_max(mx);
+  if (lane == 0) {
+    s_red[w] = mn;
+    s_red[NWB + w] = mx;
+  }
+  s_cnt[t] = 0;
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NWB; ++i) {
+    mn = min(mn, s_red[i]);
+    mx = max(mx, s_red[NWB + i]);
+  }
+  const uint32_t range = mx - mn + 1u;
+  const uint32_t mul =
+      range <= (uint32_t)NT ? 0u
+                            : (uint32_t)fminf((float)NT * 4294967296.0f / (float)range, 4294967040.0f);
+  uint32_t br[BR];  // sub-range << 16 | rank in it
+#pragma unroll
+  for (int e = 0; e < BR; ++e) {
+    br[e] = 0u;
+    if (e * NT + t < n) {
+      const uint32_t o = (uint32_t)(key[e] >> PB) - mn;
+      const uint32_t b = range <= (uint32_t)NT ? o : min(__umulhi(o, mul), (uint32_t)NT - 1u);
+      br[e] = (b << 16) | (uint32_t)atomicAdd(&s_cnt[b], 1);
+    }
+  }
+  __syncthreads();
+  const int c = s_cnt[t];
+  const bool over32 = __syncthreads_or(c > 32) != 0;
+  const bool over16 = __syncthreads_or(c > 16) != 0;
+  int tot;
+  const int st = block_exclusive_scan<NT>(c, s_ws, &tot);
+  s_bst[t] = st;
+  __syncthreads();
+#pragma unroll
+  for (int e = 0; e < BR; ++e)
+    if (e * NT + t < n) s_key[s_bst[br[e] >> 16] + (int)(br[e] & 0xffffu)] = key[e];
+  __syncthreads();
+  if (over32) {  // the block network, on the keys in any order
+#pragma unroll
+    for (int e = 0; e < BR; ++e) key[e] = e * NT + t < n ? s_key[e * NT + t] : ~K(0);
+    __syncthreads();
+    block_sort_keys<NT>(key, s_key);
+    return;
+  }
+  if (over16) {
+    K kk[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) kk[i] = i < c ? s_key[st + i] : ~K(0);
+    lane_oddeven_sort<32>(kk);
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (i < c) s_key[st + i] = kk[i];
+  } else {
+    K kk[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) kk[i] = i < c ? s_key[st + i] : ~K(0);
+    lane_oddeven_sort<16>(kk);
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (i < c) s_key[st + i] = kk[i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int e = 0; e < BR; ++e) {
+    const int q = t * BR + e;
+    key[e] = q < n ? s_key[q] : ~K(0);
+  }
+  __syncthreads();
+}
+
 template <typename K, bool NUMERIC>
-__global__ void __launch_bounds__(BS_NT)
+__global__ void __launch_bounds__(BS_NT, 4)
     k_bucket_sort(const BigBucket* __restrict__ list, const int32_t* __restrict__ n_list,
                   const int32_t* __restrict__ chunk_col, const double* __restrict__ chunk_val,
                   int sc, int32_t* __restrict__ bucket_cnt, int32_t* __restrict__ c_col,
@@ -389,6 +486,10 @@ __global__ void __launch_bounds__(BS_NT)
   __shared__ double s_val[NUMERIC ? BS_CAP : 1];
   __shared__ uint32_t s_head[BS_CAP / 32];
   __shared__ int32_t s_hpre[BS_CAP / 32 + 1];
+  __shared__ int32_t s_cnt[BS_NT];
+  __shared__ int32_t s_bst[BS_NT];
+  __shared__ uint32_t s_red[2 * (BS_NT / 32)];
+  __shared__ int32_t s_ws[BS_NT / 32 + 1];
   const int t = threadIdx.x;
   const int lane = lane_id(), w = warp_id();
   constexpr K PMASK = (K(1) << BS_PB) - 1;
@@ -410,7 +511,7 @@ __global__ void __launch_bounds__(BS_NT)
         key[e] = ~K(0);
       }
     }
-    block_sort_keys<BS_NT>(key, s_key);
+    bucket_sort_keys<BS_NT, BS_PB>(key, n, s_key, s_cnt, s_bst, s_red, s_ws);
     // sorted positions t*BR + e: stage them, mark the run heads
 #pragma unroll
     for (int e = 0; e < BR; ++e) s_key[t * BR + e] = key[e];
