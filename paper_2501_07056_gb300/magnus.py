@@ -606,7 +606,9 @@ def spgemm_host(A, B, params: Params | None = None, blocks: int = 4, device="cud
     enough for C, else allocated with ``host_empty``.  ``timing``:
     optional dict that receives the device time of each part (ms, CUDA
     events): h2d, plan_symbolic, rowptr_d2h, numeric (sum over slabs), d2h
-    (first slab copy start to last copy end), total.  Returns (row_ptr,
+    (first slab copy start to last copy end), slab_setup (C.rowPtr home to
+    the first slab's numeric launch: the host's cut and buffer work), total.
+    Returns (row_ptr,
     col, val) host tensors (views of ``out`` when given)."""
     import numpy as np
     import torch
@@ -644,7 +646,9 @@ def spgemm_host(A, B, params: Params | None = None, blocks: int = 4, device="cud
         t_rp.record(main)
         rp = o_rp.numpy()
         nb = max(1, min(blocks, A.n_rows))
-        cuts = np.searchsorted(rp[:A.n_rows + 1], np.linspace(0, nnz, nb + 1)[1:-1], side="left")
+        # integer targets: float ones would make numpy convert all of C.rowPtr
+        targets = (np.arange(1, nb, dtype=np.int64) * nnz) // nb
+        cuts = np.searchsorted(rp[:A.n_rows + 1], targets, side="left")
         cuts = np.unique(np.concatenate(([0], cuts, [A.n_rows]))).astype(np.int64)
         slabs = [(int(cuts[k]), int(cuts[k + 1])) for k in range(len(cuts) - 1)]
         most = max(int(rp[r1] - rp[r0]) for r0, r1 in slabs)
@@ -682,6 +686,7 @@ def spgemm_host(A, B, params: Params | None = None, blocks: int = 4, device="cud
             timing.update(
                 h2d=t0.elapsed_time(t_h2d), plan_symbolic=t_h2d.elapsed_time(t_sym),
                 rowptr_d2h=t_sym.elapsed_time(t_rp),
+                slab_setup=t_rp.elapsed_time(marks[0][0]) if marks else 0.0,
                 numeric=sum(c0.elapsed_time(c1) for c0, c1, _, _ in marks),
                 d2h=marks[0][2].elapsed_time(marks[-1][3]) if marks else 0.0,
                 total=t0.elapsed_time(marks[-1][3]) if marks else t0.elapsed_time(t_rp),
