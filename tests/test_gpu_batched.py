@@ -226,3 +226,7 @@ def test_spgemm_host_pipelined(blocks):
     rp, col, val = magnus.spgemm_host(S, S, blocks=blocks)
     refs = oracle.spgemm(S, S)
     assert np.array_equal(rp.numpy(), refs.row_ptr) and np.array_equal(col.numpy(), refs.col)
+    # a product with no entries: one empty slab, nothing copied back
+    Z = inputs.ragged(64, 64, 0, 0, seed=1, matrix_id=3)
+    rp, col, val = magnus.spgemm_host(Z, Z, blocks=blocks)
+    assert rp.numel() == 65 and int(rp.sum()) == 0 and col.numel() == 0 and val.numel() == 0
