@@ -48,7 +48,7 @@ enum magnus_status {
                                     nnz of B >= 2^40) */
   MAGNUS_OUT_OF_MEMORY = 4,      /* device allocation failed or the request exceeds the memory cap */
   MAGNUS_CUDA_ERROR = 5,         /* a CUDA runtime call failed; see magnus_last_cuda_error() */
-  MAGNUS_TIMEOUT = 6,            /* a bounded device-side wait expired (reserved) */
+  MAGNUS_TIMEOUT = 6,            /* a bounded device-side wait expired (see magnus_device_status) */
   MAGNUS_NOT_SYMBOLIC = 7,       /* magnus_numeric called before magnus_symbolic on this plan */
   MAGNUS_BAD_STATE = 8,          /* the plan was built for other inputs or is unusable */
   MAGNUS_SCRATCH_LIMIT = 9,      /* magnus_numeric_noalloc: the fixed staging buffer is too small */
@@ -207,7 +207,8 @@ int magnus_plan(magnus_plan_t* plan, const magnus_csr_t* A, const magnus_csr_t* 
  * nnz_c:     host, receives c_row_ptr[A.n_rows].  The call synchronises
  *            `stream` to read it (the caller needs it to allocate C).
  * Per-(row, coarse chunk) counts of coarse rows are kept in the plan for
- * magnus_numeric. */
+ * magnus_numeric.  MAGNUS_TIMEOUT if a bounded device wait gave up (see
+ * magnus_device_status); the counts are then incomplete. */
 int magnus_symbolic(magnus_plan_t plan, int64_t* c_row_ptr, int64_t* nnz_c, void* stream);
 
 /* magnus_numeric - Algorithms 1-4: fills C.col and C.val.
@@ -559,6 +560,19 @@ int magnus_host_free(void* ptr, size_t bytes);
 
 /* Number of kernels this library has launched in this process. */
 uint64_t magnus_launch_count(void);
+
+/* magnus_device_status - synchronises `stream` and reports whether a bounded
+ * device-side wait of this library gave up since the last report (then
+ * MAGNUS_TIMEOUT; the flag is cleared), else MAGNUS_OK.  The waits are those
+ * of the coarse level's bucket sort on its bulk copies (one-dimensional TMA
+ * copies of a bucket's staged products into shared memory, Section 3.3's
+ * chunk staging): each gives up after about a second of SM clock, lets the
+ * block's copies in flight land and ends the block, leaving its buckets
+ * unwritten.  magnus_symbolic reports such a timeout itself (it
+ * synchronises anyway); a numeric call does not synchronise, so a caller
+ * that wants the check calls this after it.  MAGNUS_CUDA_ERROR when the
+ * synchronisation fails. */
+int magnus_device_status(void* stream);
 
 /* ---- chunk model (host only; no GPU needed) -----------------------------
  * The paper sizes chunks so that the accumulator and the reorder bookkeeping

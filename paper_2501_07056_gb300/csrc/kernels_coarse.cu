@@ -365,19 +365,130 @@ __global__ void __launch_bounds__(FNT)
   }
 }
 
+// ---------------------------------------------------------------------------
+// One-dimensional bulk copies (the TMA engine's cp.async.bulk) from global
+// to shared memory, completed on an mbarrier with a transaction count.
+// Every wait is bounded by the SM clock (about a second); a wait that gives
+// up sets g_wait_timeout, which the host reads and clears
+// (wait_timeout_take, behind magnus_symbolic and magnus_device_status).
+__device__ int g_wait_timeout;
+
+constexpr long long WAIT_CYCLES = 1ll << 31;  // about one second at 2 GHz
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// one arrival that also announces `bytes` of copies to come
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_to_shared(void* dst, const void* src, unsigned bytes,
+                                               uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// shared-memory reads of the generic proxy are ordered before the next bulk
+// copy into the same buffer
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// true when the barrier's phase of this parity completed within the bound
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const unsigned a = smem_addr(bar);
+  const long long t0 = clock64();
+  for (;;) {
+    unsigned done;
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > WAIT_CYCLES) return false;
+  }
+}
+
+// Reads and clears the bounded-wait flag (synchronises the stream).
+cudaError_t wait_timeout_take(int* timed_out, cudaStream_t s) {
+  int h = 0;
+  const int zero = 0;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&h, g_wait_timeout, sizeof(int));
+  if (e == cudaSuccess && h) e = cudaMemcpyToSymbol(g_wait_timeout, &zero, sizeof(int));
+  *timed_out = h;
+  return e;
+}
+
 // Coarse buckets of 257..BS_CAP products: the sort accumulator widened to
 // a thread block (Algorithm 2; the per-chunk hybrid of Section 3.4 choosing
-// sort for the smaller chunks).  Keys (chunk-local column, position in the
-// bucket) are loaded with coalesced reads, sorted by the block bitonic
-// network, and the runs of equal columns summed in position order, so the
-// bucket needs no atomics at all (a dense accumulator's FP64 atomics
-// contend on the hub columns of power-law rows).  Emission is striped:
-// thread t takes sorted positions t, t + BS_NT, ..., whose ranks among the
-// run heads come from a prefix over a head bitmap, so consecutive threads
-// write consecutive entries of C.
+// sort for the smaller chunks).  A bucket's staged products are contiguous,
+// so one thread stages them into shared memory with two bulk copies
+// (columns, values) while the block still works on the previous bucket:
+// the buffers alternate, and the next bucket's copies are issued before the
+// current bucket's are awaited.  Keys (chunk-local column, position in the
+// bucket) are sorted (bucket_sort_keys), and the runs of equal columns
+// summed in position order, so the bucket needs no atomics at all (a dense
+// accumulator's FP64 atomics contend on the hub columns of power-law rows).
+// Emission is striped: thread t takes sorted positions t, t + BS_NT, ...,
+// whose ranks among the run heads come from a prefix over a head bitmap, so
+// consecutive threads write consecutive entries of C.
 constexpr int BS_NT = 256;
 constexpr int BS_CAP = BS_NT * BR;  // 2,048 products
 constexpr int BS_PB = 11;           // position bits of a key
+// one staging buffer: the bucket's columns from the 16-byte boundary at or
+// below its first product to the one at or above its end (at most 6 more
+// entries than the bucket), and its values likewise (at most 2 more)
+constexpr int BS_CB = (BS_CAP + 8) * 4;
+constexpr int BS_VB = (BS_CAP + 4) * 8;
+
+inline size_t bucket_sort_smem(bool numeric) {
+  return 2 * (size_t)BS_CB + (numeric ? 2 * (size_t)BS_VB : 0);
+}
+
+// Issued by one thread: the bulk copies of bucket bb into one buffer pair.
+// The staging arrays are carved with 16-byte aligned starts and padded at
+// the end, so the rounded windows stay inside them.
+template <bool NUMERIC>
+__device__ __forceinline__ void stage_bucket(const BigBucket& bb, const int32_t* chunk_col,
+                                             const double* chunk_val, unsigned char* cbuf,
+                                             unsigned char* vbuf, uint64_t* bar) {
+  const int64_t c0 = bb.p0 & ~(int64_t)3, c1 = (bb.p0 + bb.n + 3) & ~(int64_t)3;
+  const unsigned cbytes = (unsigned)(c1 - c0) * 4u;
+  unsigned vbytes = 0;
+  int64_t v0 = 0;
+  if (NUMERIC) {
+    v0 = bb.p0 & ~(int64_t)1;
+    const int64_t v1 = (bb.p0 + bb.n + 1) & ~(int64_t)1;
+    vbytes = (unsigned)(v1 - v0) * 8u;
+  }
+  fence_proxy_async();
+  mbar_arrive_expect(bar, cbytes + vbytes);
+  if (cbytes) bulk_to_shared(cbuf, chunk_col + c0, cbytes, bar);
+  if (NUMERIC && vbytes) bulk_to_shared(vbuf, chunk_val + v0, vbytes, bar);
+}
 
 // Block sort of one bucket's keys (chunk-local column << PB | position) by
 // column sub-ranges: the bucket's column range is split into NT sub-ranges
@@ -482,8 +593,9 @@ __global__ void __launch_bounds__(BS_NT, 4)
                   const int32_t* __restrict__ chunk_col, const double* __restrict__ chunk_val,
                   int sc, int32_t* __restrict__ bucket_cnt, int32_t* __restrict__ c_col,
                   double* __restrict__ c_val) {
+  extern __shared__ __align__(128) unsigned char bsm[];  // two column, two value buffers
+  __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ K s_key[BS_CAP];
-  __shared__ double s_val[NUMERIC ? BS_CAP : 1];
   __shared__ uint32_t s_head[BS_CAP / 32];
   __shared__ int32_t s_hpre[BS_CAP / 32 + 1];
   __shared__ int32_t s_cnt[BS_NT];
@@ -493,23 +605,49 @@ __global__ void __launch_bounds__(BS_NT, 4)
   const int t = threadIdx.x;
   const int lane = lane_id(), w = warp_id();
   constexpr K PMASK = (K(1) << BS_PB) - 1;
+  if (t == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
   const int nl = *n_list;
   BigBucket nxt{};
-  if (blockIdx.x < nl) nxt = list[blockIdx.x];
+  if (blockIdx.x < nl) {
+    nxt = list[blockIdx.x];
+    if (t == 0) stage_bucket<NUMERIC>(nxt, chunk_col, chunk_val, bsm, bsm + 2 * BS_CB, &s_bar[0]);
+  }
+  int buf = 0;
+  unsigned phases = 0u;  // bit b: parity of buffer b's next completion
   for (int q = blockIdx.x; q < nl; q += gridDim.x) {
     const BigBucket bb = nxt;
-    if (q + gridDim.x < nl) nxt = list[q + gridDim.x];  // next bucket's record, in flight
+    const bool more = q + gridDim.x < nl;
+    if (more) {  // the next bucket's record, and its copies into the other buffers
+      nxt = list[q + gridDim.x];
+      if (t == 0)
+        stage_bucket<NUMERIC>(nxt, chunk_col, chunk_val, bsm + (buf ^ 1) * BS_CB,
+                              bsm + 2 * BS_CB + (buf ^ 1) * BS_VB, &s_bar[buf ^ 1]);
+    }
+    const unsigned par = (phases >> buf) & 1u;
+    const bool ok = mbar_wait(&s_bar[buf], par);
+    if (__syncthreads_or(!ok)) {
+      // give up on the bucket list; the copies in flight land first
+      if (t == 0) atomicExch(&g_wait_timeout, 1);
+      if (!ok) mbar_wait(&s_bar[buf], par);
+      if (more) mbar_wait(&s_bar[buf ^ 1], (phases >> (buf ^ 1)) & 1u);
+      return;
+    }
+    phases ^= 1u << buf;
+    const int32_t* cb = reinterpret_cast<const int32_t*>(bsm + buf * BS_CB) + (bb.p0 & 3);
+    const double* vb =
+        NUMERIC ? reinterpret_cast<const double*>(bsm + 2 * BS_CB + buf * BS_VB) + (bb.p0 & 1)
+                : nullptr;
     const int n = bb.n;
     K key[BR];
 #pragma unroll
     for (int e = 0; e < BR; ++e) {
       const int pos = e * BS_NT + t;
-      if (pos < n) {
-        key[e] = ((K)(uint32_t)__ldcs(chunk_col + bb.p0 + pos) << BS_PB) | (K)pos;
-        if (NUMERIC) s_val[pos] = __ldcs(chunk_val + bb.p0 + pos);
-      } else {
-        key[e] = ~K(0);
-      }
+      key[e] = pos < n ? ((K)(uint32_t)cb[pos] << BS_PB) | (K)pos : ~K(0);
     }
     bucket_sort_keys<BS_NT, BS_PB>(key, n, s_key, s_cnt, s_bst, s_red, s_ws);
     // sorted positions t*BR + e: stage them, mark the run heads
@@ -553,11 +691,11 @@ __global__ void __launch_bounds__(BS_NT, 4)
           const int rank = s_hpre[qp >> 5] + __popc(wd & ((1u << (qp & 31)) - 1u));
           const K k0 = s_key[qp];
           const K c = k0 >> BS_PB;
-          double acc = s_val[(int)(k0 & PMASK)];
+          double acc = vb[(int)(k0 & PMASK)];
           for (int q2 = qp + 1; q2 < n; ++q2) {  // the run, in position order
             const K k2 = s_key[q2];
             if ((k2 >> BS_PB) != c) break;
-            acc += s_val[(int)(k2 & PMASK)];
+            acc += vb[(int)(k2 & PMASK)];
           }
           c_col[bb.out + rank] = (int32_t)(col_base + (int64_t)c);
           c_val[bb.out + rank] = acc;
@@ -567,6 +705,7 @@ __global__ void __launch_bounds__(BS_NT, 4)
       bucket_cnt[bb.out] = s_hpre[64];
     }
     __syncthreads();
+    buf ^= 1;
   }
 }
 
@@ -780,10 +919,12 @@ static cudaError_t coarse_impl(CoarseArgs& a, cudaStream_t s) {
     // the grid is one resident wave; blocks beyond the list's length exit
     auto kern = (a.shift_coarse + BS_PB <= 32) ? k_bucket_sort<uint32_t, NUMERIC>
                                                : k_bucket_sort<uint64_t, NUMERIC>;
+    const size_t smem = bucket_sort_smem(NUMERIC);
+    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 1;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BS_NT, 0));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BS_NT, smem));
     if (per_sm < 1) per_sm = 1;
-    kern<<<(unsigned)(a.num_sms * per_sm), BS_NT, 0, s>>>(a.big_list, a.n_big + 1, a.chunk_col,
+    kern<<<(unsigned)(a.num_sms * per_sm), BS_NT, smem, s>>>(a.big_list, a.n_big + 1, a.chunk_col,
                                                         a.chunk_val, a.shift_coarse,
                                                         a.bucket_cnt, a.c_col, a.c_val);
     count_launch();

@@ -191,6 +191,12 @@ struct magnus_plan_s {
   cudaStream_t last_stream = nullptr;
 };
 
+namespace magnus {
+// kernels_coarse.cu: reads and clears the flag of a bounded device wait that
+// gave up (synchronises the stream)
+cudaError_t wait_timeout_take(int* timed_out, cudaStream_t s);
+}  // namespace magnus
+
 namespace {
 
 int dev_alloc(void** p, size_t bytes, cudaStream_t s) {
@@ -815,10 +821,12 @@ void carve_phase(magnus_plan_t pl, bool numeric, bool rows_mode, Arena& ar, Phas
     a.counts = ar.get<int64_t>((size_t)nbk + 1);
     a.cursor = ar.get<unsigned long long>((size_t)nbk);
     const bool fine_inside = pl->shift_coarse > 13;
-    a.chunk_col = ar.get<int32_t>((size_t)z.maxP);
+    // staging, padded so that the bucket sort's bulk copies may round a
+    // bucket's window out to 16-byte boundaries
+    a.chunk_col = ar.get<int32_t>((size_t)z.maxP + 8);
     if (fine_inside) a.fine_col = ar.get<int32_t>((size_t)z.maxP);
     if (numeric) {
-      a.chunk_val = ar.get<double>((size_t)z.maxP);
+      a.chunk_val = ar.get<double>((size_t)z.maxP + 4);
       if (fine_inside) a.fine_val = ar.get<double>((size_t)z.maxP);
       a.bucket_out = ar.get<int64_t>((size_t)nbk);
     }
@@ -1101,7 +1109,9 @@ static int symbolic_impl(magnus_plan_t pl, int64_t* c_row_ptr, int64_t* nnz_c, v
   }
   int64_t h = 0;
   CUDA_TRY(cudaMemcpyAsync(&h, c_row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaStreamSynchronize(s));
+  int timed_out = 0;
+  CUDA_TRY(wait_timeout_take(&timed_out, s));  // synchronises the stream
+  if (timed_out) return MAGNUS_TIMEOUT;
   *nnz_c = h;
   pl->nnz_c = h;
   pl->symbolic_done = true;
@@ -1175,6 +1185,12 @@ int magnus_numeric_rows(magnus_plan_t pl, int64_t row_begin, int64_t row_end, co
   // empty C are accepted, as for magnus_numeric
   return numeric_impl(pl, rr, a_val, b_val, c_row_ptr, c_col, c_val, workspace, workspace_bytes,
                       (cudaStream_t)stream);
+}
+
+int magnus_device_status(void* stream) {
+  int timed_out = 0;
+  CUDA_TRY(wait_timeout_take(&timed_out, (cudaStream_t)stream));
+  return timed_out ? MAGNUS_TIMEOUT : MAGNUS_OK;
 }
 
 int magnus_workspace_size(magnus_plan_t pl, size_t* bytes) {

@@ -125,6 +125,7 @@ SIGNATURES = {
     "magnus_enable_timing": (c_i32, [c_p, ctypes.c_int]),
     "magnus_stage_times": (c_i32, [c_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "magnus_launch_count": (c_u64, []),
+    "magnus_device_status": (c_i32, [c_p]),
     "magnus_device_memory": (c_i32, [ctypes.POINTER(ctypes.c_size_t),
                                      ctypes.POINTER(ctypes.c_size_t)]),
     "magnus_host_alloc": (c_i32, [ctypes.c_size_t, ctypes.POINTER(c_p)]),
@@ -259,6 +260,14 @@ def magnus_stage_times(plan: int) -> dict:
 
 def magnus_launch_count() -> int:
     return int(_lib().magnus_launch_count())
+
+
+def device_status(stream=None) -> int:
+    """magnus_device_status: synchronises the stream; MAGNUS_OK, or
+    MAGNUS_TIMEOUT when a bounded device wait gave up since the last call."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(_lib().magnus_device_status(c_p(s.cuda_stream)))
 
 
 def magnus_device_memory() -> tuple:

@@ -425,3 +425,5 @@ def test_coarse_reorder_forms(case, reorder, bsort):
     got = run_gpu(A, B, params, same=A is B)
     assert got["info"]["rows_per_category"][COARSE] > 0
     assert_parity(got, A, B)
+    from paper_2501_07056_gb300 import magnus
+    assert magnus.device_status() == 0  # no bounded wait of the bucket sort gave up
