@@ -971,13 +971,17 @@ def run_e2e(args, dist, A, dev, params, n_inter, nnz_c):
     pinned = ((h_rp, h_col, h_val), (h_rp, h_col, h_val))
     parts = []
 
+    walls = []
+
     def step(record):
         t = {} if record else None
+        w0 = time.perf_counter()
         magnus.spgemm_host(A, A, params, blocks=args.e2e_blocks, device=dev,
                            out=(o_rp, o_col, o_val), pinned=pinned, timing=t)
         torch.cuda.synchronize()
         if record:
             parts.append(t)
+            walls.append(1e3 * (time.perf_counter() - w0))
 
     for _ in range(max(1, args.warmup)):
         step(False)
@@ -992,15 +996,22 @@ def run_e2e(args, dist, A, dev, params, n_inter, nnz_c):
     dt = time.perf_counter() - t0
     dist.barrier()
     dt_max = dist.max(dt)
+    # the link again after the timed steps: copies that were slow inside the
+    # loop but not here met other traffic on the host's memory meanwhile
+    link_h2d_after, link_d2h_after = _link_bandwidth(o_val, h_val, dev)
     units = dist.sum(2.0 * n_inter * steps)
     mean = {k: statistics.mean(p[k] for p in parts) for k in parts[0]} if parts else {}
     return {"value": units / dt_max / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "row_slabs": args.e2e_blocks, "steps": steps,
             "ms_per_step": 1e3 * dt_max / steps,
             "parts_ms": mean,
+            "step_ms": {"min": min(walls), "median": statistics.median(walls),
+                        "max": max(walls)} if walls else {},
             "link_gbs": {"h2d": link_h2d, "d2h": link_d2h,
+                         "h2d_after": link_h2d_after, "d2h_after": link_d2h_after,
                          "how": "plain pinned copies of 1 GB pieces on one stream into the "
-                                "e2e output buffer (D2H) and from the input (H2D)"},
+                                "e2e output buffer (D2H) and from the input (H2D), before and "
+                                "after the timed steps"},
             "copy_floor_ms": 1e3 * (h2d / (link_h2d * 1e9) + d2h / (link_d2h * 1e9))}
 
 
