@@ -574,6 +574,13 @@ uint64_t magnus_launch_count(void);
  * synchronisation fails. */
 int magnus_device_status(void* stream);
 
+/* magnus_wait_selftest - exercises the bounded wait: one block announces a
+ * copy on an mbarrier and issues none, waits `limit_cycles` SM clocks
+ * (1..2^31), gives up and raises the flag that magnus_device_status reports
+ * (so the next magnus_device_status returns MAGNUS_TIMEOUT).  No copy is in
+ * flight at any time.  MAGNUS_INVALID_ARG for a limit out of range. */
+int magnus_wait_selftest(int64_t limit_cycles, void* stream);
+
 /* ---- chunk model (host only; no GPU needed) -----------------------------
  * The paper sizes chunks so that the accumulator and the reorder bookkeeping
  * of one thread fit its private L2 (Section 3.5, Eq. 2-7).  On the GPU the

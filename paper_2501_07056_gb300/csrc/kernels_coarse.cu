@@ -412,7 +412,8 @@ __device__ __forceinline__ void fence_proxy_async() {
 }
 
 // true when the barrier's phase of this parity completed within the bound
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity,
+                                          long long limit = WAIT_CYCLES) {
   const unsigned a = smem_addr(bar);
   const long long t0 = clock64();
   for (;;) {
@@ -427,8 +428,28 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > WAIT_CYCLES) return false;
+    if (clock64() - t0 > limit) return false;
   }
+}
+
+// Self-test of the bounded wait: one thread announces 16 bytes on an
+// mbarrier and issues no copy, so the phase never completes; the wait gives
+// up after `limit` SM clocks and raises g_wait_timeout.  No copy is ever in
+// flight, so the block may end at once.
+__global__ void k_wait_selftest(long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+    mbar_arrive_expect(&bar, 16u);
+    if (!mbar_wait(&bar, 0u, limit)) atomicExch(&g_wait_timeout, 1);
+  }
+}
+
+cudaError_t launch_wait_selftest(long long limit, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(limit);
+  count_launch();
+  return cudaGetLastError();
 }
 
 // Reads and clears the bounded-wait flag (synchronises the stream).

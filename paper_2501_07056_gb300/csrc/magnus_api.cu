@@ -195,6 +195,8 @@ namespace magnus {
 // kernels_coarse.cu: reads and clears the flag of a bounded device wait that
 // gave up (synchronises the stream)
 cudaError_t wait_timeout_take(int* timed_out, cudaStream_t s);
+// kernels_coarse.cu: a bounded wait that nothing completes
+cudaError_t launch_wait_selftest(long long limit_cycles, cudaStream_t s);
 }  // namespace magnus
 
 namespace {
@@ -1185,6 +1187,12 @@ int magnus_numeric_rows(magnus_plan_t pl, int64_t row_begin, int64_t row_end, co
   // empty C are accepted, as for magnus_numeric
   return numeric_impl(pl, rr, a_val, b_val, c_row_ptr, c_col, c_val, workspace, workspace_bytes,
                       (cudaStream_t)stream);
+}
+
+int magnus_wait_selftest(int64_t limit_cycles, void* stream) {
+  if (limit_cycles <= 0 || limit_cycles > ((int64_t)1 << 31)) return MAGNUS_INVALID_ARG;
+  CUDA_TRY(launch_wait_selftest((long long)limit_cycles, (cudaStream_t)stream));
+  return MAGNUS_OK;
 }
 
 int magnus_device_status(void* stream) {

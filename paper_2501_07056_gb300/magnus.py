@@ -126,6 +126,7 @@ SIGNATURES = {
     "magnus_stage_times": (c_i32, [c_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "magnus_launch_count": (c_u64, []),
     "magnus_device_status": (c_i32, [c_p]),
+    "magnus_wait_selftest": (c_i32, [c_i64, c_p]),
     "magnus_device_memory": (c_i32, [ctypes.POINTER(ctypes.c_size_t),
                                      ctypes.POINTER(ctypes.c_size_t)]),
     "magnus_host_alloc": (c_i32, [ctypes.c_size_t, ctypes.POINTER(c_p)]),
@@ -268,6 +269,14 @@ def device_status(stream=None) -> int:
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     return int(_lib().magnus_device_status(c_p(s.cuda_stream)))
+
+
+def wait_selftest(limit_cycles: int, stream=None) -> None:
+    """magnus_wait_selftest: a bounded device wait that runs out."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(_lib().magnus_wait_selftest(int(limit_cycles), c_p(s.cuda_stream)),
+           "magnus_wait_selftest")
 
 
 def magnus_device_memory() -> tuple:

@@ -85,6 +85,10 @@ def test_plan_rejects_bad_args_without_gpu(lib):
     assert lib.magnus_plan(ctypes.byref(h), ctypes.byref(A40), ctypes.byref(B40), None, None) == 3
     assert lib.magnus_numeric(None, None, None, None, None, None, None) == 1
     assert lib.magnus_symbolic(None, None, None, None) == 1
+    # the bounded-wait self-test checks its limit before any CUDA call
+    lib.magnus_wait_selftest.argtypes = [ctypes.c_int64, ctypes.c_void_p]
+    assert lib.magnus_wait_selftest(0, None) == 1
+    assert lib.magnus_wait_selftest((1 << 31) + 1, None) == 1
 
 
 L2 = 126 * (1 << 20)
