@@ -13,7 +13,8 @@ namespace magnus {
 
 // Row bins.  Sort rows are split by capacity (32 * E products, E = 1,2,4,8)
 // so each warp kernel sorts in registers with a fixed network size; rows of
-// 257..1024 products sort in one thread block (bins SORT512, SORT1024).
+// 257..1024 products (bins SORT512, SORT1024) sort in one warp and replay in
+// one warp (SORT512) or one thread block (SORT1024).
 enum Bin : int {
   BIN_EMPTY = 0,
   BIN_SORT32 = 1,
@@ -118,7 +119,7 @@ struct SortArgs {
   int key32;            // 1: (col << slot_bits | slot) fits 32 bits
   uint8_t* perm;        // sorted slot order, 32*E bytes per listed row
                         // (written by the symbolic pass, replayed by the numeric pass)
-  uint16_t* perm2;      // block bins: sorted slot order, P_i entries per row at
+  uint16_t* perm2;      // bins SORT512/1024: sorted slot order, P_i entries per row at
   const int64_t* perm2_off;  // perm2 + perm2_off[k] for the bin's k-th row
   // symbolic
   int64_t* out_cnt;     // indexed by row

@@ -89,8 +89,8 @@ __device__ __forceinline__ int warp_merge_emit(const K (&k)[E], int n, const dou
   return total;
 }
 
-// Block sort of the block sort rows and of the coarse buckets of 257..2048
-// products (kernels_sort_block.cu, kernels_coarse.cu).
+// Block sort of the coarse buckets of 257..2048 products whose column
+// sub-ranges overflow (the fallback of bucket_sort_keys in kernels_coarse.cu).
 constexpr int BR = 8;  // keys per thread
 
 // Bitonic sort of NT * BR keys; thread t holds positions t * BR + e.  As in
