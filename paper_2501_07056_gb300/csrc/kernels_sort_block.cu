@@ -17,6 +17,8 @@
 // write consecutive entries of the row of C.
 //
 // Warps and blocks are persistent: each takes rows idx, idx + its stride, ...
+#include <type_traits>
+
 #include "sort_accum.cuh"
 
 namespace magnus {
@@ -189,27 +191,28 @@ __global__ void __launch_bounds__((1 << CAPLOG) / BR) k_sort_block_numeric(SortA
 }
 
 // Symbolic pass of the SORT512 and SORT1024 bins with one warp per row.
-// The row's (column, slot) keys are split by column into NB = CAP/16
+// The row's (column, slot) keys are split by column into NB = CAP/8
 // buckets of consecutive column ranges (a multiply-high of the column's
 // offset from the row's smallest column; counts by shared-memory atomics,
-// bucket starts by a warp scan), and every lane sorts its bucket(s) of at
-// most 32 keys in registers (odd-even merge sort): half the compare-exchanges
-// of one warp-wide network over all CAP keys and none of its shuffles, which
-// matters because the network keeps the integer pipe busy.  Buckets follow
-// column order, so their concatenation is the sorted order.  A row with a
-// bucket of more than 32 keys (a narrow or skewed column range) takes the
-// warp-wide bitonic network instead (group_bitonic_sort over 32 lanes: swaps
+// bucket starts by a warp scan), and every lane sorts its buckets in
+// registers (odd-even merge sort: each bucket alone when all hold at most 16
+// keys, else adjacent pairs of at most 32 keys): well under half the
+// compare-exchanges of one warp-wide network over all CAP keys and none of
+// its shuffles, which matters because the network keeps the integer pipe
+// busy.  Buckets follow column order, so their concatenation is the sorted
+// order.  A row with a pair of more than 32 keys (a narrow or skewed column
+// range) takes the warp-wide bitonic network instead (group_bitonic_sort over 32 lanes: swaps
 // in registers below distance CAP/32, shuffles above).  The distinct columns
 // are counted (precise prediction, Section 2.1) and the sorted slot order
 // is stored, two bytes per product, for the numeric replay.
 constexpr int SW_NW = 4;
 
 template <int CAPLOG, typename K>
-__global__ void __launch_bounds__(SW_NW * 32) k_sortw_symbolic(SortArgs a) {
+__global__ void __launch_bounds__(SW_NW * 32, CAPLOG == 9 ? (sizeof(K) == 4 ? 6 : 4) : (sizeof(K) == 4 ? 4 : 3))
+    k_sortw_symbolic(SortArgs a) {
   constexpr int CAP = 1 << CAPLOG, R = CAP / 32, SB = CAPLOG, HW = CAP / 32;
-  constexpr int NBL = R / 16;   // buckets per lane
-  constexpr int NB = 32 * NBL;  // buckets per row: at most 16 keys each on average
-  constexpr int BC = 32;        // bucket capacity: the keys one lane sorts
+  constexpr int NBL = R / 8;    // buckets per lane
+  constexpr int NB = 32 * NBL;  // buckets per row: at most 8 keys each on average
   using KT = KeyTraits<K>;
   union Area {
     int64_t bs[CAP];  // B.rowPtr of each segment's B row
@@ -315,15 +318,18 @@ __global__ void __launch_bounds__(SW_NW * 32) k_sortw_symbolic(SortArgs a) {
       }
     }
     __syncwarp();
-    // lane l owns buckets l*NBL .. l*NBL + NBL - 1
+    // lane l owns buckets l*NBL .. l*NBL + NBL - 1 (adjacent column ranges):
+    // each sorted alone when every bucket holds at most 16 keys, else each
+    // pair together when every pair holds at most 32, else the warp network
     int cb[NBL];
     int tot = 0;
-    bool over = false;
+    bool over16 = false, over32 = false;
 #pragma unroll
     for (int j = 0; j < NBL; ++j) {
       cb[j] = s_cnt[w][lane * NBL + j];
       tot += cb[j];
-      over = over || cb[j] > BC;
+      over16 = over16 || cb[j] > 16;
+      if (j & 1) over32 = over32 || cb[j - 1] + cb[j] > 32;
     }
     const int start = warp_inclusive_scan(tot) - tot;
     {
@@ -334,7 +340,8 @@ __global__ void __launch_bounds__(SW_NW * 32) k_sortw_symbolic(SortArgs a) {
         st += cb[j];
       }
     }
-    const bool fallback = __any_sync(FULL, over);
+    const bool fallback = __any_sync(FULL, over32);
+    const bool pairs = __any_sync(FULL, over16);
     __syncwarp();  // the segment starts are consumed; their space takes the keys
 #pragma unroll
     for (int e = 0; e < R; ++e) {
@@ -343,23 +350,37 @@ __global__ void __launch_bounds__(SW_NW * 32) k_sortw_symbolic(SortArgs a) {
     }
     __syncwarp();
     int h = 0;
+    // sorts keys [st, st + c) of the lane in registers, stages their slots,
+    // counts the first key of every column
+    auto sort_run = [&](auto nk, int st, int c) {
+      constexpr int N = decltype(nk)::value;
+      K kk[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) kk[i] = i < c ? ar.key[st + i] : ~K(0);
+      lane_oddeven_sort<N>(kk);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        if (i < c) {
+          s_off[w][st + i] = (uint16_t)KT::template slot<SB>(kk[i]);
+          h += (i == 0 || KT::template col<SB>(kk[i]) != KT::template col<SB>(kk[i > 0 ? i - 1 : 0]))
+                   ? 1 : 0;
+        }
+      }
+    };
     if (!fallback) {
       int st = start;
+      if (!pairs) {
 #pragma unroll
-      for (int j = 0; j < NBL; ++j) {
-        K kk[BC];
-#pragma unroll
-        for (int i = 0; i < BC; ++i) kk[i] = i < cb[j] ? ar.key[st + i] : ~K(0);
-        lane_oddeven_sort<BC>(kk);
-#pragma unroll
-        for (int i = 0; i < BC; ++i) {
-          if (i < cb[j]) {
-            s_off[w][st + i] = (uint16_t)KT::template slot<SB>(kk[i]);
-            h += (i == 0 || KT::template col<SB>(kk[i]) != KT::template col<SB>(kk[i > 0 ? i - 1 : 0]))
-                     ? 1 : 0;
-          }
+        for (int j = 0; j < NBL; ++j) {
+          sort_run(std::integral_constant<int, 16>{}, st, cb[j]);
+          st += cb[j];
         }
-        st += cb[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < NBL; j += 2) {
+          sort_run(std::integral_constant<int, 32>{}, st, cb[j] + cb[j + 1]);
+          st += cb[j] + cb[j + 1];
+        }
       }
       __syncwarp();
       // the sorted slots, written coalesced
