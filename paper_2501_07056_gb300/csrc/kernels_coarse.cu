@@ -12,6 +12,8 @@
 //      chunks, a thread block running Algorithm 3 for large ones.
 // Each B row is loaded once per batch and reused for every batch row that
 // references it (the reason Algorithm 4 uses the outer product).
+#include <type_traits>
+
 #include "fine_level.cuh"
 #include "sort_accum.cuh"
 
@@ -512,20 +514,22 @@ __device__ __forceinline__ void stage_bucket(const BigBucket& bb, const int32_t*
 }
 
 // Block sort of one bucket's keys (chunk-local column << PB | position) by
-// column sub-ranges: the bucket's column range is split into NT sub-ranges
-// (the high word of the column's offset from the smallest column times a
-// per-bucket multiplier, monotone in the column), the keys are counted and
-// scattered into their sub-ranges through shared memory, and every thread
-// sorts its own sub-range in registers (odd-even merge network of 16 keys,
-// or 32 when some sub-range holds more than 16).  That is about a third of
-// the compare-exchanges of the block bitonic network, with four barriers
-// instead of its shared-memory stages.  A sub-range of more than 32 keys (a
-// narrow or skewed bucket) sends the bucket to block_sort_keys.  On return
+// column sub-ranges: the bucket's column range is split into 2*NT
+// sub-ranges (the high word of the column's offset from the smallest column
+// times a per-bucket multiplier, monotone in the column), the keys are
+// counted and scattered into their sub-ranges through shared memory, and
+// every thread sorts its two adjacent sub-ranges in registers (odd-even
+// merge networks: each of 16 keys, or both together as 32 when some
+// sub-range holds more than 16).  That is about a third of the
+// compare-exchanges of the block bitonic network, with four barriers instead
+// of its shared-memory stages.  A pair of more than 32 keys (a narrow or
+// skewed bucket) sends the bucket to block_sort_keys.  On return
 // key[e] holds sorted position t*BR + e, as block_sort_keys leaves it.
 template <int NT, int PB, typename K>
 __device__ __forceinline__ void bucket_sort_keys(K (&key)[BR], int n, K* s_key, int32_t* s_cnt,
                                                  int32_t* s_bst, uint32_t* s_red, int32_t* s_ws) {
   constexpr int NWB = NT / 32;
+  constexpr int NS = 2 * NT;  // sub-ranges: thread t owns 2t and 2t + 1
   const int t = threadIdx.x, lane = lane_id(), w = warp_id();
   uint32_t mn = 0xffffffffu, mx = 0u;
 #pragma unroll
@@ -542,7 +546,8 @@ __device__ __forceinline__ void bucket_sort_keys(K (&key)[BR], int n, K* s_key, 
     s_red[w] = mn;
     s_red[NWB + w] = mx;
   }
-  s_cnt[t] = 0;
+  s_cnt[2 * t] = 0;
+  s_cnt[2 * t + 1] = 0;
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < NWB; ++i) {
@@ -551,25 +556,28 @@ __device__ __forceinline__ void bucket_sort_keys(K (&key)[BR], int n, K* s_key, 
   }
   const uint32_t range = mx - mn + 1u;
   const uint32_t mul =
-      range <= (uint32_t)NT ? 0u
-                            : (uint32_t)fminf((float)NT * 4294967296.0f / (float)range, 4294967040.0f);
+      range <= (uint32_t)NS ? 0u
+                            : (uint32_t)fminf((float)NS * 4294967296.0f / (float)range, 4294967040.0f);
   uint32_t br[BR];  // sub-range << 16 | rank in it
 #pragma unroll
   for (int e = 0; e < BR; ++e) {
     br[e] = 0u;
     if (e * NT + t < n) {
       const uint32_t o = (uint32_t)(key[e] >> PB) - mn;
-      const uint32_t b = range <= (uint32_t)NT ? o : min(__umulhi(o, mul), (uint32_t)NT - 1u);
+      const uint32_t b = range <= (uint32_t)NS ? o : min(__umulhi(o, mul), (uint32_t)NS - 1u);
       br[e] = (b << 16) | (uint32_t)atomicAdd(&s_cnt[b], 1);
     }
   }
   __syncthreads();
-  const int c = s_cnt[t];
-  const bool over32 = __syncthreads_or(c > 32) != 0;
-  const bool over16 = __syncthreads_or(c > 16) != 0;
+  const int c0 = s_cnt[2 * t], c1 = s_cnt[2 * t + 1];
+  // each sub-range sorted alone when all hold at most 16 keys, else each
+  // thread's pair together when all pairs hold at most 32
+  const bool over32 = __syncthreads_or(c0 + c1 > 32) != 0;
+  const bool over16 = __syncthreads_or(c0 > 16 || c1 > 16) != 0;
   int tot;
-  const int st = block_exclusive_scan<NT>(c, s_ws, &tot);
-  s_bst[t] = st;
+  const int st = block_exclusive_scan<NT>(c0 + c1, s_ws, &tot);
+  s_bst[2 * t] = st;
+  s_bst[2 * t + 1] = st + c0;
   __syncthreads();
 #pragma unroll
   for (int e = 0; e < BR; ++e)
@@ -582,22 +590,21 @@ __device__ __forceinline__ void bucket_sort_keys(K (&key)[BR], int n, K* s_key, 
     block_sort_keys<NT>(key, s_key);
     return;
   }
+  auto sort_run = [&](auto nk, int from, int c) {
+    constexpr int N = decltype(nk)::value;
+    K kk[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) kk[i] = i < c ? s_key[from + i] : ~K(0);
+    lane_oddeven_sort<N>(kk);
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (i < c) s_key[from + i] = kk[i];
+  };
   if (over16) {
-    K kk[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) kk[i] = i < c ? s_key[st + i] : ~K(0);
-    lane_oddeven_sort<32>(kk);
-#pragma unroll
-    for (int i = 0; i < 32; ++i)
-      if (i < c) s_key[st + i] = kk[i];
+    sort_run(std::integral_constant<int, 32>{}, st, c0 + c1);
   } else {
-    K kk[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) kk[i] = i < c ? s_key[st + i] : ~K(0);
-    lane_oddeven_sort<16>(kk);
-#pragma unroll
-    for (int i = 0; i < 16; ++i)
-      if (i < c) s_key[st + i] = kk[i];
+    sort_run(std::integral_constant<int, 16>{}, st, c0);
+    sort_run(std::integral_constant<int, 16>{}, st + c0, c1);
   }
   __syncthreads();
 #pragma unroll
@@ -619,8 +626,8 @@ __global__ void __launch_bounds__(BS_NT, 4)
   __shared__ K s_key[BS_CAP];
   __shared__ uint32_t s_head[BS_CAP / 32];
   __shared__ int32_t s_hpre[BS_CAP / 32 + 1];
-  __shared__ int32_t s_cnt[BS_NT];
-  __shared__ int32_t s_bst[BS_NT];
+  __shared__ int32_t s_cnt[2 * BS_NT];
+  __shared__ int32_t s_bst[2 * BS_NT];
   __shared__ uint32_t s_red[2 * (BS_NT / 32)];
   __shared__ int32_t s_ws[BS_NT / 32 + 1];
   const int t = threadIdx.x;
