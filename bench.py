@@ -134,7 +134,8 @@ def parse_args(argv=None):
                    help="served workload: a second, overloading offered load (0 = skip)")
     p.add_argument("--autotune", type=int, default=0,
                    help="1 = run magnus_autotune (row sample of about 2^27 products, at most "
-                        "16 runs) before the warm-up and time its choice")
+                        "16 runs; batched workload: magnus_autotune_batched on the first "
+                        "wave, 2^28 products) before the warm-up and time its choice")
     p.add_argument("--numeric-graph", type=int, default=0,
                    help="1 = capture the numeric phase in a CUDA graph")
     p.add_argument("--l2-fetch", type=int, default=0,
@@ -677,6 +678,15 @@ def run_batched(args, dist):
     nw = max(1, min(args.batch_waves, count))
     bounds = [round(w * count / nw) for w in range(nw + 1)]
     stats = {"n_inter": 0, "nnz_c": 0, "stage_ms": {}, "rows_per_category": [0, 0, 0, 0]}
+    tuned = None
+    if args.autotune:
+        # untimed setup: tune on the first wave's packed products (a row
+        # sample), then plan every wave with the result
+        bp = magnus.BatchPlan(As[bounds[0]:bounds[1]], Bs[bounds[0]:bounds[1]], params, stream)
+        best, rep = bp.autotune(params, sample_products=1 << 28, max_trials=16)
+        bp.free()
+        params = best
+        tuned = dict(rep, params={name: getattr(best, name) for name, _ in best._fields_})
 
     def step(record=False):
         tot_i = tot_c = 0
@@ -762,7 +772,7 @@ def run_batched(args, dist):
         "gpu_launches": n_launch,
         "detail": {"stage_ms_untimed_step": stats["stage_ms"],
                    "rows_per_category": stats["rows_per_category"],
-                   "last_wave_plan": stats.get("plan")},
+                   "last_wave_plan": stats.get("plan"), "autotune": tuned},
     }
 
 
@@ -1023,7 +1033,7 @@ def _summary(res):
     out = {k: res[k] for k in keep if k in res}
     d = res.get("detail", {})
     for k in ("stage_ms", "t_over_t_ideal", "nnz_c", "stage_ms_untimed_step",
-              "rows_per_category", "last_wave_plan"):
+              "rows_per_category", "last_wave_plan", "autotune"):
         if k in d:
             out[k] = d[k]
     if "served_batched" in res:
@@ -1039,7 +1049,8 @@ def run_other_configs(args, dist):
     same process after the headline workload."""
     import torch
     out = {}
-    for name, extra in (("rmat20", ["--steps", "3"]), ("batched4096", ["--steps", "2"]),
+    for name, extra in (("rmat20", ["--steps", "3"]),
+                        ("batched4096", ["--steps", "2", "--autotune", "1"]),
                         ("served", ["--requests", "2000"])):
         torch.cuda.empty_cache()
         sub = parse_args(["--workload", name, "--warmup", "3", "--no-e2e", "--no-cpu",

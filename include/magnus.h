@@ -406,6 +406,16 @@ int magnus_autotune(const magnus_csr_t* A, const magnus_csr_t* B, const magnus_p
                     int64_t sample_products, int32_t max_trials, magnus_params_t* best,
                     magnus_tune_report_t* report, void* stream);
 
+/* magnus_autotune_batched - magnus_autotune on a batch's packed
+ * block-diagonal operands (the products' rows sampled together), so that
+ * later batches of the same kind of products can be planned with *best
+ * (magnus_plan_batched's params).  Packs the current values first (they are
+ * read by the trials); the batch itself is left as it was planned.  Status
+ * codes as for magnus_autotune. */
+int magnus_autotune_batched(magnus_batch_t batch, const magnus_params_t* base,
+                            int64_t sample_products, int32_t max_trials, magnus_params_t* best,
+                            magnus_tune_report_t* report, void* stream);
+
 /* ---- building-block microbenchmark ---------------------------------------
  * The steps of one reorder level (Section 4.1, Figures 5-6) on a stream of
  * `length` (index, value) pairs with indices in [0, m): histogram per chunk

@@ -328,6 +328,16 @@ int magnus_numeric_batched(magnus_batch_t b, const int64_t* c_row_ptr, int32_t* 
 
 magnus_plan_t magnus_batch_inner_plan(magnus_batch_t b) { return b ? b->inner : nullptr; }
 
+int magnus_autotune_batched(magnus_batch_t b, const magnus_params_t* base, int64_t sample_products,
+                            int32_t max_trials, magnus_params_t* best,
+                            magnus_tune_report_t* report, void* stream) {
+  if (!b || !best) return MAGNUS_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  b->last_stream = s;
+  MAG_TRY(pack_values(b, s));  // the trials read the packed values
+  return magnus_autotune(&b->pa, &b->pb, base, sample_products, max_trials, best, report, stream);
+}
+
 int magnus_batch_info(magnus_batch_t b, magnus_plan_info_t* info) {
   if (!b || !info) return MAGNUS_INVALID_ARG;
   return magnus_plan_info(b->inner, info);

@@ -144,6 +144,8 @@ SIGNATURES = {
     "magnus_autotune": (c_i32, [ctypes.POINTER(CsrDesc), ctypes.POINTER(CsrDesc),
                                 ctypes.POINTER(Params), c_i64, c_i32, ctypes.POINTER(Params),
                                 ctypes.POINTER(TuneReport), c_p]),
+    "magnus_autotune_batched": (c_i32, [c_p, ctypes.POINTER(Params), c_i64, c_i32,
+                                        ctypes.POINTER(Params), ctypes.POINTER(TuneReport), c_p]),
     "magnus_chunk_model": (c_i32, [c_i64, c_i64, c_i64, c_i32, ctypes.POINTER(ChunkModel)]),
     "magnus_microbench_rates": (c_i32, [ctypes.POINTER(Rates), c_p]),
 }
@@ -575,6 +577,18 @@ class BatchPlan:
         info = PlanInfo()
         _check(_lib().magnus_batch_info(c_p(self.handle), ctypes.byref(info)), "magnus_batch_info")
         return info.as_dict()
+
+    def autotune(self, base: Params | None = None, sample_products=0, max_trials=16):
+        """magnus_autotune_batched: (best Params, report dict) for batches of
+        products like these."""
+        best = Params()
+        rep = TuneReport()
+        _check(_lib().magnus_autotune_batched(c_p(self.handle),
+                                              ctypes.byref(base) if base is not None else None,
+                                              sample_products, max_trials, ctypes.byref(best),
+                                              ctypes.byref(rep), c_p(self.stream.cuda_stream)),
+               "magnus_autotune_batched")
+        return best, {name: getattr(rep, name) for name, _ in rep._fields_}
 
     def enable_timing(self, on=True):
         magnus_enable_timing(_lib().magnus_batch_inner_plan(c_p(self.handle)), on)

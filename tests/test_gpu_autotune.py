@@ -60,3 +60,31 @@ def test_autotune_cache_keyed_by_base_params():
     assert_parity(got, A, A)
     _, rep3 = magnus.autotune(dA, dA, base, max_trials=3)
     assert rep3["from_cache"] == 1
+
+
+def test_autotune_batched():
+    # tuned on a batch's packed products; a batch planned with the result
+    # still computes every product's oracle C
+    from paper_2501_07056_gb300 import magnus
+    import oracle
+    from tests._util import values_close
+    rng = np.random.default_rng(5)
+    ns = [int(x) for x in rng.integers(200, 3000, size=12)]
+    As = [inputs.ragged(n, n, 2, 32, seed=11, matrix_id=2 * i + 1) for i, n in enumerate(ns)]
+    Bs = [inputs.ragged(n, n, 2, 32, seed=11, matrix_id=2 * i + 2) for i, n in enumerate(ns)]
+    dAs = [magnus.DeviceCSR.from_host(a) for a in As]
+    dBs = [magnus.DeviceCSR.from_host(b) for b in Bs]
+    bp = magnus.BatchPlan(dAs, dBs)
+    best, rep = bp.autotune(max_trials=8)
+    bp.free()
+    assert 1 <= rep["trials"] <= 8 and rep["best_ms"] <= rep["base_ms"]
+    bp = magnus.BatchPlan(dAs, dBs, best)
+    bp.symbolic()
+    bp.numeric()
+    for i in range(len(ns)):
+        C = bp.result(i)
+        ref = oracle.spgemm(As[i], Bs[i], threads=8)
+        assert np.array_equal(C.row_ptr.cpu().numpy(), ref.row_ptr)
+        assert np.array_equal(C.col.cpu().numpy(), ref.col)
+        assert values_close(C.val.cpu().numpy(), ref.val, ref.abs).all()
+    bp.free()
