@@ -798,10 +798,14 @@ def run_served(args, dist):
 
     # capacity of the one-call path: a closed-loop sample (all arrive at 0)
     nsamp = min(len(descs), 200)
+    # PyTorch caches blocks per stream and every server has streams of its
+    # own: the cache goes back to the device between servers (untimed)
     serve.Server(work, params, mode="single", device=dev).run(reqs_at(1e12, descs[:16]))
+    torch.cuda.empty_cache()
     srv = serve.Server(work, params, mode="single", device=dev)
     srv.run(reqs_at(1e12, descs[:nsamp]))
     cap = srv.executed_products / srv.makespan
+    torch.cuda.empty_cache()
     srvb = serve.Server(work, params, mode="batched", n_streams=3, max_requests=64,
                         max_products=1 << 30, device=dev)
     srvb.run(reqs_at(1e12, descs[:nsamp]))
@@ -811,6 +815,7 @@ def run_served(args, dist):
     out = {}
     for mode in ("single", "batched"):
         reqs = reqs_at(rate)
+        torch.cuda.empty_cache()
         srv = serve.Server(work, params, mode=mode, n_streams=3, max_requests=64,
                            max_products=1 << 30, device=dev)
         clocks = ClockSampler(dev.index).start()
@@ -821,7 +826,7 @@ def run_served(args, dist):
         out[mode] = dict(serve.latency_stats(reqs), requests_per_s=len(reqs) / srv.makespan,
                          gflops=2.0 * prods / srv.makespan / 1e9, makespan_s=srv.makespan,
                          batches=srv.n_batches, gpu_launches=magnus.magnus_launch_count() - n0,
-                         clocks=clk)
+                         cache_reclaims=srv.reclaims, clocks=clk)
     b, o = out["batched"], out["single"]
     high = None
     if args.rho_high > 0:
@@ -831,11 +836,13 @@ def run_served(args, dist):
         high = {"rho": args.rho_high, "arrival_rate_per_s": rate_h}
         for mode in ("single", "batched"):
             reqs = reqs_at(rate_h)
+            torch.cuda.empty_cache()
             srv = serve.Server(work, params, mode=mode, n_streams=3, max_requests=64,
                                max_products=1 << 30, device=dev)
             srv.run(reqs)
             high[mode] = dict(serve.latency_stats(reqs), requests_per_s=len(reqs) / srv.makespan,
-                              makespan_s=srv.makespan, batches=srv.n_batches)
+                              makespan_s=srv.makespan, batches=srv.n_batches,
+                              cache_reclaims=srv.reclaims)
     return {
         "metric": "served products/s", "value": b["requests_per_s"], "unit": "products/s",
         "n_gpus": dist.world, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * b["makespan_s"],
@@ -1017,6 +1024,11 @@ def run_e2e(args, dist, A, dev, params, n_inter, nnz_c):
             "parts_ms": mean,
             "step_ms": {"min": min(walls), "median": statistics.median(walls),
                         "max": max(walls)} if walls else {},
+            # steps above 1.5x the median, with their parts: which copy was slow
+            "slow_steps": [dict({k: round(v, 2) for k, v in parts[i].items()}, step=i,
+                                wall_ms=round(walls[i], 2))
+                           for i in range(len(walls))
+                           if walls[i] > 1.5 * statistics.median(walls)][:8],
             "link_gbs": {"h2d": link_h2d, "d2h": link_d2h,
                          "h2d_after": link_h2d_after, "d2h_after": link_d2h_after,
                          "how": "plain pinned copies of 1 GB pieces on one stream into the "

@@ -18,6 +18,11 @@ resident until the request completes, and runs a loop that
   * retires a batch when its completion event fires: each request's latency
     is completion time minus arrival time.
 
+The free-memory figure counts the blocks PyTorch's caching allocator holds
+unused, which the library's own stream-ordered pool cannot take: before the
+library allocates, the server hands that cache back to the device when free
+memory and the pool's idle bytes alone fall short.
+
 The one-call-per-product server (``mode="single"``) runs the same loop with
 one request at a time through the single-product API, on one stream.
 
@@ -144,6 +149,7 @@ class Server:
         self.executed_products = 0
         self.plan_waits = 0       # batches whose planning waited for memory
         self.launch_waits = 0     # planned batches whose launch waited for memory
+        self.reclaims = 0         # times PyTorch's unused cache was handed back
 
     def free_memory(self) -> int:
         """Device bytes new work may use: free device memory, plus what the
@@ -155,6 +161,23 @@ class Server:
         cached = torch.cuda.memory_reserved(self.device) - torch.cuda.memory_allocated(self.device)
         return free + pool_idle + cached - self.mem_reserve
 
+    def _reclaim(self, nbytes: int):
+        """PyTorch's cached blocks count in ``free_memory()``, but the
+        library's stream-ordered pool cannot take them (nor can PyTorch reuse
+        blocks cached on another server's streams).  When free device memory
+        plus the pool's idle bytes, less the reserve, falls short of the
+        ``nbytes`` that the next step allocates, PyTorch's unused cache goes
+        back to the device first."""
+        from . import magnus
+        torch = self.torch
+        cached = torch.cuda.memory_reserved(self.device) - torch.cuda.memory_allocated(self.device)
+        if cached <= 0:
+            return
+        free, pool_idle = magnus.magnus_device_memory()
+        if free + pool_idle - self.mem_reserve < nbytes:
+            torch.cuda.empty_cache()
+            self.reclaims += 1
+
     def _estimate(self, reqs) -> int:
         est = getattr(self.executor, "estimate_bytes", None)
         return sum(est(r) for r in reqs) if est is not None else 0
@@ -163,6 +186,7 @@ class Server:
     def _plan(self, reqs, stream, batch_id):
         from . import magnus
         torch = self.torch
+        self._reclaim(self._estimate(reqs))
         f = _Flight()
         f.reqs, f.stream, f.batch = reqs, stream, batch_id
         with torch.cuda.stream(stream):
@@ -192,6 +216,7 @@ class Server:
 
     def _launch(self, f):
         torch = self.torch
+        self._reclaim(f.nbytes)
         with torch.cuda.stream(f.stream):
             f.outputs = f.plan.numeric()
             f.event = torch.cuda.Event()

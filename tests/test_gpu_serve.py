@@ -114,6 +114,36 @@ def test_free_memory_figure():
     assert srv.free_memory() >= free
 
 
+def test_reclaims_pytorch_cache_when_the_library_is_short():
+    """Blocks PyTorch cached on another stream count as free memory but the
+    library's pool cannot take them: when the library's own figure is short,
+    the server hands them back before it allocates; when it is not, it keeps
+    them."""
+    import torch
+    from paper_2501_07056_gb300 import serve
+    dev = torch.device("cuda", 0)
+    side = torch.cuda.Stream(dev)
+    with torch.cuda.stream(side):
+        x = torch.empty(64 << 20, dtype=torch.uint8, device=dev)
+    del x
+    torch.cuda.synchronize()
+
+    def cached():
+        return torch.cuda.memory_reserved(dev) - torch.cuda.memory_allocated(dev)
+    before = cached()
+    assert before >= 64 << 20
+    roomy = serve.Server(serve.StencilTimesRandom(), mem_reserve=0)
+    roomy._reclaim(1 << 20)
+    assert roomy.reclaims == 0 and cached() == before
+    total = torch.cuda.get_device_properties(dev).total_memory
+    short = serve.Server(serve.StencilTimesRandom(), mem_reserve=total)
+    short._reclaim(1 << 20)
+    assert short.reclaims == 1
+    # the side stream's block was a segment of its own; segments that still
+    # hold live blocks of earlier tests stay
+    assert cached() <= before - (64 << 20)
+
+
 def test_latency_accounting():
     from paper_2501_07056_gb300 import serve
     reqs = _requests(30, rate=200.0, k_lo=3, k_hi=8)
