@@ -53,15 +53,59 @@ cudaError_t launch_validate(const Csr& M, int* d_flag, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Row analysis (Section 3.1): P_i, column range [lo, hi] of the intermediate
 // product (from the first and last column of each referenced B row, which is
-// valid because rows are sorted), and the bin of the row.  V lanes per row.
+// valid because rows are sorted), and the bin of the row.
 // Also writes the segment table: for every nonzero j of A, the start and the
 // length of the B row it selects (B.rowPtr[A.col[j]] and the row's nnz,
 // packed into one word by seg_pack), so later passes read it as a stream
 // instead of gathering B.rowPtr again.
-template <int V>
-__global__ void k_rowinfo(Csr A, Csr B, CatParams cp, int64_t* __restrict__ P,
-                          uint8_t* __restrict__ bin, int32_t* __restrict__ lo_out,
-                          int32_t* __restrict__ hi_out, uint64_t* __restrict__ seg) {
+//
+// The B.rowPtr gathers are the pass's cost.  When B has fewer than 2^32
+// nonzeros they read a copy of B.rowPtr narrowed to 32 bits (RP = uint32_t):
+// half the bytes, and for B of up to about 2^25 rows a table that stays in
+// L2 while A's columns and the segment table stream past it.
+
+// Bin of a row from its products alone; need_range when the choice needs the
+// row's column range.
+__device__ __forceinline__ int rowinfo_sort_bin(int64_t q) {
+  return q <= 32 ? BIN_SORT32 : q <= 64 ? BIN_SORT64 : q <= 128 ? BIN_SORT128
+         : q <= 256 ? BIN_SORT256 : q <= 512 ? BIN_SORT512 : BIN_SORT1024;
+}
+
+__device__ __forceinline__ int rowinfo_first_bin(int64_t p, const CatParams& cp, bool* need_range) {
+  *need_range = false;
+  if (p <= 0) return BIN_EMPTY;
+  const bool sort_ok = p <= SORT_BLOCK_MAX;
+  const bool want_sort = (cp.force == MAGNUS_CAT_SORT) ? sort_ok
+                         : (cp.force < 0 ? (p < cp.sort_threshold) : false);
+  if (want_sort) return rowinfo_sort_bin(p);
+  *need_range = true;
+  return BIN_EMPTY;
+}
+
+// Bin of a row whose column range [lo, hi] was needed.
+__device__ __forceinline__ int rowinfo_range_bin(int64_t p, int32_t lo, int32_t hi,
+                                                 const CatParams& cp) {
+  const int64_t range = (int64_t)hi - lo + 1;
+  const int64_t nfine = (int64_t)(hi >> cp.fine_shift) - (lo >> cp.fine_shift) + 1;
+  const bool dense_ok = range <= cp.dense_cols;
+  const bool fine_ok = nfine <= cp.fine_max_chunks && p <= cp.fine_max_products &&
+                       p < ((int64_t)1 << 31);
+  if (cp.force == MAGNUS_CAT_COARSE) return BIN_COARSE;
+  if (cp.force == MAGNUS_CAT_FINE) return fine_ok ? BIN_FINE : BIN_COARSE;
+  // automatic: a row of at most wide_sort_max products that fills less than
+  // half of its column range sorts instead (the dense accumulator's work
+  // follows the range, the sort's the products)
+  if (dense_ok && (cp.force >= 0 || p > cp.wide_sort_max || range <= 2 * p)) return BIN_DENSE;
+  if (cp.force < 0 && p <= cp.wide_sort_max) return rowinfo_sort_bin(p);
+  return (cp.prefer_fine && fine_ok) ? BIN_FINE : BIN_COARSE;
+}
+
+// V lanes per row (rows of more than about 8 nonzeros on average).
+template <int V, typename RP>
+__global__ void k_rowinfo(Csr A, const RP* __restrict__ brp, Csr B, CatParams cp,
+                          int64_t* __restrict__ P, uint8_t* __restrict__ bin,
+                          int32_t* __restrict__ lo_out, int32_t* __restrict__ hi_out,
+                          uint64_t* __restrict__ seg) {
   const int sub = threadIdx.x & (V - 1);
   const int64_t groups = (int64_t)gridDim.x * (blockDim.x / V);
   const unsigned gmask = (V == 32) ? FULL : (((1u << V) - 1) << ((threadIdx.x & 31) & ~(V - 1)));
@@ -82,8 +126,8 @@ __global__ void k_rowinfo(Csr A, Csr B, CatParams cp, int64_t* __restrict__ P,
       const bool two = j2 < e;
       const int32_t c = A.col[j];
       const int32_t c2 = two ? A.col[j2] : 0;
-      const int64_t b0 = B.rp[c], b1 = B.rp[c + 1];
-      const int64_t b2 = two ? B.rp[c2] : 0, b3 = two ? B.rp[c2 + 1] : 0;
+      const int64_t b0 = (int64_t)brp[c], b1 = (int64_t)brp[c + 1];
+      const int64_t b2 = two ? (int64_t)brp[c2] : 0, b3 = two ? (int64_t)brp[c2 + 1] : 0;
       p += (b1 - b0) + (b3 - b2);
       seg[j] = seg_pack(b0, b1 - b0);
       if (two) seg[j2] = seg_pack(b2, b3 - b2);
@@ -94,25 +138,10 @@ __global__ void k_rowinfo(Csr A, Csr B, CatParams cp, int64_t* __restrict__ P,
     }
 #pragma unroll
     for (int d = V / 2; d > 0; d >>= 1) p += __shfl_xor_sync(gmask, p, d, V);
-    // category
-    int b = BIN_EMPTY;
-    bool need_range = false;
-    auto sort_bin = [](int64_t q) {
-      return q <= 32 ? BIN_SORT32 : q <= 64 ? BIN_SORT64 : q <= 128 ? BIN_SORT128
-             : q <= 256 ? BIN_SORT256 : q <= 512 ? BIN_SORT512 : BIN_SORT1024;
-    };
-    if (p > 0) {
-      const bool sort_ok = p <= SORT_BLOCK_MAX;
-      const bool want_sort = (cp.force == MAGNUS_CAT_SORT) ? sort_ok
-                             : (cp.force < 0 ? (p < cp.sort_threshold) : false);
-      if (want_sort) {
-        b = sort_bin(p);
-      } else {
-        need_range = true;
-      }
-    }
-    int32_t lo = 0x7fffffff, hi = -1;
     // need_range is uniform within a group (p is the group-reduced sum)
+    bool need_range = false;
+    int b = rowinfo_first_bin(p, cp, &need_range);
+    int32_t lo = 0x7fffffff, hi = -1;
     if (need_range) {
       if (e - s <= 2 * V) {  // one step: the bounds are r0..r3 (empty pairs when unused)
         if (r1 > r0) {
@@ -127,7 +156,7 @@ __global__ void k_rowinfo(Csr A, Csr B, CatParams cp, int64_t* __restrict__ P,
       } else {
         for (int64_t j = s + sub; j < e; j += V) {
           const int32_t c = A.col[j];
-          const int64_t bs = B.rp[c], be = B.rp[c + 1];
+          const int64_t bs = (int64_t)brp[c], be = (int64_t)brp[c + 1];
           if (be > bs) {
             const int32_t c0 = B.col[bs], c1 = B.col[be - 1];
             lo = c0 < lo ? c0 : lo;
@@ -135,8 +164,6 @@ __global__ void k_rowinfo(Csr A, Csr B, CatParams cp, int64_t* __restrict__ P,
           }
         }
       }
-    }
-    if (need_range) {
 #pragma unroll
       for (int d = V / 2; d > 0; d >>= 1) {
         int32_t l2 = __shfl_xor_sync(gmask, lo, d, V);
@@ -144,21 +171,7 @@ __global__ void k_rowinfo(Csr A, Csr B, CatParams cp, int64_t* __restrict__ P,
         lo = l2 < lo ? l2 : lo;
         hi = h2 > hi ? h2 : hi;
       }
-    }
-    if (need_range) {
-      const int64_t range = (int64_t)hi - lo + 1;
-      const int64_t nfine = (int64_t)(hi >> cp.fine_shift) - (lo >> cp.fine_shift) + 1;
-      const bool dense_ok = range <= cp.dense_cols;
-      const bool fine_ok = nfine <= cp.fine_max_chunks && p <= cp.fine_max_products &&
-                           p < ((int64_t)1 << 31);
-      if (cp.force == MAGNUS_CAT_COARSE) b = BIN_COARSE;
-      else if (cp.force == MAGNUS_CAT_FINE) b = fine_ok ? BIN_FINE : BIN_COARSE;
-      // automatic: a row of at most wide_sort_max products that fills less
-      // than half of its column range sorts instead (the dense
-      // accumulator's work follows the range, the sort's the products)
-      else if (dense_ok && (cp.force >= 0 || p > cp.wide_sort_max || range <= 2 * p)) b = BIN_DENSE;
-      else if (cp.force < 0 && p <= cp.wide_sort_max) b = sort_bin(p);
-      else b = (cp.prefer_fine && fine_ok) ? BIN_FINE : BIN_COARSE;
+      b = rowinfo_range_bin(p, lo, hi, cp);
     }
     if (active && sub == 0) {
       P[i] = p;
@@ -169,25 +182,126 @@ __global__ void k_rowinfo(Csr A, Csr B, CatParams cp, int64_t* __restrict__ P,
   }
 }
 
+// One lane per row (rows of at most about 8 nonzeros on average): each step
+// issues the loads of U entries of the row together, so a warp keeps up to
+// 32 * U column loads and then 32 * U B-row-bound gathers in flight instead
+// of a few per lane.
+template <int U, typename RP>
+__global__ void __launch_bounds__(256) k_rowinfo_lane(Csr A, const RP* __restrict__ brp, Csr B,
+                                                      CatParams cp, int64_t* __restrict__ P,
+                                                      uint8_t* __restrict__ bin,
+                                                      int32_t* __restrict__ lo_out,
+                                                      int32_t* __restrict__ hi_out,
+                                                      uint64_t* __restrict__ seg) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n_rows; i += stride) {
+    const int64_t s = A.rp[i], e = A.rp[i + 1];
+    int64_t p = 0;
+    for (int64_t j0 = s; j0 < e; j0 += U) {
+      const int64_t left = e - j0;
+      int32_t c[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) c[k] = k < left ? __ldg(A.col + j0 + k) : 0;
+      int64_t b0[U], b1[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        b0[k] = k < left ? (int64_t)__ldg(brp + c[k]) : 0;
+        b1[k] = k < left ? (int64_t)__ldg(brp + c[k] + 1) : 0;
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        if (k < left) {
+          p += b1[k] - b0[k];
+          seg[j0 + k] = seg_pack(b0[k], b1[k] - b0[k]);
+        }
+      }
+    }
+    bool need_range = false;
+    int b = rowinfo_first_bin(p, cp, &need_range);
+    int32_t lo = 0x7fffffff, hi = -1;
+    if (need_range) {
+      for (int64_t j0 = s; j0 < e; j0 += U) {
+        const int64_t left = e - j0;
+        int32_t c[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) c[k] = k < left ? __ldg(A.col + j0 + k) : 0;
+        int64_t bs[U], be[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          bs[k] = k < left ? (int64_t)__ldg(brp + c[k]) : 0;
+          be[k] = k < left ? (int64_t)__ldg(brp + c[k] + 1) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          if (be[k] > bs[k]) {  // empty B rows (and the unused slots) add nothing
+            const int32_t c0 = B.col[bs[k]], c1 = B.col[be[k] - 1];
+            lo = c0 < lo ? c0 : lo;
+            hi = c1 > hi ? c1 : hi;
+          }
+        }
+      }
+      b = rowinfo_range_bin(p, lo, hi, cp);
+    }
+    P[i] = p;
+    bin[i] = (uint8_t)b;
+    lo_out[i] = need_range ? lo : 0;
+    hi_out[i] = need_range ? hi : -1;
+  }
+}
+
+__global__ void k_narrow_rp(const int64_t* __restrict__ rp, int64_t n,
+                            uint32_t* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (uint32_t)rp[i];
+}
+
+template <typename RP>
+static void launch_rowinfo_rp(const Csr& A, const RP* brp, const Csr& B, CatParams cp,
+                              int64_t* P, uint8_t* bin, int32_t* lo, int32_t* hi, uint64_t* seg,
+                              cudaStream_t s) {
+  const double avg = A.n_rows ? (double)A.nnz / (double)A.n_rows : 0.0;
+  const int nt = 256;
+  if (avg <= 8.0) {
+    const unsigned g = grid_cap(cdiv(A.n_rows, nt), 1 << 20);
+    k_rowinfo_lane<8, RP><<<g, nt, 0, s>>>(A, brp, B, cp, P, bin, lo, hi, seg);
+    return;
+  }
+  int v = 1;  // lanes per row: about half the row's nonzeros (two per lane)
+  while (v < 32 && 2 * v < avg) v <<= 1;
+  const unsigned g = grid_cap(cdiv(A.n_rows * v, nt), 1 << 20);
+  switch (v) {
+    case 8: k_rowinfo<8, RP><<<g, nt, 0, s>>>(A, brp, B, cp, P, bin, lo, hi, seg); break;
+    case 16: k_rowinfo<16, RP><<<g, nt, 0, s>>>(A, brp, B, cp, P, bin, lo, hi, seg); break;
+    default: k_rowinfo<32, RP><<<g, nt, 0, s>>>(A, brp, B, cp, P, bin, lo, hi, seg); break;
+  }
+}
+
 cudaError_t launch_rowinfo(const Csr& A, const Csr& B, CatParams cp, int64_t* P, uint8_t* bin,
                            int32_t* lo, int32_t* hi, uint64_t* seg,
                            cudaStream_t s) {
   if (A.n_rows == 0) return cudaSuccess;
-  const double avg = A.n_rows ? (double)A.nnz / (double)A.n_rows : 0.0;
-  const int nt = 256;
-  int v = 1;  // lanes per row: about half the row's nonzeros (two per lane)
-  while (v < 32 && 2 * v < avg) v <<= 1;
-  unsigned g = grid_cap(cdiv(A.n_rows * v, nt), 1 << 20);
-  switch (v) {
-    case 1: k_rowinfo<1><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg); break;
-    case 2: k_rowinfo<2><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg); break;
-    case 4: k_rowinfo<4><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg); break;
-    case 8: k_rowinfo<8><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg); break;
-    case 16: k_rowinfo<16><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg); break;
-    default: k_rowinfo<32><<<g, nt, 0, s>>>(A, B, cp, P, bin, lo, hi, seg); break;
+  // the 32-bit copy of B.rowPtr, stream-ordered and freed after the pass; the
+  // pass reads B.rowPtr itself when B has 2^32 nonzeros or more or the copy
+  // cannot be allocated
+  uint32_t* brp32 = nullptr;
+  if (B.nnz < ((int64_t)1 << 32) &&
+      cudaMallocAsync(reinterpret_cast<void**>(&brp32), (size_t)(B.n_rows + 1) * 4, s) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    brp32 = nullptr;
+  }
+  if (brp32) {
+    k_narrow_rp<<<grid_cap(cdiv(B.n_rows + 1, 256), 4096), 256, 0, s>>>(B.rp, B.n_rows, brp32);
+    count_launch();
+    launch_rowinfo_rp<uint32_t>(A, brp32, B, cp, P, bin, lo, hi, seg, s);
+  } else {
+    launch_rowinfo_rp<int64_t>(A, B.rp, B, cp, P, bin, lo, hi, seg, s);
   }
   count_launch();
-  return cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
+  if (brp32) cudaFreeAsync(brp32, s);
+  return e;
 }
 
 // ---------------------------------------------------------------------------
