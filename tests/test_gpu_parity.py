@@ -62,6 +62,25 @@ def test_ragged_mixed_categories(seed, T):
     assert_parity(got, A, B)
 
 
+@pytest.mark.parametrize("force", [-1, SORT, DENSE, FINE, COARSE])
+def test_sparse_a_long_b_rows(force):
+    """A with at most 8 nonzeros per row on average (the row analysis runs
+    one lane per row, eight entries per step) over B rows of 0..400 entries:
+    rows from empty to several thousand products, so the products alone place
+    some rows and the column range places the others (dense or sort), and
+    every forced category reads the range of every row."""
+    A = inputs.ragged(3000, 4000, 0, 12, seed=21, matrix_id=1)
+    B = inputs.ragged(4000, 6000, 0, 400, seed=21, matrix_id=2)
+    assert A.nnz <= 8 * A.n_rows
+    got = run_gpu(A, B, P(force_category=force, validate=1))
+    assert_parity(got, A, B)
+    cats = got["info"]["rows_per_category"]
+    if force < 0:
+        assert cats[SORT] > 0 and cats[DENSE] > 0
+    elif force != SORT:
+        assert cats[force] > 0
+
+
 @pytest.mark.parametrize("T,wide", [(512, 0), (1025, 0), (0, 0), (0, -1), (100, 300)])
 def test_block_sort_bins(T, wide):
     # rows of about 200-1600 products over 200000 columns: the block sort bins
