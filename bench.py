@@ -5,7 +5,8 @@ Workload (one step = the whole hot path on one product): C = A*A with A a
 uniform random square matrix, n = 2^24, exactly 8 distinct uniform columns per
 row, FP64 values U(-1, 1), seed 0 (1.07e9 intermediate products).  A step is
 plan (setup, Section 3.1) + symbolic (Section 2.1) + allocation of C +
-numeric (Algorithms 1-4), timed with CUDA events on the calling stream.  The
+numeric (Algorithms 1-4) + freeing the plan, timed with CUDA events on the
+calling stream.  The
 inputs (1.6 GB) are larger than the 126 MB L2, so no flush is needed between
 steps.
 
@@ -328,7 +329,7 @@ def workload_config(args, n_rows, nnz_a, n_inter, dist):
             "n_interprod": int(n_inter),
             "parallelism": "replicas" if dist.world > 1 else "single",
             "l2": "inputs larger than L2 (A and B exceed the 126 MB L2), no flush",
-            "step": "plan+symbolic+alloc C+numeric"}
+            "step": "plan+symbolic+alloc C+numeric+free plan"}
 
 
 # The paper's massive nonsquare uniform workload (Section 4.3): C has 4096
