@@ -1,5 +1,6 @@
 """Host logic of the serving loop (no GPU): FIFO batch formation under the
-product and request budgets, and output-memory admission."""
+product and request budgets, output-memory admission, and when the server
+hands PyTorch's unused cache back before the library allocates."""
 from paper_2501_07056_gb300.serve import Request, Scheduler, make_requests, stencil_products
 from paper_2501_07056_gb300 import inputs
 
@@ -86,3 +87,46 @@ def test_make_requests_arrivals():
     arr = [r.arrival for r in reqs]
     assert arr == sorted(arr) and arr[0] > 0
     assert abs(arr[-1] - sum(d["gap"] for d in descs) / 100.0) < 1e-9
+
+
+def test_reclaim_decision_on_the_host(monkeypatch):
+    """The server hands PyTorch's unused cache back only when it holds some
+    and free device memory plus the library pool's idle bytes, less the
+    reserve, is short of the bytes about to be allocated (fake memory
+    figures, no GPU)."""
+    from paper_2501_07056_gb300 import magnus, serve
+
+    class FakeCuda:
+        def __init__(self):
+            self.reserved, self.allocated, self.emptied = 0, 0, 0
+
+        def memory_reserved(self, dev=None):
+            return self.reserved
+
+        def memory_allocated(self, dev=None):
+            return self.allocated
+
+        def empty_cache(self):
+            self.emptied += 1
+            self.reserved = self.allocated
+
+    class FakeTorch:
+        cuda = FakeCuda()
+
+    mem = {"free": 0, "idle": 0}
+    monkeypatch.setattr(magnus, "magnus_device_memory", lambda: (mem["free"], mem["idle"]))
+    srv = object.__new__(serve.Server)
+    srv.torch, srv.device, srv.mem_reserve, srv.reclaims = FakeTorch, None, 100, 0
+    cuda = FakeTorch.cuda
+
+    # nothing cached: nothing to hand back, however short the library is
+    srv._reclaim(10 ** 9)
+    assert srv.reclaims == 0 and cuda.emptied == 0
+    # cached blocks, and free + idle - reserve covers the request: kept
+    cuda.reserved, cuda.allocated = 5000, 1000
+    mem["free"], mem["idle"] = 600, 500
+    srv._reclaim(1000)
+    assert srv.reclaims == 0 and cuda.reserved == 5000
+    # one byte more than that: handed back
+    srv._reclaim(1001)
+    assert srv.reclaims == 1 and cuda.emptied == 1 and cuda.reserved == 1000
